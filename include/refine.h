@@ -1,0 +1,241 @@
+/*
+ * refine.h -- C ABI of librefine, a GB300 (sm_103a) implementation of the
+ * rendering-free primitive importance pass of REFINE (arXiv 2606.09074):
+ * per-primitive Hessian-weight scoring (Sec. 3.2, Eq. 7 and Eq. 20), ratio
+ * pruning by global rank (Sec. 3.3) and compaction of the kept primitives.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns a refine_status; REFINE_OK is 0.  On failure a
+ *    human-readable message is available from refine_last_error(ctx).
+ *    Nothing aborts the process.
+ *  - "_dev" pointers are CUDA device pointers on the context's device;
+ *    "_host" pointers are host memory (pinned host memory makes the copies
+ *    asynchronous and fast; pageable memory works but is slower).
+ *  - The caller owns every buffer it passes.  The library never frees or
+ *    retains caller buffers after a call returns.  Scratch memory is owned
+ *    by the context, grows on demand and is released by refine_ctx_destroy.
+ *  - Work is enqueued on the caller's stream and is asynchronous unless a
+ *    function says it synchronises.  A context is not thread-safe: calls on
+ *    one context must be issued from one thread and ordered on one stream,
+ *    because they share the context's scratch memory.
+ *  - Errors found by device code (NaN / Inf inputs, invalid cameras, a
+ *    bounded wait that ran out) are recorded in a device status word and
+ *    reported by the next synchronising call (refine_select with a
+ *    threshold_out, refine_compact with an n_keep_out, refine_ctx_check).
+ *  - Sizes: 0 <= n <= 2^31 - 1 primitives; 1 <= n_views <= 65535.
+ */
+#ifndef REFINE_H
+#define REFINE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *refine_stream_t;
+
+typedef enum refine_status {
+    REFINE_OK = 0,
+    REFINE_EINVAL = 1,      /* bad argument (NULL, size or ratio out of range, misaligned) */
+    REFINE_ENOMEM = 2,      /* device or pinned allocation failed                          */
+    REFINE_ECUDA = 3,       /* CUDA runtime error; details in refine_last_error            */
+    REFINE_ENONFINITE = 4,  /* NaN or Inf in an input that the device read                 */
+    REFINE_ETIMEOUT = 5,    /* a bounded device wait ran out                               */
+    REFINE_EBUSY = 6,
+    REFINE_ECANCELLED = 7,
+    REFINE_ENOTFOUND = 8
+} refine_status;
+
+/* Storage type of primitive rows 3..58 (positions are always float32). */
+enum { REFINE_F32 = 0, REFINE_BF16 = 1 };
+
+/* refine_params.flags */
+#define REFINE_FLAG_NO_VIS       (1 << 0) /* Table 3 "w/o V": alpha -> 1 in Eq. 20          */
+#define REFINE_FLAG_NO_PROJ      (1 << 1) /* Table 3 "w/o P": 1/(z^2+eta) -> 1 in Eq. 20    */
+#define REFINE_FLAG_EQUAL_LAMBDA (1 << 2) /* Table 3 "Equal lambda^k": lambda^k = 1/3       */
+#define REFINE_FLAG_NORM_ATTR    (1 << 3) /* G~^k = m^k / mean_j(m^k_j) (default on)        */
+
+/* Defaults.  eta is the paper's stability constant (Eq. 17, Sec. 3.2).  The
+ * paper calibrates lambda~ by expectations E[.] (Eq. 18) without printing
+ * them; these are ln F_gem, F_col and F_opa of 1,000,000 synthetic
+ * core-shell primitives (seed 12345) computed in FP64. */
+#define REFINE_DEFAULT_ETA      0.05
+#define REFINE_DEFAULT_E_LN_GEM (-0.4889612576346142)
+#define REFINE_DEFAULT_E_COL    0.008896804239666543
+#define REFINE_DEFAULT_E_OPA    0.1515067583205341
+
+/* A pinhole camera (Eq. 13).  80 bytes.  R (row-major) and t map world
+ * points to camera space with OpenCV axes (x right, y down, z forward):
+ * x_cam = R x_world + t.  Pixel (u, v) = (fx x/z + cx, fy y/z + cy); the
+ * image is the closed rectangle [0, width] x [0, height].  Requirements:
+ * all fields finite, fx, fy > 0, width, height >= 1, 0 < znear < zfar. */
+typedef struct refine_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear, zfar;
+} refine_camera;
+
+/* A scene of n primitives in structure-of-arrays form (Eq. 1: mean, scale,
+ * rotation, SH colour, opacity -- 59 parameters per primitive).
+ *   pos   device, float32 [3][row_stride]: rows 0-2, mean x, y, z
+ *   attr  device, [56][row_stride] in `dtype` (float32 or bfloat16):
+ *           row 0-2   log-scale
+ *           row 3-6   rotation quaternion (w, x, y, z), need not be unit
+ *           row 7     opacity logit
+ *           row 8-10  SH DC (r, g, b)
+ *           row 11-55 SH degree 1-3, 15 coefficients x 3 channels
+ *   row_stride  elements between consecutive rows, >= n (for BF16 the
+ *           stride counts bfloat16 elements of attr and float32 of pos).
+ * pos and attr must be 16-byte aligned. */
+typedef struct refine_scene {
+    int64_t n;
+    int32_t dtype;
+    int32_t reserved;
+    const float *pos;
+    const void *attr;
+    int64_t row_stride;
+} refine_scene;
+
+/* Method parameters.  Fill with refine_params_default() and override. */
+typedef struct refine_params {
+    float eta;        /* Eq. 17 and Eq. 18 stability constant (> 0)                  */
+    float luma[3];    /* weights of the perceptual luma Y of the SH DC colour          */
+    double e_ln_gem;  /* Eq. 18 calibration E[ln F_gem] (nonzero)                      */
+    double e_col;     /* Eq. 18 calibration E[F_col]    (nonzero)                      */
+    double e_opa;     /* Eq. 18 calibration E[F_opa]    (nonzero)                      */
+    int32_t flags;    /* REFINE_FLAG_*                                                 */
+    int32_t reserved;
+} refine_params;
+
+/* Scene statistics computed on the device (Eq. (features), Eq. 18-19). */
+typedef struct refine_scene_stats {
+    double F_col, F_opa, F_gem;
+    double lambda_t[3];  /* unnormalised lambda~ (gem, col, opa), negatives clamped to 0 */
+    double lambda[3];    /* Eq. 19 (gem, col, opa)                                        */
+    double mean_m[3];    /* scene means of the magnitudes m^gem, m^col, m^opa             */
+} refine_scene_stats;
+
+typedef struct refine_ctx refine_ctx;
+
+/* Library version string. */
+const char *refine_version(void);
+
+/* Fills *out with eta = 0.05, BT.601 luma (0.299, 0.587, 0.114), the
+ * default E[.] constants and flags = REFINE_FLAG_NORM_ATTR.  EINVAL if out
+ * is NULL. */
+refine_status refine_params_default(refine_params *out);
+
+/* Creates a context bound to CUDA device `device` (it becomes current on
+ * the calling thread).  *out receives the handle.  EINVAL for a bad device
+ * or NULL out; ECUDA if the device cannot be initialised. */
+refine_status refine_ctx_create(refine_ctx **out, int device);
+
+/* Frees the context's scratch memory and the context.  NULL is a no-op.
+ * Synchronises the context's device first. */
+void refine_ctx_destroy(refine_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none).  The string is
+ * owned by the context and valid until its next call. */
+const char *refine_last_error(const refine_ctx *ctx);
+
+/* Importance score D(G_i) of every primitive (Sec. 3.2: Eq. 7 with the
+ * Hessian weights of Eq. 20, lambda^k from Eq. 18-19, the projection term
+ * of Eq. 17 and, for each view, the visibility of the primitive's 3-sigma
+ * footprint under the EWA projected covariance J W Sigma W^T J^T, Eq. 13-14).
+ *   scene       primitives (see refine_scene), device memory
+ *   cams_dev    device array of n_views refine_camera records
+ *   params      host pointer; NULL means refine_params_default()
+ *   scores_dev  device float32 [scene->n], written
+ * Asynchronous on `stream`.  Input NaN/Inf and invalid cameras are
+ * reported through the device status word (ENONFINITE / EINVAL). */
+refine_status refine_score(refine_ctx *ctx, const refine_scene *scene,
+                           const refine_camera *cams_dev, int32_t n_views,
+                           const refine_params *params, float *scores_dev,
+                           refine_stream_t stream);
+
+/* refine_score plus diagnostics.
+ *   view_sum_dev  device float32 [n] or NULL: sum over views of
+ *                 vis * 1/(z^2+eta) (Eq. 20's bracket without alpha, 1/|V|)
+ *   stats_out     host pointer or NULL: scene statistics; when non-NULL the
+ *                 call synchronises `stream` to return them. */
+refine_status refine_score_ex(refine_ctx *ctx, const refine_scene *scene,
+                              const refine_camera *cams_dev, int32_t n_views,
+                              const refine_params *params, float *scores_dev,
+                              float *view_sum_dev, refine_scene_stats *stats_out,
+                              refine_stream_t stream);
+
+/* Ratio pruning by global rank (Sec. 3.3): the bottom floor(ratio * n)
+ * primitives are pruned, ranking by score and breaking ties by index
+ * (among equal scores the higher index is pruned first; -0 equals +0).
+ *   scores_dev     device float32 [n] (NaN rejected with ENONFINITE)
+ *   ratio          pruning ratio beta in [0, 1)
+ *   keep_mask_dev  device uint32 [ceil(n/32)], written: bit (i % 32) of word
+ *                  i / 32 is set when primitive i is kept; bits >= n are 0
+ *   threshold_out  host, or NULL: the smallest kept score (-inf when nothing
+ *                  is pruned).  Non-NULL makes the call synchronise.
+ *   n_keep_out     host, or NULL: n - floor(ratio * n) (known on the host,
+ *                  no synchronisation)
+ * Uses context scratch memory (radix-select histograms and state). */
+refine_status refine_select(refine_ctx *ctx, const float *scores_dev, int64_t n, double ratio,
+                            uint32_t *keep_mask_dev, float *threshold_out, int64_t *n_keep_out,
+                            refine_stream_t stream);
+
+/* Stable compaction of the kept primitives (Sec. 3.3, "saving primitives"):
+ * every one of the 59 rows of the kept primitives, in index order.
+ *   in             the scene (device)
+ *   keep_mask_dev  device uint32 [ceil(n/32)] as written by refine_select
+ *   out_pos_dev    device float32 [3][out_row_stride]
+ *   out_attr_dev   device [56][out_row_stride] in in->dtype
+ *   out_row_stride >= number of kept primitives
+ *   kept_idx_dev   device int32 [n_keep] original indices, or NULL
+ *   n_keep_out     host or NULL; non-NULL synchronises and returns the count
+ * The kept count must not exceed out_row_stride; the kernel writes nothing
+ * beyond it and reports EINVAL through the status word if it would. */
+refine_status refine_compact(refine_ctx *ctx, const refine_scene *in,
+                             const uint32_t *keep_mask_dev, float *out_pos_dev,
+                             void *out_attr_dev, int64_t out_row_stride,
+                             int32_t *kept_idx_dev, int64_t *n_keep_out,
+                             refine_stream_t stream);
+
+/* The whole pass from host memory: copies the scene (pos_host float32
+ * [3][n], attr_host [56][n] in `dtype`, both row-contiguous) and cameras to
+ * the device, scores, selects and compacts, and copies back the kept
+ * primitives (out_pos_host [3][n_keep], out_attr_host [56][n_keep]), their
+ * indices (out_idx_host int32 [n_keep], or NULL) and the scores
+ * (scores_host float32 [n], or NULL).  Device buffers are context scratch.
+ * Synchronises `stream` before returning; *n_keep_out and *threshold_out
+ * (either may be NULL) receive the kept count and threshold. */
+refine_status refine_prune_host(refine_ctx *ctx, int64_t n, int32_t dtype,
+                                const float *pos_host, const void *attr_host,
+                                const refine_camera *cams_host, int32_t n_views,
+                                const refine_params *params, double ratio,
+                                float *out_pos_host, void *out_attr_host,
+                                int32_t *out_idx_host, float *scores_host,
+                                int64_t *n_keep_out, float *threshold_out,
+                                refine_stream_t stream);
+
+/* Synchronises `stream` and returns (then clears) the device status word:
+ * REFINE_OK, or the first error a kernel recorded since the last check. */
+refine_status refine_ctx_check(refine_ctx *ctx, refine_stream_t stream);
+
+/* Instrumentation.  When timing is enabled every kernel launch is
+ * bracketed by CUDA events on its stream; refine_ctx_kernel_times
+ * synchronises, then reports the accumulated device milliseconds and launch
+ * counts per kernel class (names[i], ms[i], launches[i] for i < *count,
+ * at most `cap` entries) and resets them.  refine_ctx_launch_count returns
+ * the number of kernels the context has launched since creation. */
+refine_status refine_ctx_set_timing(refine_ctx *ctx, int enable);
+refine_status refine_ctx_kernel_times(refine_ctx *ctx, const char **names, double *ms,
+                                      int64_t *launches, int32_t cap, int32_t *count);
+int64_t refine_ctx_launch_count(const refine_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REFINE_H */
