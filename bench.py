@@ -1,0 +1,363 @@
+"""Benchmark of the REFINE importance / prune / compact pass on GB300.
+
+One step = refine_score + refine_select + refine_compact (every hot-path
+step) over one resident synthetic scene.  The default workload is the
+3.5M-primitive core-shell scene with 250 views at 1600x1063, plain FP32,
+prune ratio 0.5.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c2|c1|c0]
+
+Under torchrun each rank scores its own replica scene (weak scaling, no
+data-path collective); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic FP32 work per (primitive, view) pair of the score kernel, FMA
+# counted as 2 FLOPs (the operation table is in the design doc): camera transform
+# 18, J W rows 18, L g products 30, squared norms 10, footprint box test 14,
+# depth test 2, Eq. 17 weight 3 (one MUFU reciprocal), accumulation 1.
+FLOPS_PER_PAIR = 96
+FP32_LANES_PER_SM = 128
+METRIC = "Gaussian×view pairs/s"
+
+
+def workload(name: str, rank: int = 0):
+    from paper_2606_09074_gb300 import synth
+    if name == "c2":
+        w = synth.config2(seed=2 + 1000 * rank)
+        w.name = "core-shell N=3.5M V=250 1600x1063, FP32, ratio 0.5"
+    elif name == "c1":
+        w = synth.config1(seed=1 + 1000 * rank)
+        w.ratios = (0.5,)
+        w.name = "core-shell N=1M V=150 1297x840, FP32, ratio 0.5"
+    elif name == "c0":
+        w = synth.config0(seed=0 + 1000 * rank)
+        w.name = "normal N=10k V=16 640x480, FP32, ratio 0.5"
+    else:
+        raise ValueError(name)
+    return w
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2606_09074_gb300", "csrc")
+    for f in ("kernels_score.cu", "common.cuh"):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload_name: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel
+    source is unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+
+    def summary(self, t0, t1):
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for t, line in self.lines:
+            if not (t0 <= t <= t1 + 0.25):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "power_w_max": max(pw),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle
+
+def oracle_sample_run(w, m: int, threads: int):
+    """The FP64 oracle on the first m primitives of a seeded permutation of
+    the workload, all views: score -> select -> compact.  Returns seconds."""
+    import oracle
+    oracle.set_threads(threads)
+    perm = np.random.default_rng(12).permutation(w.scene.n)[:m]
+    sub = w.scene.subset(np.sort(perm))
+    g = sub.params_f64()
+    rows = np.concatenate([sub.pos, sub.attr], axis=0)
+    t = time.perf_counter()
+    o = oracle.score(g, w.cams, detail=False)
+    mask, thr, nk = oracle.select(o["scores"], w.ratios[0])
+    oracle.compact(rows, mask)
+    return time.perf_counter() - t
+
+
+def oracle_rate(w, budget_s: float, threads: int):
+    """Pairs/s of the oracle on a bounded sample sized to ~budget_s."""
+    m = min(2000, w.scene.n)
+    dt = oracle_sample_run(w, m, threads)
+    rate = m * len(w.cams) / max(dt, 1e-9)
+    m2 = int(min(w.scene.n, max(m, rate * budget_s / len(w.cams))))
+    if m2 > m:
+        dt = oracle_sample_run(w, m2, threads)
+        m = m2
+    return m * len(w.cams) / dt, m, dt
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    import oracle
+    w = workload(args.workload)
+    threads = os.cpu_count() or 1
+    steps = args.steps + args.warmup
+    budget = max(0.05, min(20.0, 90.0 / max(steps, 1)))
+    _, m, _ = oracle_rate(w, budget, threads)
+    for _ in range(args.warmup):
+        oracle_sample_run(w, m, threads)
+    times = [oracle_sample_run(w, m, threads) for _ in range(args.steps)]
+    tot = sum(times)
+    value = args.steps * m * len(w.cams) / tot
+    sample = (f"{m} of {w.scene.n} primitives (seeded permutation) x all {len(w.cams)} views, "
+              f"score+select+compact, FP64 oracle, OpenMP")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "n": w.scene.n, "views": len(w.cams),
+                                            "ratio": w.ratios[0], "sample_primitives": m},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args, rank: int, world: int):
+    import torch
+    from paper_2606_09074_gb300 import binding as rb
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    w = workload(args.workload, rank)
+    n, V, ratio = w.scene.n, len(w.cams), w.ratios[0]
+    pos = torch.from_numpy(w.scene.pos).to(dev)
+    attr = torch.from_numpy(w.scene.attr).to(dev)
+    cams = rb.cameras_to_device(w.cams, dev)
+    n_keep = n - math.floor(ratio * n)
+    scores = torch.empty(n, dtype=torch.float32, device=dev)
+    mask = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
+    out_pos = torch.empty((3, n_keep), dtype=torch.float32, device=dev)
+    out_attr = torch.empty((56, n_keep), dtype=torch.float32, device=dev)
+    kept = torch.empty(n_keep, dtype=torch.int32, device=dev)
+    ctx = rb.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.score(pos, attr, cams, scores=scores, stream=stream)
+        ctx.select(scores, ratio, mask=mask, threshold=False, stream=stream)
+        ctx.compact(pos, attr, mask, n_keep, out_pos=out_pos, out_attr=out_attr, kept_idx=True,
+                    out_row_stride=n_keep, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ctx.check()
+    ctx.kernel_times()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    ctx.set_timing(True)
+    launches0 = ctx.launch_count()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
+    evs[0].record(stream)
+    for k in range(args.steps):
+        step()
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    t_wall1 = time.time()
+    launches = ctx.launch_count() - launches0
+    ctx.set_timing(False)
+    ktimes = ctx.kernel_times()
+    clocks.stop()
+    ctx.check()
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    pairs = n * V
+    value = world * args.steps * pairs / (total_ms / 1000.0)
+
+    # roofline of the dominant kernel (score): live CUDA-event timing
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    clk_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * clk_max * 1e6 / 1e12
+    sc = ktimes.get("score", {"ms": float("nan"), "launches": 1})
+    score_ms = sc["ms"] / max(sc["launches"], 1)
+    achieved = pairs * FLOPS_PER_PAIR / (score_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": recorded_traffic("score", args.workload),
+                "kernel": "k_score", "kernel_ms": score_ms,
+                "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                              f"{clk_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+                "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in ktimes.items()}}
+    clock_summary = clocks.summary(t_wall0, t_wall1)
+
+    line = None
+    if rank == 0:
+        # end to end through the public API from pinned host memory
+        e2e = None
+        if not args.no_e2e:
+            pos_h = torch.from_numpy(w.scene.pos).pin_memory()
+            attr_h = torch.from_numpy(w.scene.attr).pin_memory()
+            outs = {"out_pos": torch.empty((3, n_keep), dtype=torch.float32, pin_memory=True),
+                    "out_attr": torch.empty((56, n_keep), dtype=torch.float32, pin_memory=True),
+                    "idx": torch.empty(n_keep, dtype=torch.int32, pin_memory=True)}
+            for _ in range(2):
+                ctx.prune_host(pos_h, attr_h, w.cams, ratio, out=outs, stream=stream)
+            k_e2e = max(3, min(args.steps, 60))
+            t0 = time.perf_counter()
+            for _ in range(k_e2e):
+                ctx.prune_host(pos_h, attr_h, w.cams, ratio, out=outs, stream=stream)
+            dt = (time.perf_counter() - t0) / k_e2e
+            e2e = {"value": pairs / dt, "unit": "pairs/s", "h2d_bytes_per_step": 12 * n + 224 * n + 80 * V,
+                   "d2h_bytes_per_step": (12 + 224 + 4) * n_keep + 4 + 4, "ms_per_step": dt * 1000,
+                   "steps": k_e2e, "api": "refine_prune_host (pinned host buffers)"}
+        cpu = None
+        if not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            rate, m, dt = oracle_rate(w, 12.0, threads)
+            import oracle
+            cpu = {"value": rate, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+                   "sample": f"{m} of {n} primitives (seeded permutation) x all {V} views, "
+                             f"score+select+compact, {dt:.1f} s"}
+        lat = sorted(per_step)
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "n": n, "views": V, "ratio": ratio, "storage": "f32",
+                           "l2": f"inputs larger than L2 ({(236 * n) / 1e6:.0f} MB scene), no flush",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "scenes_per_s": world * 1000.0 / ms_step,
+                "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clock_summary, "gpu": props.name}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return line
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(1)))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -87,6 +87,9 @@ def lib():
             L.orc_scene_stats.argtypes = [dp, i64, i64, C.POINTER(Params), C.POINTER(Stats)]
             L.orc_score.argtypes = [dp, i64, i64, C.POINTER(Camera), C.c_int, C.POINTER(Params),
                                     dp, dp, dp, C.POINTER(C.c_int32), dp, C.POINTER(Stats)]
+            L.orc_score_subset.argtypes = [dp, i64, i64, C.POINTER(C.c_int64), i64,
+                                           C.POINTER(Camera), C.c_int, C.POINTER(Params),
+                                           dp, dp, dp, C.POINTER(C.c_int32), dp, C.POINTER(Stats)]
             L.orc_select.argtypes = [dp, i64, C.c_double, C.POINTER(C.c_uint32), dp]
             L.orc_select.restype = i64
             L.orc_compact.argtypes = [C.c_void_p, i64, i64, C.c_int, C.c_int,
@@ -222,6 +225,25 @@ def score(g: np.ndarray, cams, p: Params | None = None, detail: bool = True) -> 
     if detail:
         out.update(S=S, S_sure=Ss, nborder=nb, bterms=bt)
     return out
+
+
+def score_subset(g: np.ndarray, idx: np.ndarray, cams, p: Params | None = None) -> dict:
+    """Like ``score`` for the primitives ``idx`` only; the scene statistics
+    (lambda, magnitude means) still come from every column of ``g``."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    m = idx.shape[0]
+    camarr = cams if isinstance(cams, C.Array) else cameras(cams)
+    o = {"scores": np.zeros(m), "S": np.zeros(m), "S_sure": np.zeros(m),
+         "nborder": np.zeros(m, dtype=np.int32), "bterms": np.zeros((m, 4))}
+    st = Stats()
+    lib().orc_score_subset(_dp(g), g.shape[1], g.shape[1], idx.ctypes.data_as(C.POINTER(C.c_int64)),
+                           m, camarr, len(cams), C.byref(p or params()), _dp(o["scores"]),
+                           _dp(o["S"]), _dp(o["S_sure"]),
+                           o["nborder"].ctypes.data_as(C.POINTER(C.c_int32)), _dp(o["bterms"]),
+                           C.byref(st))
+    o["stats"] = st.as_dict()
+    return o
 
 
 def select(scores: np.ndarray, beta: float):

@@ -30,7 +30,7 @@
  *
  * Parity band: besides each score, the oracle reports which (primitive, view)
  * visibility decisions lie so close to a boundary that a float32 evaluation
- * may legitimately take the other side (see orc_pair_is_borderline).
+ * may legitimately take the other side (see orc_visible).
  */
 #include <math.h>
 #include <stdint.h>
@@ -270,15 +270,30 @@ void orc_scene_stats(const double *g, int64_t stride, int64_t n, const orc_param
  *   nborder out [n]    number of borderline pairs (may be NULL)
  *   bterms  out [n][4] the first four borderline pairs' terms (may be NULL)
  *   st      out        scene statistics (may be NULL) */
+void orc_score_subset(const double *g, int64_t stride, int64_t n, const int64_t *idx, int64_t m_out,
+                      const orc_camera *cams, int V, const orc_params *p, double *scores, double *S,
+                      double *S_sure, int32_t *nborder, double *bterms, orc_stats *st_out);
+
 void orc_score(const double *g, int64_t stride, int64_t n, const orc_camera *cams, int V,
                const orc_params *p, double *scores, double *S, double *S_sure,
                int32_t *nborder, double *bterms, orc_stats *st_out)
 {
+    orc_score_subset(g, stride, n, NULL, n, cams, V, p, scores, S, S_sure, nborder, bterms, st_out);
+}
+
+/* As orc_score, but the outputs cover only the m_out primitives listed in
+ * idx (all n when idx is NULL); the scene statistics still come from all n
+ * primitives.  Output arrays are indexed 0 .. m_out-1. */
+void orc_score_subset(const double *g, int64_t stride, int64_t n, const int64_t *idx, int64_t m_out,
+                      const orc_camera *cams, int V, const orc_params *p, double *scores, double *S,
+                      double *S_sure, int32_t *nborder, double *bterms, orc_stats *st_out)
+{
     orc_stats st;
     orc_scene_stats(g, stride, n, p, &st);
     if (st_out) *st_out = st;
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t o = 0; o < m_out; ++o) {
+        int64_t i = idx ? idx[o] : o;
         double alpha, s[3], Rq[9], Sigma[9], m[3];
         double mu[3] = {g[i], g[stride + i], g[2 * stride + i]};
         orc_activate(g, stride, i, &alpha, s, Rq, Sigma);
@@ -292,15 +307,15 @@ void orc_score(const double *g, int64_t stride, int64_t n, const orc_camera *cam
             double P = (p->flags & ORC_NO_PROJ) ? 1.0 : 1.0 / (tc[2] * tc[2] + p->eta); /* Eq. 17 */
             if (vis) sum += P;
             if (border) {
-                if (bterms && nb < 4) bterms[4 * i + nb] = P;
+                if (bterms && nb < 4) bterms[4 * o + nb] = P;
                 ++nb;
             } else if (vis) {
                 sure += P;
             }
         }
-        if (S) S[i] = sum;
-        if (S_sure) S_sure[i] = sure;
-        if (nborder) nborder[i] = nb;
+        if (S) S[o] = sum;
+        if (S_sure) S_sure[o] = sure;
+        if (nborder) nborder[o] = nb;
         double vis_alpha = (p->flags & ORC_NO_VIS) ? 1.0 : alpha;          /* Eq. 12, T = 1 */
         double A = vis_alpha * sum / (double)V;                            /* Eq. 20 / lambda */
         orc_magnitudes(g, stride, i, m);
@@ -310,7 +325,7 @@ void orc_score(const double *g, int64_t stride, int64_t n, const orc_camera *cam
             if (p->flags & ORC_NORM_ATTR) Gt = st.mean_m[k] > 0.0 ? m[k] / st.mean_m[k] : 0.0;
             coupled += st.lambda[k] * Gt;
         }
-        scores[i] = A * coupled;
+        scores[o] = A * coupled;
     }
 }
 

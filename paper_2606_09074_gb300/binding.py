@@ -1,0 +1,315 @@
+"""Python binding of librefine, the GB300 (sm_103a) implementation of REFINE's
+rendering-free primitive importance, ratio pruning and compaction
+(arXiv 2606.09074, Sec. 3.2-3.3).
+
+The functions named ``refine_*`` mirror the C ABI in ``include/refine.h``
+one to one (ctypes, argument marshalling only).  ``Context`` wraps them for
+PyTorch tensors: PyTorch supplies device memory and streams; every step of
+the computation runs in librefine's CUDA kernels.  There is no CPU path: if
+the shared library is missing, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+from .synth import CAMERA_DTYPE
+
+LIB_PATH = _build.LIB
+
+REFINE_OK = 0
+REFINE_EINVAL = 1
+REFINE_ENOMEM = 2
+REFINE_ECUDA = 3
+REFINE_ENONFINITE = 4
+REFINE_ETIMEOUT = 5
+REFINE_EBUSY = 6
+REFINE_ECANCELLED = 7
+REFINE_ENOTFOUND = 8
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 5: "ETIMEOUT",
+                6: "EBUSY", 7: "ECANCELLED", 8: "ENOTFOUND"}
+
+REFINE_F32 = 0
+REFINE_BF16 = 1
+
+FLAG_NO_VIS = 1 << 0
+FLAG_NO_PROJ = 1 << 1
+FLAG_EQUAL_LAMBDA = 1 << 2
+FLAG_NORM_ATTR = 1 << 3
+
+
+class RefineError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class refine_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("znear", C.c_float), ("zfar", C.c_float)]
+
+
+class refine_scene(C.Structure):
+    _fields_ = [("n", C.c_int64), ("dtype", C.c_int32), ("reserved", C.c_int32),
+                ("pos", C.c_void_p), ("attr", C.c_void_p), ("row_stride", C.c_int64)]
+
+
+class refine_params(C.Structure):
+    _fields_ = [("eta", C.c_float), ("luma", C.c_float * 3), ("e_ln_gem", C.c_double),
+                ("e_col", C.c_double), ("e_opa", C.c_double), ("flags", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class refine_scene_stats(C.Structure):
+    _fields_ = [("F_col", C.c_double), ("F_opa", C.c_double), ("F_gem", C.c_double),
+                ("lambda_t", C.c_double * 3), ("lambda_", C.c_double * 3), ("mean_m", C.c_double * 3)]
+
+    def as_dict(self):
+        return {"F_col": self.F_col, "F_opa": self.F_opa, "F_gem": self.F_gem,
+                "lambda_t": list(self.lambda_t), "lambda": list(self.lambda_),
+                "mean_m": list(self.mean_m)}
+
+
+assert C.sizeof(refine_camera) == 80 and C.sizeof(refine_scene) == 40
+assert C.sizeof(refine_params) == 48
+
+_P = C.c_void_p
+_SIGNATURES = {
+    "refine_version": (C.c_char_p, []),
+    "refine_params_default": (C.c_int, [C.POINTER(refine_params)]),
+    "refine_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
+    "refine_ctx_destroy": (None, [_P]),
+    "refine_last_error": (C.c_char_p, [_P]),
+    "refine_score": (C.c_int, [_P, C.POINTER(refine_scene), _P, C.c_int32, C.POINTER(refine_params),
+                               _P, _P]),
+    "refine_score_ex": (C.c_int, [_P, C.POINTER(refine_scene), _P, C.c_int32,
+                                  C.POINTER(refine_params), _P, _P, C.POINTER(refine_scene_stats), _P]),
+    "refine_select": (C.c_int, [_P, _P, C.c_int64, C.c_double, _P, C.POINTER(C.c_float),
+                                C.POINTER(C.c_int64), _P]),
+    "refine_compact": (C.c_int, [_P, C.POINTER(refine_scene), _P, _P, _P, C.c_int64, _P,
+                                 C.POINTER(C.c_int64), _P]),
+    "refine_prune_host": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P, C.c_int32,
+                                    C.POINTER(refine_params), C.c_double, _P, _P, _P, _P,
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_float), _P]),
+    "refine_ctx_check": (C.c_int, [_P, _P]),
+    "refine_ctx_set_timing": (C.c_int, [_P, C.c_int]),
+    "refine_ctx_kernel_times": (C.c_int, [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_int64), C.c_int32, C.POINTER(C.c_int32)]),
+    "refine_ctx_launch_count": (C.c_int64, [_P]),
+}
+
+
+def _load():
+    import torch  # noqa: F401  -- loads the CUDA runtime that librefine shares with PyTorch
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"librefine is not built ({LIB_PATH} is missing). Build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` or "
+            "`python paper_2606_09074_gb300/build.py`. There is no CPU fallback.")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+globals().update({name: getattr(_lib, name) for name in _SIGNATURES})
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def default_params(**overrides) -> refine_params:
+    p = refine_params()
+    refine_params_default(C.byref(p))  # noqa: F821
+    for k, v in overrides.items():
+        if k == "luma":
+            p.luma[:] = list(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _check(ctx, st):
+    if st != REFINE_OK:
+        raise RefineError(st, refine_last_error(ctx).decode(errors="replace"))  # noqa: F821
+
+
+def _stream_handle(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return REFINE_F32
+    if t.dtype in (torch.bfloat16, torch.int16, torch.uint16):
+        return REFINE_BF16
+    raise TypeError(f"unsupported attribute dtype {t.dtype}")
+
+
+def make_scene(pos, attr) -> refine_scene:
+    """refine_scene view of device tensors pos [3, n] float32 and attr
+    [56, n] float32 / bfloat16 with a common row stride."""
+    n = pos.shape[1]
+    if pos.shape[0] != 3 or attr.shape[0] != 56 or attr.shape[1] != n:
+        raise ValueError("expected pos [3, n] and attr [56, n]")
+    if n and (pos.stride(1) != 1 or attr.stride(1) != 1 or pos.stride(0) != attr.stride(0)):
+        raise ValueError("pos and attr must be row-contiguous with the same row stride")
+    sc = refine_scene()
+    sc.n = n
+    sc.dtype = _dtype_code(attr)
+    sc.pos = pos.data_ptr()
+    sc.attr = attr.data_ptr()
+    sc.row_stride = pos.stride(0) if n else 0
+    return sc
+
+
+def cameras_to_device(cams, device):
+    """Uploads a ``synth.CAMERA_DTYPE`` array as raw refine_camera records."""
+    import torch
+    arr = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+    return torch.from_numpy(arr.view(np.uint8).copy()).to(device)
+
+
+class Context:
+    """A librefine context bound to one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.device = torch.device("cuda", device)
+        h = C.c_void_p()
+        st = refine_ctx_create(C.byref(h), device)  # noqa: F821
+        if st != REFINE_OK:
+            raise RefineError(st, f"refine_ctx_create(device={device}) failed")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            refine_ctx_destroy(self.handle)  # noqa: F821
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------------
+    def score(self, pos, attr, cams_dev, n_views=None, params=None, scores=None, view_sum=None,
+              stats=False, stream=None):
+        """Importance scores (float32 [n]).  ``cams_dev`` is a device uint8
+        tensor of refine_camera records.  With ``stats`` also returns the
+        scene statistics dict (synchronises)."""
+        import torch
+        sc = make_scene(pos, attr)
+        V = n_views if n_views is not None else cams_dev.numel() // 80
+        if scores is None:
+            scores = torch.empty(sc.n, dtype=torch.float32, device=self.device)
+        st_out = refine_scene_stats() if stats else None
+        rc = refine_score_ex(self.handle, C.byref(sc), C.c_void_p(cams_dev.data_ptr()), V,  # noqa: F821
+                             C.byref(params) if params is not None else None,
+                             C.c_void_p(scores.data_ptr()),
+                             C.c_void_p(view_sum.data_ptr()) if view_sum is not None else None,
+                             C.byref(st_out) if stats else None, _stream_handle(stream, self.device))
+        _check(self.handle, rc)
+        return (scores, st_out.as_dict()) if stats else scores
+
+    def select(self, scores, ratio, mask=None, threshold=True, stream=None):
+        """Returns (keep mask uint32 words as int32 tensor, threshold or None, n_keep)."""
+        import torch
+        n = scores.numel()
+        if mask is None:
+            mask = torch.empty(max((n + 31) // 32, 1), dtype=torch.int32, device=self.device)
+        thr = C.c_float()
+        nk = C.c_int64()
+        rc = refine_select(self.handle, C.c_void_p(scores.data_ptr()), n, float(ratio),  # noqa: F821
+                           C.c_void_p(mask.data_ptr()), C.byref(thr) if threshold else None,
+                           C.byref(nk), _stream_handle(stream, self.device))
+        _check(self.handle, rc)
+        return mask, (thr.value if threshold else None), nk.value
+
+    def compact(self, pos, attr, mask, n_keep, out_pos=None, out_attr=None, kept_idx=True,
+                out_row_stride=None, return_count=False, stream=None):
+        """Compacts the kept primitives; returns (out_pos, out_attr, kept_idx[, count])."""
+        import torch
+        sc = make_scene(pos, attr)
+        stride = out_row_stride if out_row_stride is not None else max(n_keep, 1)
+        if out_pos is None:
+            out_pos = torch.empty((3, stride), dtype=torch.float32, device=self.device)
+        if out_attr is None:
+            out_attr = torch.empty((56, stride), dtype=attr.dtype, device=self.device)
+        idx = torch.empty(max(n_keep, 1), dtype=torch.int32, device=self.device) if kept_idx else None
+        cnt = C.c_int64()
+        rc = refine_compact(self.handle, C.byref(sc), C.c_void_p(mask.data_ptr()),  # noqa: F821
+                            C.c_void_p(out_pos.data_ptr()), C.c_void_p(out_attr.data_ptr()), stride,
+                            C.c_void_p(idx.data_ptr()) if idx is not None else None,
+                            C.byref(cnt) if return_count else None, _stream_handle(stream, self.device))
+        _check(self.handle, rc)
+        out = (out_pos[:, :n_keep], out_attr[:, :n_keep], idx[:n_keep] if idx is not None else None)
+        return out + (cnt.value,) if return_count else out
+
+    def prune_host(self, pos_host, attr_host, cams, ratio, params=None, want_scores=False,
+                   out=None, stream=None):
+        """Whole pass from host tensors (ideally pinned).  Returns a dict with
+        out_pos, out_attr, idx, (scores), n_keep, threshold."""
+        import torch
+        n = pos_host.shape[1]
+        dt = _dtype_code(attr_host)
+        cams_arr = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+        n_keep = n - int(np.floor(float(ratio) * n))
+        if out is None:
+            pin = pos_host.is_pinned()
+            out = {"out_pos": torch.empty((3, max(n_keep, 1)), dtype=torch.float32, pin_memory=pin),
+                   "out_attr": torch.empty((56, max(n_keep, 1)), dtype=attr_host.dtype, pin_memory=pin),
+                   "idx": torch.empty(max(n_keep, 1), dtype=torch.int32, pin_memory=pin)}
+            if want_scores:
+                out["scores"] = torch.empty(max(n, 1), dtype=torch.float32, pin_memory=pin)
+        nk = C.c_int64()
+        thr = C.c_float()
+        rc = refine_prune_host(self.handle, n, dt, C.c_void_p(pos_host.data_ptr()),  # noqa: F821
+                               C.c_void_p(attr_host.data_ptr()),
+                               cams_arr.ctypes.data_as(C.c_void_p), len(cams_arr),
+                               C.byref(params) if params is not None else None, float(ratio),
+                               C.c_void_p(out["out_pos"].data_ptr()),
+                               C.c_void_p(out["out_attr"].data_ptr()),
+                               C.c_void_p(out["idx"].data_ptr()),
+                               C.c_void_p(out["scores"].data_ptr()) if "scores" in out else None,
+                               C.byref(nk), C.byref(thr), _stream_handle(stream, self.device))
+        _check(self.handle, rc)
+        res = {"out_pos": out["out_pos"][:, :nk.value], "out_attr": out["out_attr"][:, :nk.value],
+               "idx": out["idx"][:nk.value], "n_keep": nk.value, "threshold": thr.value}
+        if "scores" in out:
+            res["scores"] = out["scores"][:n]
+        return res
+
+    def check(self, stream=None):
+        _check(self.handle, refine_ctx_check(self.handle, _stream_handle(stream, self.device)))  # noqa: F821
+
+    def status(self, stream=None) -> int:
+        return refine_ctx_check(self.handle, _stream_handle(stream, self.device))  # noqa: F821
+
+    def set_timing(self, on: bool):
+        refine_ctx_set_timing(self.handle, 1 if on else 0)  # noqa: F821
+
+    def kernel_times(self) -> dict:
+        cap = 32
+        names = (C.c_char_p * cap)()
+        ms = (C.c_double * cap)()
+        ln = (C.c_int64 * cap)()
+        cnt = C.c_int32()
+        _check(self.handle, refine_ctx_kernel_times(self.handle, names, ms, ln, cap, C.byref(cnt)))  # noqa: F821
+        return {names[i].decode(): {"ms": ms[i], "launches": ln[i]} for i in range(cnt.value)}
+
+    def launch_count(self) -> int:
+        return int(refine_ctx_launch_count(self.handle))  # noqa: F821

@@ -1,0 +1,92 @@
+// Host-side declarations of the kernel launchers.  Each launch_* enqueues
+// exactly one kernel on `stream` and returns the launch error.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/refine.h"
+#include "common.cuh"
+
+namespace refine {
+
+// Cameras processed per score launch (64 bytes each in shared memory).  A
+// larger view set is split into passes of this size; pass boundaries fall
+// on multiples of 16 views so the summation order is independent of it.
+constexpr int kViewsPerPass = 1024;
+constexpr int kScoreThreads = 256;
+constexpr int kFeatThreads = 256;
+
+struct ScoreLaunch {
+    const float *pos;
+    const void *attr;
+    int dtype;
+    int64_t stride;
+    int64_t n;
+    const CamRec *cams;   // this pass's cameras (device, 16-byte aligned)
+    int vcount;           // cameras in this pass
+    int first, last;      // first / last pass of the view set
+    float eta;
+    float inv_views;      // 1 / |V|
+    int flags;
+    const SceneConsts *consts;
+    const float *m_col;
+    float *running;       // per-primitive running view sum between passes
+    float *scores;
+    float *view_sum;      // optional
+    int *status;
+    int grid;             // CTAs (persistent)
+    int gpt;              // primitives per thread (1 or 2)
+};
+
+cudaError_t launch_cam_prep(const refine_camera *cams, int V, CamRec *out, int *status,
+                            cudaStream_t s);
+int feature_blocks(int64_t n, int dtype);
+cudaError_t launch_features(const void *attr, int dtype, int64_t stride, int64_t n, float eta,
+                            const float luma[3], float *m_col, double *partials, bool vec,
+                            int *status, cudaStream_t s);
+cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_t n,
+                                     const refine_params *p, SceneConsts *consts,
+                                     SceneStats *stats, cudaStream_t s);
+cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s);
+int score_grid(int num_sms, int64_t n, int vcount, int gpt);
+
+// ------------------------------------------------------------- select
+struct SelState {
+    unsigned int hist[2048];
+    unsigned int done;
+    unsigned int prefix;
+    unsigned int remaining;
+    unsigned int count_gt;
+    unsigned int kstar;
+    unsigned int cnt_eq;
+    unsigned int need_ties;
+    unsigned int pad;
+    long long idx_cut;
+};
+constexpr int kTieSeg = 4096;
+int select_grid(int num_sms, int64_t n);
+cudaError_t launch_select_pass(int pass, const float *scores, int64_t n, uint32_t n_keep,
+                               SelState *st, bool vec, int grid, int *status, cudaStream_t s);
+cudaError_t launch_select_ties(const float *scores, int64_t n, SelState *st, unsigned *seg_cnt,
+                               int grid, cudaStream_t s);
+cudaError_t launch_select_mask(const float *scores, int64_t n, const SelState *st, uint32_t *mask,
+                               int grid, cudaStream_t s);
+cudaError_t launch_mask_fill(uint32_t *mask, int64_t n, cudaStream_t s);
+
+// ------------------------------------------------------------- compact
+struct CmpState {
+    unsigned int done;
+    unsigned int ok;
+    long long total;
+};
+constexpr int kCmpSeg = 2048;  // elements per compaction segment (64 mask words)
+cudaError_t launch_compact_count(const uint32_t *mask, int64_t n, unsigned *seg_cnt,
+                                 unsigned long long *seg_off, CmpState *cs, int64_t out_stride,
+                                 int grid, int *status, cudaStream_t s);
+cudaError_t launch_compact_scatter(const refine_scene &in, const uint32_t *mask,
+                                   const unsigned long long *seg_off, const CmpState *cs,
+                                   float *out_pos, void *out_attr, int64_t out_stride,
+                                   int32_t *out_idx, bool vec, int grid, cudaStream_t s);
+
+}  // namespace refine

@@ -1,0 +1,643 @@
+// C ABI of librefine: argument validation, context scratch, launches.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.h"
+
+using namespace refine;
+
+namespace {
+
+enum KClass {
+    K_CAM_PREP = 0,
+    K_FEATURES,
+    K_FEAT_FINAL,
+    K_SCORE,
+    K_SEL_PASS,
+    K_SEL_TIES,
+    K_SEL_MASK,
+    K_MASK_FILL,
+    K_CMP_COUNT,
+    K_CMP_SCATTER,
+    K_NCLASS
+};
+const char *const kClassName[K_NCLASS] = {"cam_prep",    "features",  "features_finalize",
+                                          "score",       "select_pass", "select_ties",
+                                          "select_mask", "mask_fill", "compact_count",
+                                          "compact_scatter"};
+
+struct Arena {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+// Bump allocator over an arena (256-byte aligned sub-blocks).
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *p) : base(static_cast<char *>(p)) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *r = reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return r;
+    }
+};
+
+size_t carve_size(std::initializer_list<size_t> parts)
+{
+    size_t off = 0;
+    for (size_t p : parts) off = ((off + 255) & ~size_t(255)) + p;
+    return off + 256;
+}
+
+}  // namespace
+
+struct refine_ctx {
+    int device = 0;
+    int num_sms = 0;
+    char err[512] = {0};
+    int *d_status = nullptr;
+    void *h_small = nullptr;  // pinned 4 KB for read-backs
+    Arena score, select, compact, host;
+    bool timing = false;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[K_NCLASS] = {0};
+    int64_t launches[K_NCLASS] = {0};
+    int64_t launch_count = 0;
+    int score_gpt = 2;
+};
+
+namespace {
+
+refine_status fail(refine_ctx *c, refine_status st, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+refine_status cuda_fail(refine_ctx *c, cudaError_t e, const char *what)
+{
+    cudaGetLastError();  // clear non-sticky errors
+    return fail(c, e == cudaErrorMemoryAllocation ? REFINE_ENOMEM : REFINE_ECUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+refine_status use_device(refine_ctx *c)
+{
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != c->device) {
+        cudaError_t e = cudaSetDevice(c->device);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    }
+    return REFINE_OK;
+}
+
+refine_status ensure(refine_ctx *c, Arena &a, size_t bytes)
+{
+    if (bytes <= a.cap) return REFINE_OK;
+    size_t want = bytes + bytes / 4;
+    want = (want + (size_t(2) << 20) - 1) & ~((size_t(2) << 20) - 1);
+    if (a.p) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaDeviceSynchronize (scratch growth)");
+        cudaFree(a.p);
+        a.p = nullptr;
+        a.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&a.p, want);
+    if (e != cudaSuccess) {
+        a.p = nullptr;
+        return cuda_fail(c, e, "cudaMalloc (scratch)");
+    }
+    a.cap = want;
+    return REFINE_OK;
+}
+
+cudaEvent_t take_event(refine_ctx *c)
+{
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Runs one kernel launcher, bracketed by events when timing is enabled.
+template <typename F>
+refine_status launch(refine_ctx *c, int cls, cudaStream_t s, F &&f)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->timing) {
+        a = take_event(c);
+        cudaEventRecord(a, s);
+    }
+    cudaError_t e = f();
+    if (e != cudaSuccess) return cuda_fail(c, e, kClassName[cls]);
+    if (c->timing) {
+        b = take_event(c);
+        cudaEventRecord(b, s);
+        c->pending.push_back({cls, a, b});
+    }
+    c->launch_count++;
+    c->launches[cls]++;
+    return REFINE_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+refine_status check_params(refine_ctx *c, const refine_params *p)
+{
+    if (!(p->eta > 0.f) || !isfinite(p->eta)) return fail(c, REFINE_EINVAL, "params: eta must be finite and > 0");
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(p->luma[k])) return fail(c, REFINE_EINVAL, "params: luma must be finite");
+    if (!(isfinite(p->e_ln_gem) && p->e_ln_gem != 0.0 && isfinite(p->e_col) && p->e_col != 0.0 &&
+          isfinite(p->e_opa) && p->e_opa != 0.0))
+        return fail(c, REFINE_EINVAL, "params: calibration constants must be finite and nonzero");
+    return REFINE_OK;
+}
+
+refine_status check_scene(refine_ctx *c, const refine_scene *s)
+{
+    if (!s) return fail(c, REFINE_EINVAL, "scene is NULL");
+    if (s->n < 0 || s->n > INT32_MAX) return fail(c, REFINE_EINVAL, "scene: n=%lld out of [0, 2^31-1]", (long long)s->n);
+    if (s->dtype != REFINE_F32 && s->dtype != REFINE_BF16) return fail(c, REFINE_EINVAL, "scene: unknown dtype %d", s->dtype);
+    if (s->n == 0) return REFINE_OK;
+    if (!s->pos || !s->attr) return fail(c, REFINE_EINVAL, "scene: NULL pos/attr");
+    if (s->row_stride < s->n) return fail(c, REFINE_EINVAL, "scene: row_stride < n");
+    if (!aligned16(s->pos) || !aligned16(s->attr)) return fail(c, REFINE_EINVAL, "scene: pos/attr must be 16-byte aligned");
+    return REFINE_OK;
+}
+
+// Rows may be read with 16-byte vector loads.
+bool scene_vec_ok(const refine_scene *s)
+{
+    const size_t es = s->dtype == REFINE_BF16 ? 2 : 4;
+    return aligned16(s->pos) && aligned16(s->attr) && ((size_t)s->row_stride * 4) % 16 == 0 &&
+           ((size_t)s->row_stride * es) % 16 == 0;
+}
+
+// Reads back and clears the device status word (synchronises `s`).
+refine_status read_status(refine_ctx *c, cudaStream_t s)
+{
+    int *h = static_cast<int *>(c->h_small);
+    cudaError_t e = cudaMemcpyAsync(h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read-back");
+    int st = h[0];
+    if (st != 0) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), s);
+        switch (st) {
+        case kEnonfinite: return fail(c, REFINE_ENONFINITE, "device: non-finite input value");
+        case kEtimeout: return fail(c, REFINE_ETIMEOUT, "device: a bounded wait ran out");
+        default: return fail(c, REFINE_EINVAL, "device: invalid input (camera, quaternion or output size)");
+        }
+    }
+    return REFINE_OK;
+}
+
+// ------------------------------------------------------------------ score
+refine_status score_impl(refine_ctx *c, const refine_scene *sc, const refine_camera *cams, int V,
+                         const refine_params *pin, float *scores, float *view_sum, SceneStats **stats_dev,
+                         cudaStream_t s)
+{
+    refine_params p;
+    if (pin) p = *pin; else refine_params_default(&p);
+    refine_status st = check_scene(c, sc);
+    if (st) return st;
+    if (V < 1 || V > 65535) return fail(c, REFINE_EINVAL, "n_views=%d out of [1, 65535]", V);
+    if (!cams) return fail(c, REFINE_EINVAL, "cams_dev is NULL");
+    if ((st = check_params(c, &p))) return st;
+    if (sc->n == 0) return REFINE_OK;
+    if (!scores) return fail(c, REFINE_EINVAL, "scores_dev is NULL");
+    const int64_t n = sc->n;
+    const bool multipass = V > kViewsPerPass;
+    const int nb = feature_blocks(n, sc->dtype);
+    size_t need = carve_size({sizeof(CamRec) * (size_t)V, sizeof(float) * (size_t)n,
+                              sizeof(double) * kFeatSums * 1024, sizeof(SceneConsts), sizeof(SceneStats),
+                              multipass ? sizeof(float) * (size_t)n : 0});
+    if ((st = ensure(c, c->score, need))) return st;
+    Carver cv(c->score.p);
+    CamRec *recs = cv.take<CamRec>(V);
+    float *m_col = cv.take<float>(n);
+    double *partials = cv.take<double>(kFeatSums * 1024);
+    SceneConsts *consts = cv.take<SceneConsts>(1);
+    SceneStats *stats = cv.take<SceneStats>(1);
+    float *running = multipass ? cv.take<float>(n) : nullptr;
+    if (stats_dev) *stats_dev = stats;
+
+    if ((st = launch(c, K_CAM_PREP, s, [&] { return launch_cam_prep(cams, V, recs, c->d_status, s); }))) return st;
+    const bool vec = scene_vec_ok(sc);
+    if ((st = launch(c, K_FEATURES, s, [&] {
+             return launch_features(sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, m_col, partials, vec,
+                                    c->d_status, s);
+         })))
+        return st;
+    if ((st = launch(c, K_FEAT_FINAL, s,
+                     [&] { return launch_features_finalize(partials, nb, n, &p, consts, stats, s); })))
+        return st;
+    for (int v0 = 0; v0 < V; v0 += kViewsPerPass) {
+        ScoreLaunch a;
+        a.pos = sc->pos;
+        a.attr = sc->attr;
+        a.dtype = sc->dtype;
+        a.stride = sc->row_stride;
+        a.n = n;
+        a.cams = recs + v0;
+        a.vcount = V - v0 < kViewsPerPass ? V - v0 : kViewsPerPass;
+        a.first = v0 == 0;
+        a.last = v0 + a.vcount >= V;
+        a.eta = p.eta;
+        a.inv_views = 1.0f / (float)V;
+        a.flags = p.flags;
+        a.consts = consts;
+        a.m_col = m_col;
+        a.running = running;
+        a.scores = scores;
+        a.view_sum = view_sum;
+        a.status = c->d_status;
+        a.gpt = c->score_gpt;
+        a.grid = score_grid(c->num_sms, n, a.vcount, a.gpt);
+        if ((st = launch(c, K_SCORE, s, [&] { return launch_score(a, s); }))) return st;
+    }
+    return REFINE_OK;
+}
+
+// ----------------------------------------------------------------- select
+refine_status select_impl(refine_ctx *c, const float *scores, int64_t n, double ratio, uint32_t *mask,
+                          unsigned int **kstar_dev, int64_t *n_keep, cudaStream_t s)
+{
+    if (n < 0 || n > INT32_MAX) return fail(c, REFINE_EINVAL, "select: n=%lld out of range", (long long)n);
+    if (!(ratio >= 0.0 && ratio < 1.0)) return fail(c, REFINE_EINVAL, "select: ratio must lie in [0, 1)");
+    const int64_t n_prune = (int64_t)floor(ratio * (double)n);
+    *n_keep = n - n_prune;
+    *kstar_dev = nullptr;
+    if (n == 0) return REFINE_OK;
+    if (!scores || !mask) return fail(c, REFINE_EINVAL, "select: NULL scores or mask");
+    refine_status st;
+    if (n_prune == 0)
+        return launch(c, K_MASK_FILL, s, [&] { return launch_mask_fill(mask, n, s); });
+    const int64_t nseg = (n + kTieSeg - 1) / kTieSeg;
+    if ((st = ensure(c, c->select, carve_size({sizeof(SelState), sizeof(unsigned) * (size_t)nseg})))) return st;
+    Carver cv(c->select.p);
+    SelState *ss = cv.take<SelState>(1);
+    unsigned *seg = cv.take<unsigned>(nseg);
+    cudaError_t e = cudaMemsetAsync(ss, 0, sizeof(SelState), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+    const bool vec = aligned16(scores);
+    const int grid = select_grid(c->num_sms, n);
+    for (int pass = 0; pass < 3; ++pass)
+        if ((st = launch(c, K_SEL_PASS, s, [&] {
+                 return launch_select_pass(pass, scores, n, (uint32_t)*n_keep, ss, vec, grid, c->d_status, s);
+             })))
+            return st;
+    if ((st = launch(c, K_SEL_TIES, s, [&] { return launch_select_ties(scores, n, ss, seg, grid, s); }))) return st;
+    if ((st = launch(c, K_SEL_MASK, s, [&] { return launch_select_mask(scores, n, ss, mask, grid, s); }))) return st;
+    *kstar_dev = &ss->kstar;
+    return REFINE_OK;
+}
+
+refine_status read_threshold(refine_ctx *c, unsigned int *kstar_dev, float *thr, cudaStream_t s)
+{
+    if (!kstar_dev) {
+        *thr = -INFINITY;
+        return read_status(c, s);
+    }
+    unsigned int *h = reinterpret_cast<unsigned int *>(static_cast<char *>(c->h_small) + 64);
+    cudaError_t e = cudaMemcpyAsync(h, kstar_dev, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "threshold read-back");
+    refine_status st = read_status(c, s);  // synchronises
+    if (st) return st;
+    *thr = key_to_score(*h);
+    return REFINE_OK;
+}
+
+// ---------------------------------------------------------------- compact
+refine_status compact_impl(refine_ctx *c, const refine_scene *in, const uint32_t *mask, float *out_pos,
+                           void *out_attr, int64_t out_stride, int32_t *idx, long long **total_dev,
+                           cudaStream_t s)
+{
+    refine_status st = check_scene(c, in);
+    if (st) return st;
+    *total_dev = nullptr;
+    if (in->n == 0) return REFINE_OK;
+    if (!mask || !out_pos || !out_attr) return fail(c, REFINE_EINVAL, "compact: NULL mask or output");
+    if (out_stride < 0) return fail(c, REFINE_EINVAL, "compact: negative out_row_stride");
+    const int64_t n = in->n;
+    const int64_t nseg = (n + kCmpSeg - 1) / kCmpSeg;
+    if ((st = ensure(c, c->compact,
+                     carve_size({sizeof(CmpState), sizeof(unsigned) * (size_t)nseg,
+                                 sizeof(unsigned long long) * (size_t)nseg}))))
+        return st;
+    Carver cv(c->compact.p);
+    CmpState *cs = cv.take<CmpState>(1);
+    unsigned *seg_cnt = cv.take<unsigned>(nseg);
+    unsigned long long *seg_off = cv.take<unsigned long long>(nseg);
+    cudaError_t e = cudaMemsetAsync(cs, 0, sizeof(CmpState), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+    int64_t cgrid = (nseg + 7) / 8;
+    if (cgrid > 2 * c->num_sms) cgrid = 2 * c->num_sms;
+    if (cgrid < 1) cgrid = 1;
+    if ((st = launch(c, K_CMP_COUNT, s, [&] {
+             return launch_compact_count(mask, n, seg_cnt, seg_off, cs, out_stride, (int)cgrid, c->d_status, s);
+         })))
+        return st;
+    int64_t sgrid = nseg < (int64_t)c->num_sms * 8 ? nseg : (int64_t)c->num_sms * 8;
+    const bool vec = scene_vec_ok(in);
+    if ((st = launch(c, K_CMP_SCATTER, s, [&] {
+             return launch_compact_scatter(*in, mask, seg_off, cs, out_pos, out_attr, out_stride, idx, vec,
+                                           (int)sgrid, s);
+         })))
+        return st;
+    *total_dev = &cs->total;
+    return REFINE_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char *refine_version(void) { return "librefine 0.1 (sm_103a)"; }
+
+refine_status refine_params_default(refine_params *out)
+{
+    if (!out) return REFINE_EINVAL;
+    memset(out, 0, sizeof *out);
+    out->eta = (float)REFINE_DEFAULT_ETA;
+    out->luma[0] = 0.299f;
+    out->luma[1] = 0.587f;
+    out->luma[2] = 0.114f;
+    out->e_ln_gem = REFINE_DEFAULT_E_LN_GEM;
+    out->e_col = REFINE_DEFAULT_E_COL;
+    out->e_opa = REFINE_DEFAULT_E_OPA;
+    out->flags = REFINE_FLAG_NORM_ATTR;
+    return REFINE_OK;
+}
+
+refine_status refine_ctx_create(refine_ctx **out, int device)
+{
+    if (!out) return REFINE_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return REFINE_ECUDA;
+    }
+    if (device < 0 || device >= count) return REFINE_EINVAL;
+    refine_ctx *c = new refine_ctx();
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&c->d_status, 256) != cudaSuccess || cudaMemset(c->d_status, 0, 256) != cudaSuccess ||
+        cudaMallocHost(&c->h_small, 4096) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->d_status) cudaFree(c->d_status);
+        delete c;
+        return REFINE_ECUDA;
+    }
+    if (const char *g = getenv("REFINE_SCORE_GPT")) {
+        int v = atoi(g);
+        if (v == 1 || v == 2) c->score_gpt = v;
+    }
+    *out = c;
+    return REFINE_OK;
+}
+
+void refine_ctx_destroy(refine_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (Arena *a : {&c->score, &c->select, &c->compact, &c->host})
+        if (a->p) cudaFree(a->p);
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->h_small) cudaFreeHost(c->h_small);
+    delete c;
+}
+
+const char *refine_last_error(const refine_ctx *c) { return c ? c->err : "NULL context"; }
+
+refine_status refine_score(refine_ctx *c, const refine_scene *scene, const refine_camera *cams_dev,
+                           int32_t n_views, const refine_params *params, float *scores_dev,
+                           refine_stream_t stream)
+{
+    return refine_score_ex(c, scene, cams_dev, n_views, params, scores_dev, nullptr, nullptr, stream);
+}
+
+refine_status refine_score_ex(refine_ctx *c, const refine_scene *scene, const refine_camera *cams_dev,
+                              int32_t n_views, const refine_params *params, float *scores_dev,
+                              float *view_sum_dev, refine_scene_stats *stats_out, refine_stream_t stream)
+{
+    if (!c) return REFINE_EINVAL;
+    refine_status st = use_device(c);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    SceneStats *sd = nullptr;
+    if ((st = score_impl(c, scene, cams_dev, n_views, params, scores_dev, view_sum_dev, &sd, s))) return st;
+    if (stats_out) {
+        if (scene->n == 0) {
+            memset(stats_out, 0, sizeof *stats_out);
+            for (int k = 0; k < 3; ++k) stats_out->lambda[k] = 1.0 / 3.0;
+            return REFINE_OK;
+        }
+        SceneStats *h = reinterpret_cast<SceneStats *>(static_cast<char *>(c->h_small) + 256);
+        cudaError_t e = cudaMemcpyAsync(h, sd, sizeof(SceneStats), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stats read-back");
+        if ((st = read_status(c, s))) return st;
+        static_assert(sizeof(SceneStats) == sizeof(refine_scene_stats), "stats layout");
+        memcpy(stats_out, h, sizeof *stats_out);
+    }
+    return REFINE_OK;
+}
+
+refine_status refine_select(refine_ctx *c, const float *scores_dev, int64_t n, double ratio,
+                            uint32_t *keep_mask_dev, float *threshold_out, int64_t *n_keep_out,
+                            refine_stream_t stream)
+{
+    if (!c) return REFINE_EINVAL;
+    refine_status st = use_device(c);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned int *kd = nullptr;
+    int64_t nk = 0;
+    if ((st = select_impl(c, scores_dev, n, ratio, keep_mask_dev, &kd, &nk, s))) return st;
+    if (n_keep_out) *n_keep_out = nk;
+    if (threshold_out) return read_threshold(c, kd, threshold_out, s);
+    return REFINE_OK;
+}
+
+refine_status refine_compact(refine_ctx *c, const refine_scene *in, const uint32_t *keep_mask_dev,
+                             float *out_pos_dev, void *out_attr_dev, int64_t out_row_stride,
+                             int32_t *kept_idx_dev, int64_t *n_keep_out, refine_stream_t stream)
+{
+    if (!c) return REFINE_EINVAL;
+    refine_status st = use_device(c);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    long long *td = nullptr;
+    if ((st = compact_impl(c, in, keep_mask_dev, out_pos_dev, out_attr_dev, out_row_stride, kept_idx_dev, &td,
+                           s)))
+        return st;
+    if (n_keep_out) {
+        if (!td) {
+            *n_keep_out = 0;
+            return REFINE_OK;
+        }
+        long long *h = reinterpret_cast<long long *>(static_cast<char *>(c->h_small) + 128);
+        cudaError_t e = cudaMemcpyAsync(h, td, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "count read-back");
+        if ((st = read_status(c, s))) return st;
+        *n_keep_out = *h;
+    }
+    return REFINE_OK;
+}
+
+refine_status refine_prune_host(refine_ctx *c, int64_t n, int32_t dtype, const float *pos_host,
+                                const void *attr_host, const refine_camera *cams_host, int32_t n_views,
+                                const refine_params *params, double ratio, float *out_pos_host,
+                                void *out_attr_host, int32_t *out_idx_host, float *scores_host,
+                                int64_t *n_keep_out, float *threshold_out, refine_stream_t stream)
+{
+    if (!c) return REFINE_EINVAL;
+    refine_status st = use_device(c);
+    if (st) return st;
+    if (n < 0 || n > INT32_MAX) return fail(c, REFINE_EINVAL, "prune_host: n out of range");
+    if (dtype != REFINE_F32 && dtype != REFINE_BF16) return fail(c, REFINE_EINVAL, "prune_host: bad dtype");
+    if (n_views < 1 || n_views > 65535 || !cams_host) return fail(c, REFINE_EINVAL, "prune_host: bad cameras");
+    if (!(ratio >= 0.0 && ratio < 1.0)) return fail(c, REFINE_EINVAL, "prune_host: ratio must lie in [0, 1)");
+    if (n > 0 && (!pos_host || !attr_host || !out_pos_host || !out_attr_host))
+        return fail(c, REFINE_EINVAL, "prune_host: NULL host buffer");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t es = dtype == REFINE_BF16 ? 2 : 4;
+    const int64_t n_keep = n - (int64_t)floor(ratio * (double)n);
+    const int64_t words = (n + 31) / 32;
+    const int64_t nk_alloc = n_keep > 0 ? n_keep : 1;
+    if ((st = ensure(c, c->host,
+                     carve_size({12 * (size_t)n, 56 * es * (size_t)n, sizeof(refine_camera) * (size_t)n_views,
+                                 4 * (size_t)n, 4 * (size_t)words, 12 * (size_t)nk_alloc,
+                                 56 * es * (size_t)nk_alloc, 4 * (size_t)nk_alloc}))))
+        return st;
+    Carver cv(c->host.p);
+    float *d_pos = cv.take<float>(3 * (size_t)n);
+    char *d_attr = cv.take<char>(56 * es * (size_t)n);
+    refine_camera *d_cams = cv.take<refine_camera>(n_views);
+    float *d_scores = cv.take<float>(n);
+    uint32_t *d_mask = cv.take<uint32_t>(words);
+    float *d_opos = cv.take<float>(3 * (size_t)nk_alloc);
+    char *d_oattr = cv.take<char>(56 * es * (size_t)nk_alloc);
+    int32_t *d_idx = cv.take<int32_t>(nk_alloc);
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaMemcpyAsync(d_pos, pos_host, 12 * (size_t)n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_attr, attr_host, 56 * es * (size_t)n, cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_cams, cams_host, sizeof(refine_camera) * (size_t)n_views, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "prune_host: host-to-device copy");
+    refine_scene sc;
+    sc.n = n;
+    sc.dtype = dtype;
+    sc.reserved = 0;
+    sc.pos = d_pos;
+    sc.attr = d_attr;
+    sc.row_stride = n;
+    if ((st = score_impl(c, &sc, d_cams, n_views, params, d_scores, nullptr, nullptr, s))) return st;
+    unsigned int *kd = nullptr;
+    int64_t nk = 0;
+    if ((st = select_impl(c, d_scores, n, ratio, d_mask, &kd, &nk, s))) return st;
+    long long *td = nullptr;
+    if ((st = compact_impl(c, &sc, d_mask, d_opos, d_oattr, nk, d_idx, &td, s))) return st;
+    if (n_keep > 0) {
+        e = cudaMemcpyAsync(out_pos_host, d_opos, 12 * (size_t)n_keep, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_attr_host, d_oattr, 56 * es * (size_t)n_keep, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && out_idx_host)
+            e = cudaMemcpyAsync(out_idx_host, d_idx, 4 * (size_t)n_keep, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess && scores_host && n > 0)
+        e = cudaMemcpyAsync(scores_host, d_scores, 4 * (size_t)n, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "prune_host: device-to-host copy");
+    float thr = -INFINITY;
+    if ((st = read_threshold(c, kd, &thr, s))) return st;  // synchronises
+    if (n_keep_out) *n_keep_out = n_keep;
+    if (threshold_out) *threshold_out = thr;
+    return REFINE_OK;
+}
+
+refine_status refine_ctx_check(refine_ctx *c, refine_stream_t stream)
+{
+    if (!c) return REFINE_EINVAL;
+    refine_status st = use_device(c);
+    if (st) return st;
+    return read_status(c, reinterpret_cast<cudaStream_t>(stream));
+}
+
+refine_status refine_ctx_set_timing(refine_ctx *c, int enable)
+{
+    if (!c) return REFINE_EINVAL;
+    c->timing = enable != 0;
+    return REFINE_OK;
+}
+
+refine_status refine_ctx_kernel_times(refine_ctx *c, const char **names, double *ms, int64_t *launches,
+                                      int32_t cap, int32_t *count)
+{
+    if (!c || !count) return REFINE_EINVAL;
+    refine_status st = use_device(c);
+    if (st) return st;
+    double acc[K_NCLASS] = {0};
+    int64_t cnt[K_NCLASS] = {0};
+    for (auto &p : c->pending) {
+        float t = 0.f;
+        cudaEventSynchronize(p.b);
+        if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) acc[p.cls] += t;
+        cnt[p.cls]++;
+        c->pool.push_back(p.a);
+        c->pool.push_back(p.b);
+    }
+    c->pending.clear();
+    int32_t k = 0;
+    for (int i = 0; i < K_NCLASS; ++i) {
+        if (!cnt[i]) continue;
+        if (k < cap) {
+            if (names) names[k] = kClassName[i];
+            if (ms) ms[k] = acc[i];
+            if (launches) launches[k] = cnt[i];
+        }
+        ++k;
+    }
+    *count = k < cap ? k : cap;
+    cudaGetLastError();
+    return REFINE_OK;
+}
+
+int64_t refine_ctx_launch_count(const refine_ctx *c) { return c ? c->launch_count : -1; }
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+"""The C ABI library builds, loads without a GPU and exports every entry
+point that include/refine.h declares; the binding's ctypes layouts match
+the header's struct layouts (checked with a C compiler).  CPU only."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "refine.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(refine_[a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_09074_gb300 import build
+    return ctypes.CDLL(build.build_library())
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 12, names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    from paper_2606_09074_gb300 import binding
+    assert set(declared_functions()) <= set(binding._SIGNATURES)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    from paper_2606_09074_gb300 import binding as b
+    prog = tmp_path / "layout.c"
+    prog.write_text('''
+#include <stdio.h>
+#include <stddef.h>
+#include "refine.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(refine_camera), sizeof(refine_scene), sizeof(refine_params), sizeof(refine_scene_stats));
+  printf("%zu %zu %zu %zu\\n", offsetof(refine_camera, width), offsetof(refine_camera, zfar), offsetof(refine_scene, pos), offsetof(refine_scene, row_stride));
+  printf("%zu %zu %zu\\n", offsetof(refine_params, e_ln_gem), offsetof(refine_params, flags), offsetof(refine_scene_stats, mean_m));
+  return 0; }
+''')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    got = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().split("\n") if l]
+    C = ctypes
+    assert got[0] == [C.sizeof(b.refine_camera), C.sizeof(b.refine_scene), C.sizeof(b.refine_params),
+                      C.sizeof(b.refine_scene_stats)]
+    assert got[1] == [b.refine_camera.width.offset, b.refine_camera.zfar.offset, b.refine_scene.pos.offset,
+                      b.refine_scene.row_stride.offset]
+    assert got[2] == [b.refine_params.e_ln_gem.offset, b.refine_params.flags.offset,
+                      b.refine_scene_stats.mean_m.offset]
+
+
+def test_camera_dtype_matches_struct():
+    import numpy as np
+    from paper_2606_09074_gb300 import binding as b, synth
+    assert synth.CAMERA_DTYPE.itemsize == ctypes.sizeof(b.refine_camera)
+    assert synth.CAMERA_DTYPE.fields["width"][1] == b.refine_camera.width.offset
+    assert synth.CAMERA_DTYPE.fields["zfar"][1] == b.refine_camera.zfar.offset
+
+
+def test_params_default_and_errors_without_gpu(lib):
+    from paper_2606_09074_gb300 import binding as b
+    p = b.default_params()
+    assert abs(p.eta - 0.05) < 1e-8 and p.flags == b.FLAG_NORM_ATTR
+    assert b.refine_params_default(None) == b.REFINE_EINVAL
+    # no context: every call must refuse cleanly rather than crash
+    assert b.refine_score(None, None, None, 1, None, None, None) == b.REFINE_EINVAL
+    assert b.refine_select(None, None, 0, 0.5, None, None, None, None) == b.REFINE_EINVAL
+    assert b.refine_ctx_launch_count(None) == -1

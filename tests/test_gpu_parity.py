@@ -1,0 +1,319 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: float32 scores within 1e-5 relative of the oracle for every
+primitive whose visibility decisions are all outside the oracle's float32
+band; primitives with a borderline pair must equal the oracle's sum with
+some choice of those pairs.  Selection and compaction on identical scores
+are bit-exact.  Masks from the oracle's own scores agree except for
+primitives within 1e-5 of the threshold or with a borderline pair."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_09074_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def rb(torch):
+    from paper_2606_09074_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(rb):
+    c = rb.Context(0)
+    yield c
+    c.close()
+
+
+def upload(torch, rb, scene, cams):
+    dev = torch.device("cuda", 0)
+    pos = torch.from_numpy(np.ascontiguousarray(scene.pos)).to(dev)
+    if scene.dtype == "bf16":
+        attr = torch.from_numpy(np.ascontiguousarray(scene.attr).view(np.int16)).to(dev).view(torch.bfloat16)
+    else:
+        attr = torch.from_numpy(np.ascontiguousarray(scene.attr)).to(dev)
+    return pos, attr, rb.cameras_to_device(cams, dev)
+
+
+def gpu_score(torch, rb, ctx, scene, cams, params=None):
+    pos, attr, cd = upload(torch, rb, scene, cams)
+    vs = torch.empty(max(scene.n, 1), dtype=torch.float32, device=pos.device)
+    sc, st = ctx.score(pos, attr, cd, params=params, view_sum=vs, stats=True)
+    ctx.check()
+    return sc.cpu().numpy(), vs[: scene.n].cpu().numpy(), st, (pos, attr)
+
+
+def oracle_params_from(p, rb):
+    if p is None:
+        return oracle.params()
+    return oracle.params(eta=float(np.float32(p.eta)), e_ln_gem=p.e_ln_gem, e_col=p.e_col, e_opa=p.e_opa,
+                         luma=[float(np.float32(x)) for x in p.luma], flags=p.flags)
+
+
+def assert_score_parity(s_gpu, S_gpu, ref, rtol=RTOL):
+    clean = ref["nborder"] == 0
+    for name, got, want in (("S", S_gpu, ref["S"]), ("score", s_gpu, ref["scores"])):
+        g = got.astype(np.float64)
+        zero = clean & (want == 0)
+        assert np.all(g[zero] == 0), f"{name}: nonzero where oracle is exactly 0"
+        nz = clean & (want != 0)
+        rel = np.abs(g[nz] - want[nz]) / np.abs(want[nz])
+        if rel.size:
+            worst = int(np.argmax(rel))
+            assert rel.max() <= rtol, (f"{name}: max rel err {rel.max():.3e} at {np.nonzero(nz)[0][worst]}",
+                                       g[nz][worst], want[nz][worst])
+    ok = oracle.valid_alternative(S_gpu.astype(np.float64), ref, rtol)
+    assert ok.all(), f"borderline primitives with no valid alternative: {np.nonzero(~ok)[0][:10]}"
+    return clean
+
+
+def unpack(mask_words, n):
+    return np.unpackbits(np.asarray(mask_words, dtype=np.uint32).view(np.uint8), bitorder="little")[:n].astype(bool)
+
+
+def check_select_exact(torch, ctx, s_gpu, ratio):
+    t = torch.from_numpy(s_gpu.astype(np.float32)).cuda()
+    mask, thr, nk = ctx.select(t, ratio)
+    m_ref, thr_ref, nk_ref = oracle.select(s_gpu.astype(np.float64), ratio)
+    n = s_gpu.shape[0]
+    assert nk == nk_ref == n - math.floor(ratio * n)
+    got = mask.cpu().numpy().view(np.uint32)[: (n + 31) // 32]
+    assert np.array_equal(got, m_ref), "keep mask differs from the oracle on identical scores"
+    if math.isinf(thr_ref):
+        assert math.isinf(thr) and thr < 0
+    else:
+        assert thr == np.float32(thr_ref)
+    return mask, got, nk
+
+
+def check_mask_vs_oracle_scores(got_mask, ref, ratio, n):
+    m_ref, thr_ref, nk_ref = oracle.select(ref["scores"], ratio)
+    a, b = unpack(got_mask, n), unpack(m_ref, n)
+    diff = np.nonzero(a != b)[0]
+    band = (np.abs(ref["scores"] - thr_ref) <= RTOL * abs(thr_ref)) | (ref["nborder"] > 0)
+    assert np.all(band[diff]), f"mask differs outside the threshold band at {diff[~band[diff]][:10]}"
+    return 1.0 - diff.size / max(n, 1)
+
+
+def check_compact_exact(torch, ctx, scene, pos, attr, mask, nk):
+    op, oa, idx, cnt = ctx.compact(pos, attr, mask, nk, return_count=True)
+    assert cnt == nk
+    m = mask.cpu().numpy().view(np.uint32)[: (scene.n + 31) // 32]
+    kp, ki = oracle.compact(np.ascontiguousarray(scene.pos), m)
+    ka, _ = oracle.compact(np.ascontiguousarray(scene.attr), m)
+    assert np.array_equal(idx.cpu().numpy(), ki)
+    assert np.array_equal(op.cpu().numpy(), kp)
+    got_attr = oa.cpu()
+    got_attr = got_attr.view(torch.int16).numpy().view(np.uint16) if scene.dtype == "bf16" else got_attr.numpy()
+    assert np.array_equal(got_attr, ka)
+
+
+# ----------------------------------------------------------------- tests
+
+def test_small_scene_full_parity(torch, rb, ctx):
+    """N=10k, V=16 ring at 640x480: every score, the scene statistics, the
+    selection and the compaction."""
+    w = synth.config0()
+    s, S, st, (pos, attr) = gpu_score(torch, rb, ctx, w.scene, w.cams)
+    ref = oracle.score(w.scene.params_f64(), w.cams)
+    clean = assert_score_parity(s, S, ref)
+    assert clean.mean() > 0.99
+    for k in ("F_col", "F_opa", "F_gem"):
+        assert st[k] == pytest.approx(ref["stats"][k], rel=1e-6)
+    np.testing.assert_allclose(st["lambda"], ref["stats"]["lambda"], rtol=1e-6)
+    np.testing.assert_allclose(st["mean_m"], ref["stats"]["mean_m"], rtol=1e-6)
+    mask, words, nk = check_select_exact(torch, ctx, s, 0.5)
+    agree = check_mask_vs_oracle_scores(words, ref, 0.5, w.scene.n)
+    assert agree > 0.999
+    check_compact_exact(torch, ctx, w.scene, pos, attr, mask, nk)
+
+
+@pytest.mark.parametrize("n,v", [(1, 1), (2, 3), (31, 16), (33, 17), (257, 5), (1023, 33), (4097, 2), (6001, 48)])
+def test_ragged_sizes(torch, rb, ctx, n, v):
+    w = synth.random_scene(seed=n * 31 + v, n=n, v=v)
+    s, S, _, (pos, attr) = gpu_score(torch, rb, ctx, w.scene, w.cams)
+    ref = oracle.score(w.scene.params_f64(), w.cams)
+    assert_score_parity(s, S, ref)
+    for ratio in (0.0, 0.3, 0.5, 0.9):
+        mask, _, nk = check_select_exact(torch, ctx, s, ratio)
+        check_compact_exact(torch, ctx, w.scene, pos, attr, mask, nk)
+
+
+def test_bf16_storage_parity(torch, rb, ctx):
+    """BF16 rows 3-58: the oracle sees the same bf16-rounded numbers."""
+    w = synth.config0(seed=4)
+    sc = w.scene.to_bf16()
+    s, S, _, (pos, attr) = gpu_score(torch, rb, ctx, sc, w.cams)
+    ref = oracle.score(sc.params_f64(), w.cams)
+    assert_score_parity(s, S, ref)
+    mask, _, nk = check_select_exact(torch, ctx, s, 0.66)
+    check_compact_exact(torch, ctx, sc, pos, attr, mask, nk)
+
+
+def test_many_views_multipass(torch, rb, ctx):
+    """More views than one launch stages (1024): the view set is split."""
+    w = synth.random_scene(seed=8, n=700, v=1100)
+    s, S, _, _ = gpu_score(torch, rb, ctx, w.scene, w.cams)
+    ref = oracle.score(w.scene.params_f64(), w.cams)
+    assert_score_parity(s, S, ref)
+
+
+def test_ablation_flags(torch, rb, ctx):
+    w = synth.config0(seed=5, n=3000)
+    for flags in (rb.FLAG_NORM_ATTR | rb.FLAG_NO_VIS, rb.FLAG_NORM_ATTR | rb.FLAG_NO_PROJ,
+                  rb.FLAG_NORM_ATTR | rb.FLAG_EQUAL_LAMBDA, 0):
+        p = rb.default_params(flags=flags)
+        s, S, _, _ = gpu_score(torch, rb, ctx, w.scene, w.cams, params=p)
+        ref = oracle.score(w.scene.params_f64(), w.cams, oracle_params_from(p, rb))
+        assert_score_parity(s, S, ref)
+
+
+def test_degenerate_scales(torch, rb, ctx):
+    """Scales that underflow float32 (flat discs and needles)."""
+    w = synth.random_scene(seed=9, n=300, v=12)
+    sc = w.scene
+    sc.attr[0, 0:40] = -200.0               # disc: one zero scale
+    sc.attr[0:2, 40:80] = -200.0            # needle: two zero scales
+    sc.attr[0:3, 80:90] = -200.0            # point: three zero scales
+    s, S, _, _ = gpu_score(torch, rb, ctx, sc, w.cams)
+    ref = oracle.score(sc.params_f64(), w.cams)
+    assert_score_parity(s, S, ref)
+
+
+def test_empty_scene(torch, rb, ctx):
+    w = synth.random_scene(seed=1, n=1, v=2)
+    dev = torch.device("cuda", 0)
+    pos = torch.zeros((3, 0), device=dev)
+    attr = torch.zeros((56, 0), device=dev)
+    cams = rb.cameras_to_device(w.cams, dev)
+    s = ctx.score(pos, attr, cams)
+    assert s.numel() == 0
+    mask, thr, nk = ctx.select(s, 0.5)
+    assert nk == 0 and math.isinf(thr)
+    ctx.check()
+
+
+def test_select_edge_inputs(torch, rb, ctx):
+    rng = np.random.default_rng(3)
+    cases = {
+        "equal": np.full(5000, 0.25, dtype=np.float32),
+        "zeros_heavy": np.where(rng.random(70001) < 0.7, 0.0, rng.random(70001)).astype(np.float32),
+        "signed_zero": np.where(rng.random(9000) < 0.5, -0.0, 0.0).astype(np.float32),
+        "negative": rng.normal(size=33333).astype(np.float32),
+        "inf": np.where(rng.random(4097) < 0.2, np.inf, rng.random(4097)).astype(np.float32),
+        "few_values": rng.integers(0, 4, 100003).astype(np.float32),
+        "one": np.array([3.0], dtype=np.float32),
+        "large_random": rng.random(1_000_003).astype(np.float32),
+    }
+    for name, s in cases.items():
+        for ratio in (0.0, 0.1, 0.5, 0.66, 0.9, 0.9999):
+            check_select_exact(torch, ctx, s, ratio)
+
+
+def test_select_rejects_nan(torch, rb, ctx):
+    s = torch.rand(1000, device="cuda")
+    s[17] = float("nan")
+    with pytest.raises(rb.RefineError) as e:
+        ctx.select(s, 0.5)
+    assert e.value.status == rb.REFINE_ENONFINITE
+
+
+def test_nonfinite_and_invalid_inputs(torch, rb, ctx):
+    w = synth.random_scene(seed=2, n=500, v=4)
+    pos, attr, cams = upload(torch, rb, w.scene, w.cams)
+    attr2 = attr.clone()
+    attr2[20, 7] = float("inf")
+    ctx.score(pos, attr2, cams)
+    assert ctx.status() == rb.REFINE_ENONFINITE
+    pos2 = pos.clone()
+    pos2[1, 3] = float("nan")
+    ctx.score(pos2, attr, cams)
+    assert ctx.status() == rb.REFINE_ENONFINITE
+    bad = w.cams.copy()
+    bad[1]["znear"] = -1.0
+    ctx.score(pos, attr, rb.cameras_to_device(bad, pos.device))
+    assert ctx.status() == rb.REFINE_EINVAL
+    attr3 = attr.clone()
+    attr3[3:7, 11] = 0.0  # zero quaternion
+    ctx.score(pos, attr3, cams)
+    assert ctx.status() == rb.REFINE_EINVAL
+    assert ctx.status() == rb.REFINE_OK  # reading clears
+    # host-side argument checks
+    with pytest.raises(rb.RefineError):
+        ctx.select(torch.rand(10, device="cuda"), 1.0)
+    with pytest.raises(rb.RefineError):
+        ctx.score(pos, attr, cams, n_views=0)
+    p = rb.default_params(eta=0.0)
+    with pytest.raises(rb.RefineError):
+        ctx.score(pos, attr, cams, params=p)
+    # compaction into a too-short output is refused by the device
+    s = ctx.score(pos, attr, cams)
+    mask, _, nk = ctx.select(s, 0.5)
+    ctx.compact(pos, attr, mask, nk, out_row_stride=nk - 1)
+    assert ctx.status() == rb.REFINE_EINVAL
+
+
+def test_deterministic(torch, rb, ctx):
+    w = synth.config0(seed=6, n=20000)
+    a = gpu_score(torch, rb, ctx, w.scene, w.cams)[0]
+    b = gpu_score(torch, rb, ctx, w.scene, w.cams)[0]
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_prune_host_matches_device_path(torch, rb, ctx):
+    w = synth.config0(seed=7, n=12345)
+    s, S, _, (pos, attr) = gpu_score(torch, rb, ctx, w.scene, w.cams)
+    mask, thr, nk = ctx.select(torch.from_numpy(s).cuda(), 0.66)
+    op, oa, idx = ctx.compact(pos, attr, mask, nk)
+    r = ctx.prune_host(torch.from_numpy(w.scene.pos).pin_memory(), torch.from_numpy(w.scene.attr).pin_memory(),
+                       w.cams, 0.66, want_scores=True)
+    assert r["n_keep"] == nk and r["threshold"] == thr
+    assert np.array_equal(r["scores"].numpy().view(np.uint32), s.view(np.uint32))
+    assert np.array_equal(r["idx"].numpy(), idx.cpu().numpy())
+    assert np.array_equal(r["out_pos"].numpy(), op.cpu().numpy())
+    assert np.array_equal(r["out_attr"].numpy(), oa.cpu().numpy())
+
+
+def test_core_shell_1m_full(torch, rb, ctx):
+    """N=1M core-shell scene, 150 hemisphere views at 1297x840: every score
+    against the FP64 oracle, masks at the three ratios."""
+    w = synth.config1()
+    s, S, st, (pos, attr) = gpu_score(torch, rb, ctx, w.scene, w.cams)
+    ref = oracle.score(w.scene.params_f64(), w.cams)
+    clean = assert_score_parity(s, S, ref)
+    assert clean.mean() > 0.97
+    np.testing.assert_allclose(st["lambda"], ref["stats"]["lambda"], rtol=1e-6)
+    for ratio in w.ratios:
+        mask, words, nk = check_select_exact(torch, ctx, s, ratio)
+        assert check_mask_vs_oracle_scores(words, ref, ratio, w.scene.n) > 0.999
+    check_compact_exact(torch, ctx, w.scene, pos, attr, mask, nk)
+
+
+def test_core_shell_3p5m_sampled(torch, rb, ctx):
+    """N=3.5M, 250 views at 1600x1063, the benchmark's launch configuration:
+    a seeded 50k-primitive sample against the oracle (statistics from all
+    3.5M), exact selection and compaction of the full scene."""
+    w = synth.config2()
+    s, S, st, (pos, attr) = gpu_score(torch, rb, ctx, w.scene, w.cams)
+    g = w.scene.params_f64()
+    idx = np.sort(np.random.default_rng(22).choice(w.scene.n, 50_000, replace=False))
+    ref = oracle.score_subset(g, idx, w.cams)
+    assert_score_parity(s[idx], S[idx], ref)
+    np.testing.assert_allclose(st["lambda"], ref["stats"]["lambda"], rtol=1e-6)
+    mask, _, nk = check_select_exact(torch, ctx, s, 0.5)
+    check_compact_exact(torch, ctx, w.scene, pos, attr, mask, nk)
