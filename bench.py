@@ -21,7 +21,6 @@ import os
 import statistics
 import subprocess
 import sys
-import tempfile
 import threading
 import time
 
@@ -42,14 +41,14 @@ METRIC = "Gaussian×view pairs/s"
 def workload(name: str, rank: int = 0):
     from paper_2606_09074_gb300 import synth
     if name == "c2":
-        w = synth.config2(seed=2 + 1000 * rank)
+        w = synth.config2(seed=replica_seed(2, rank))
         w.name = "core-shell N=3.5M V=250 1600x1063, FP32, ratio 0.5"
     elif name == "c1":
-        w = synth.config1(seed=1 + 1000 * rank)
+        w = synth.config1(seed=replica_seed(1, rank))
         w.ratios = (0.5,)
         w.name = "core-shell N=1M V=150 1297x840, FP32, ratio 0.5"
     elif name == "c0":
-        w = synth.config0(seed=0 + 1000 * rank)
+        w = synth.config0(seed=replica_seed(0, rank))
         w.name = "normal N=10k V=16 640x480, FP32, ratio 0.5"
     else:
         raise ValueError(name)
@@ -144,6 +143,24 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "power_w_max": max(pw),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def aggregate_over_ranks(local_ms: float, steps: int, pairs_per_step: int, world: int, dist=None,
+                         device=None):
+    """Max over ranks of the timed-region length; whole-job throughput =
+    all ranks' pairs / that time.  Returns (max_ms, pairs_per_s)."""
+    total_ms = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps * pairs_per_step / (total_ms / 1000.0)
+
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank scores its own replica scene of the same shape."""
+    return base_seed + 1000 * rank
 
 
 # ----------------------------------------------------------------- oracle
@@ -267,14 +284,10 @@ def run_ours(args, rank: int, world: int):
     clocks.stop()
     ctx.check()
     per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_step = total_ms / args.steps
     pairs = n * V
-    value = world * args.steps * pairs / (total_ms / 1000.0)
+    total_ms, value = aggregate_over_ranks(evs[0].elapsed_time(evs[-1]), args.steps, pairs, world,
+                                           dist, dev)
+    ms_step = total_ms / args.steps
 
     # roofline of the dominant kernel (score): live CUDA-event timing
     props = torch.cuda.get_device_properties(dev)
