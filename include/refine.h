@@ -219,6 +219,32 @@ refine_status refine_prune_host(refine_ctx *ctx, int64_t n, int32_t dtype,
                                 int64_t *n_keep_out, float *threshold_out,
                                 refine_stream_t stream);
 
+/* Ratio pruning without any allocation.  The paper has no counterpart; this
+ * entry point exists for callers that cannot allocate device memory -- code
+ * recording a CUDA graph that must not contain allocation nodes, plug-ins
+ * whose host engine owns every device allocation, real-time loops whose
+ * memory is fixed at start-up -- and so cannot create a refine_ctx.
+ *
+ * Same inputs, outputs and result as refine_select (same kernels), but no
+ * context: it runs on the calling thread's current device and keeps its
+ * scratch (selection state and tie counts) in a fixed device array of about
+ * 74 KB inside the library, which every GPU that loads the library holds
+ * until the process exits.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *   n        0 <= n <= 67,108,864 (2^26); larger n returns REFINE_EINVAL
+ *   errbuf   host buffer of errlen bytes for a message, or NULL
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the one array and
+ * each call resets it: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  NaN scores are
+ * reported (REFINE_ENONFINITE) only when threshold_out is non-NULL, which
+ * makes the call synchronise `stream`. */
+refine_status refine_select_noalloc(const float *scores_dev, int64_t n, double ratio,
+                                    uint32_t *keep_mask_dev, float *threshold_out,
+                                    int64_t *n_keep_out, char *errbuf, size_t errlen,
+                                    refine_stream_t stream);
+
 /* Synchronises `stream` and returns (then clears) the device status word:
  * REFINE_OK, or the first error a kernel recorded since the last check. */
 refine_status refine_ctx_check(refine_ctx *ctx, refine_stream_t stream);

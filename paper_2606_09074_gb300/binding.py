@@ -95,6 +95,8 @@ _SIGNATURES = {
     "refine_prune_host": (C.c_int, [_P, C.c_int64, C.c_int32, _P, _P, _P, C.c_int32,
                                     C.POINTER(refine_params), C.c_double, _P, _P, _P, _P,
                                     C.POINTER(C.c_int64), C.POINTER(C.c_float), _P]),
+    "refine_select_noalloc": (C.c_int, [_P, C.c_int64, C.c_double, _P, C.POINTER(C.c_float),
+                                        C.POINTER(C.c_int64), C.c_char_p, C.c_size_t, _P]),
     "refine_ctx_check": (C.c_int, [_P, _P]),
     "refine_ctx_set_timing": (C.c_int, [_P, C.c_int]),
     "refine_ctx_kernel_times": (C.c_int, [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
