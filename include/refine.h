@@ -118,6 +118,15 @@ typedef struct refine_scene_stats {
     double lambda_t[3];  /* unnormalised lambda~ (gem, col, opa), negatives clamped to 0 */
     double lambda[3];    /* Eq. 19 (gem, col, opa)                                        */
     double mean_m[3];    /* scene means of the magnitudes m^gem, m^col, m^opa             */
+    /* How the (primitive, view) pairs were decided (work accounting):        */
+    int64_t pairs;           /* n * n_views                                                */
+    int64_t tile_views;      /* (tile of 64 primitives, view) classifications              */
+    int64_t in_pairs;        /* pairs in tiles found entirely in range and in the image    */
+    int64_t out_pairs;       /* pairs in tiles found entirely invisible                    */
+    int64_t mixed_pairs;     /* pairs decided one by one                                   */
+    int64_t bound_pairs;     /* of those: centre in the depth range but outside the image  */
+    int64_t footprint_pairs; /* of those: within the conservative footprint radius, so the
+                                exact J W Sigma W^T J^T test decided them                  */
 } refine_scene_stats;
 
 typedef struct refine_ctx refine_ctx;

@@ -66,12 +66,17 @@ class refine_params(C.Structure):
 
 class refine_scene_stats(C.Structure):
     _fields_ = [("F_col", C.c_double), ("F_opa", C.c_double), ("F_gem", C.c_double),
-                ("lambda_t", C.c_double * 3), ("lambda_", C.c_double * 3), ("mean_m", C.c_double * 3)]
+                ("lambda_t", C.c_double * 3), ("lambda_", C.c_double * 3), ("mean_m", C.c_double * 3),
+                ("pairs", C.c_int64), ("tile_views", C.c_int64), ("in_pairs", C.c_int64),
+                ("out_pairs", C.c_int64), ("mixed_pairs", C.c_int64), ("bound_pairs", C.c_int64),
+                ("footprint_pairs", C.c_int64)]
 
     def as_dict(self):
         return {"F_col": self.F_col, "F_opa": self.F_opa, "F_gem": self.F_gem,
                 "lambda_t": list(self.lambda_t), "lambda": list(self.lambda_),
-                "mean_m": list(self.mean_m)}
+                "mean_m": list(self.mean_m), "pairs": self.pairs, "tile_views": self.tile_views,
+                "in_pairs": self.in_pairs, "out_pairs": self.out_pairs, "mixed_pairs": self.mixed_pairs,
+                "bound_pairs": self.bound_pairs, "footprint_pairs": self.footprint_pairs}
 
 
 assert C.sizeof(refine_camera) == 80 and C.sizeof(refine_scene) == 40

@@ -18,21 +18,31 @@ __device__ __forceinline__ void set_status(int *status, int code)
     atomicCAS(status, 0, code);  // the first error wins
 }
 
-// Derived camera record (64 bytes).  With the intrinsic matrix K and the
-// world-to-camera rotation rows R0, R1, R2 (Eq. 13):
-//   (U, V, z) = P mu + p,  P = K W,  p = K t,  pixel (u, v) = (U / z, V / z).
+// Derived camera record (144 bytes).  With the intrinsic matrix K and the
+// world-to-camera rotation rows R0, R1, R2 (Eq. 13), each row a linear form
+// (a, a0) evaluated as a . mu + a0:
+//   U = P0 mu + p0, V = P1 mu + p1, z = R2 mu + t2   (P = K W, p = K t),
+//   pixel (u, v) = (U / z, V / z).
 struct __align__(16) CamRec {
-    float4 r0;   // (fx R0 + cx R2, fx t0 + cx t2)
-    float4 r1;   // (fy R1 + cy R2, fy t1 + cy t2)
-    float4 r2;   // (R2, t2)
+    float4 r0;   // U:        (fx R0 + cx R2, fx t0 + cx t2)
+    float4 r1;   // V:        (fy R1 + cy R2, fy t1 + cy t2)
+    float4 r2;   // z:        (R2, t2)
     float4 lim;  // (width, height, znear, zfar)
+    float4 k;    // (fx^2, fy^2, cx, cy)
+    float4 uw;   // U - w z:  (P0 - w R2, p0 - w t2)
+    float4 vh;   // V - h z:  (P1 - h R2, p1 - h t2)
+    float4 tx;   // fx x:     (fx R0, fx t0)
+    float4 ty;   // fy y:     (fy R1, fy t1)
 };
-static_assert(sizeof(CamRec) == 64, "camera record layout");
+static_assert(sizeof(CamRec) == 144, "camera record layout");
 
-// Per-scene constants produced by the content-feature pass (Eq. 18-19).
+// Per-scene constants produced by the content-feature pass (Eq. 18-19) and
+// the quantisation of the processing-order grid.
 struct SceneConsts {
     float kappa[3];   // lambda^k / mean(m^k)  (or lambda^k without NORM_ATTR)
-    float pad;
+    float lo[3];      // grid origin (mean - 3 sigma per axis)
+    float qscale[3];  // cells per unit length per axis
+    float pad[3];
 };
 
 // Scene statistics (host-visible copy of refine_scene_stats).
@@ -43,8 +53,9 @@ struct SceneStats {
     double mean_m[3];
 };
 
-// Number of float sums the content-feature pass reduces per block.
-constexpr int kFeatSums = 7;  // y, y^2, a(1-a), gem ratio, m_gem, m_col, m_opa
+// Number of float sums the content-feature pass reduces per block:
+// y, y^2, a(1-a), gem ratio, m_gem, m_col, m_opa, mu (3), mu^2 (3).
+constexpr int kFeatSums = 13;
 
 // ---------------------------------------------------------------- loads
 __device__ __forceinline__ float ld_attr(const float *p) { return __ldg(p); }

@@ -10,12 +10,31 @@
 
 namespace refine {
 
-// Cameras processed per score launch (64 bytes each in shared memory).  A
+// Cameras processed per score launch (144 bytes each in shared memory).  A
 // larger view set is split into passes of this size; pass boundaries fall
-// on multiples of 16 views so the summation order is independent of it.
-constexpr int kViewsPerPass = 1024;
+// on multiples of 32 views so the summation order is independent of it.
+constexpr int kViewsPerPass = 512;
 constexpr int kScoreThreads = 256;
+constexpr int kScoreGPT = 2;          // primitives per thread in k_score
 constexpr int kFeatThreads = 256;
+
+// Spatial cells for the processing order of k_score: a 128^3 grid over the
+// scene's mean +- 3 sigma box, numbered in Morton order.
+constexpr int kCellBits = 7;
+constexpr int kCells = 1 << (3 * kCellBits);
+constexpr int kScanThreads = 1024;
+constexpr int kScanBlocks = kCells / kScanThreads;
+
+// Diagnostic counters of k_score (written only when ScoreLaunch::need is set).
+enum {
+    kCntTiles = 0,     // (warp tile, view) classifications
+    kCntInPairs,       // pairs in tiles classified entirely visible
+    kCntOutPairs,      // pairs in tiles classified entirely invisible
+    kCntMixedPairs,    // pairs evaluated one by one
+    kCntBoundPairs,    // of those: centre outside the image, in the depth range
+    kCntExactPairs,    // of those: within the conservative footprint radius
+    kCountSlots
+};
 
 struct ScoreLaunch {
     const float *pos;
@@ -23,33 +42,41 @@ struct ScoreLaunch {
     int dtype;
     int64_t stride;
     int64_t n;
-    const CamRec *cams;   // this pass's cameras (device, 16-byte aligned)
-    int vcount;           // cameras in this pass
-    int first, last;      // first / last pass of the view set
+    const uint32_t *perm;       // processing order (a permutation of 0..n-1)
+    const float *m_col;         // per-primitive |SH|_2 from the feature pass
+    const CamRec *cams;         // this pass's cameras (device, 16-byte aligned)
+    int vcount;                 // cameras in this pass
+    int first, last;            // first / last pass of the view set
     float eta;
-    float inv_views;      // 1 / |V|
+    float inv_views;            // 1 / |V|
     int flags;
     const SceneConsts *consts;
-    const float *m_col;
-    float *running;       // per-primitive running view sum between passes
+    float *running;             // per-primitive running view sum between passes
     float *scores;
-    float *view_sum;      // optional
+    float *view_sum;            // optional
+    unsigned long long *need;   // optional diagnostic counters (kCountSlots), see k_score
     int *status;
-    int grid;             // CTAs (persistent)
-    int gpt;              // primitives per thread (1 or 2)
+    int grid;                   // CTAs (persistent)
 };
 
 cudaError_t launch_cam_prep(const refine_camera *cams, int V, CamRec *out, int *status,
                             cudaStream_t s);
-int feature_blocks(int64_t n, int dtype);
-cudaError_t launch_features(const void *attr, int dtype, int64_t stride, int64_t n, float eta,
-                            const float luma[3], float *m_col, double *partials, bool vec,
+int feature_blocks(int64_t n);
+cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
+                            float eta, const float luma[3], float *m_col, double *partials, bool vec,
                             int *status, cudaStream_t s);
 cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_t n,
                                      const refine_params *p, SceneConsts *consts,
                                      SceneStats *stats, cudaStream_t s);
+cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, const SceneConsts *consts,
+                         uint32_t *cell, unsigned *counts, int num_sms, cudaStream_t s);
+cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done,
+                             cudaStream_t s);
+cudaError_t launch_cell_scatter(const uint32_t *cell, int64_t n, unsigned *counts,
+                                const unsigned *off_local, const unsigned *bsum, uint32_t *perm,
+                                int num_sms, cudaStream_t s);
 cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s);
-int score_grid(int num_sms, int64_t n, int vcount, int gpt);
+int score_grid(int num_sms, int64_t n, int vcount);
 
 // ------------------------------------------------------------- select
 struct SelState {

@@ -1,5 +1,6 @@
 // Scoring kernels: camera preparation, the content-feature pass (Eq.
-// (features), Eq. 18-19) and the N x V importance kernel (Eq. 7, Eq. 20).
+// (features), Eq. 18-19), the spatial processing order, and the N x V
+// importance kernel (Eq. 7, Eq. 20).
 #include <math.h>
 
 #include "internal.h"
@@ -31,6 +32,8 @@ __global__ void k_cam_prep(const refine_camera *__restrict__ cams, int V, CamRec
         r.r1 = r.r0;
         r.r2 = r.r0;
         r.lim = make_float4(0.f, 0.f, 1.f, 0.f);  // znear > zfar: never visible
+        r.k = r.r0;
+        r.uw = r.vh = r.tx = r.ty = r.r0;
         out[v] = r;
         return;
     }
@@ -41,6 +44,14 @@ __global__ void k_cam_prep(const refine_camera *__restrict__ cams, int V, CamRec
                        (float)(fy * c.R[5] + cy * c.R[8]), (float)(fy * c.t[1] + cy * c.t[2]));
     r.r2 = make_float4(c.R[6], c.R[7], c.R[8], c.t[2]);
     r.lim = make_float4((float)c.width, (float)c.height, c.znear, c.zfar);
+    r.k = make_float4((float)(fx * fx), (float)(fy * fy), c.cx, c.cy);
+    const double w = c.width, h = c.height;
+    r.uw = make_float4((float)(fx * c.R[0] + (cx - w) * c.R[6]), (float)(fx * c.R[1] + (cx - w) * c.R[7]),
+                       (float)(fx * c.R[2] + (cx - w) * c.R[8]), (float)(fx * c.t[0] + (cx - w) * c.t[2]));
+    r.vh = make_float4((float)(fy * c.R[3] + (cy - h) * c.R[6]), (float)(fy * c.R[4] + (cy - h) * c.R[7]),
+                       (float)(fy * c.R[5] + (cy - h) * c.R[8]), (float)(fy * c.t[1] + (cy - h) * c.t[2]));
+    r.tx = make_float4((float)(fx * c.R[0]), (float)(fx * c.R[1]), (float)(fx * c.R[2]), (float)(fx * c.t[0]));
+    r.ty = make_float4((float)(fy * c.R[3]), (float)(fy * c.R[4]), (float)(fy * c.R[5]), (float)(fy * c.t[1]));
     out[v] = r;
 }
 
@@ -52,39 +63,36 @@ cudaError_t launch_cam_prep(const refine_camera *cams, int V, CamRec *out, int *
 }
 
 // ---------------------------------------------------------------------
-// Content features.  Per primitive (R1, R3 of the oracle's readings):
-//   y     = C0 (l . dc)           luma minus its constant offset 0.5 sum(l)
-//   a     = sigmoid(logit)
-//   s     = exp(log-scale)
-//   gem   = max(s) / (min(s) + eta)
-//   m_gem = product of the two largest scales, m_col = |SH|_2, m_opa = a
-// Sums per thread in float, per block in a fixed double tree; the block
-// partials are reduced by k_features_finalize in a fixed order, so the
-// result depends only on n and the storage type.
+// Content features.  Per primitive (the readings R1, R3):
+//   a = sigmoid(logit), s = exp(log-scale)
+//   y = C0 (l . dc)            luma minus its constant offset 0.5 sum(l)
+//   gem = max(s) / (min(s) + eta), m_gem = product of the two largest scales,
+//   m_col = |SH|_2 over 48 coefficients (written out), m_opa = a
+// Thirteen sums (the feature sums and the first two moments of the means)
+// are kept per thread in float and reduced per block in a fixed double tree;
+// the grid depends only on n, so the sums do too.
 // ---------------------------------------------------------------------
-template <typename AT, int K>
-struct RowLoad;
+template <typename AT>
+struct Row4;
 
 template <>
-struct RowLoad<float, 4> {
+struct Row4<float> {
     __device__ static void load(const float *row, int64_t i, float (&v)[4])
     {
-        float4 q = __ldg(reinterpret_cast<const float4 *>(row + i));
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(row + i));
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
 };
 
 template <>
-struct RowLoad<__nv_bfloat16, 8> {
-    __device__ static void load(const __nv_bfloat16 *row, int64_t i, float (&v)[8])
+struct Row4<__nv_bfloat16> {
+    __device__ static void load(const __nv_bfloat16 *row, int64_t i, float (&v)[4])
     {
-        uint4 q = __ldg(reinterpret_cast<const uint4 *>(row + i));
-        uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[2 * k] = __uint_as_float(w[k] << 16);
-            v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-        }
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row + i));
+        v[0] = __uint_as_float(q.x << 16);
+        v[1] = __uint_as_float(q.x & 0xffff0000u);
+        v[2] = __uint_as_float(q.y << 16);
+        v[3] = __uint_as_float(q.y & 0xffff0000u);
     }
 };
 
@@ -93,83 +101,87 @@ struct FeatAcc {
     float bad;  // accumulates x * 0, which is NaN iff some x was not finite
 };
 
-__device__ __forceinline__ void feat_accumulate(FeatAcc &acc, float ls0, float ls1, float ls2,
-                                                float logit, float dc0, float dc1, float dc2,
-                                                float sumsq, float eta, float l0, float l1,
-                                                float l2, float &m_col)
+__device__ __forceinline__ float feat_one(FeatAcc &acc, float mx, float my, float mz, float ls0, float ls1,
+                                          float ls2, float logit, float dc0, float dc1, float dc2, float sumsq,
+                                          float eta, float l0, float l1, float l2)
 {
-    float s0 = expf(ls0), s1 = expf(ls1), s2 = expf(ls2);
-    float a = 1.f / (1.f + expf(-logit));
-    float y = kSH_C0 * fmaf(l0, dc0, fmaf(l1, dc1, l2 * dc2));
-    float smax = fmaxf(s0, fmaxf(s1, s2)), smin = fminf(s0, fminf(s1, s2));
-    float mg = fmaxf(fmaxf(s0 * s1, s0 * s2), s1 * s2);
-    m_col = sqrtf(sumsq);
+    const float e0 = expf(ls0), e1 = expf(ls1), e2 = expf(ls2);
+    const float alpha = 1.f / (1.f + expf(-logit));
+    const float y = kSH_C0 * fmaf(l0, dc0, fmaf(l1, dc1, l2 * dc2));
+    const float smax = fmaxf(e0, fmaxf(e1, e2)), smin = fminf(e0, fminf(e1, e2));
+    const float mg = fmaxf(fmaxf(e0 * e1, e0 * e2), e1 * e2);
+    const float mc = sqrtf(sumsq);
     acc.s[0] += y;
     acc.s[1] = fmaf(y, y, acc.s[1]);
-    acc.s[2] = fmaf(a, 1.f - a, acc.s[2]);
+    acc.s[2] = fmaf(alpha, 1.f - alpha, acc.s[2]);
     acc.s[3] += smax / (smin + eta);
     acc.s[4] += mg;
-    acc.s[5] += m_col;
-    acc.s[6] += a;
-    acc.bad = fmaf(ls0 + ls1 + ls2 + logit, 0.f, acc.bad);
+    acc.s[5] += mc;
+    acc.s[6] += alpha;
+    acc.s[7] += mx;
+    acc.s[8] += my;
+    acc.s[9] += mz;
+    acc.s[10] = fmaf(mx, mx, acc.s[10]);
+    acc.s[11] = fmaf(my, my, acc.s[11]);
+    acc.s[12] = fmaf(mz, mz, acc.s[12]);
+    acc.bad = fmaf(mx + my + mz + ls0 + ls1 + ls2 + logit + sumsq, 0.f, acc.bad);
+    return mc;
 }
 
-template <typename AT, int K>
-__global__ void __launch_bounds__(kFeatThreads) k_features(const AT *__restrict__ attr, int64_t stride,
+template <typename AT, bool VEC>
+__global__ void __launch_bounds__(kFeatThreads) k_features(const float *__restrict__ pos,
+                                                           const AT *__restrict__ attr, int64_t stride,
                                                            int64_t n, float eta, float l0, float l1,
                                                            float l2, float *__restrict__ m_col,
-                                                           double *__restrict__ partials,
-                                                           int *status)
+                                                           double *__restrict__ partials, int *status)
 {
     FeatAcc acc;
 #pragma unroll
     for (int k = 0; k < kFeatSums; ++k) acc.s[k] = 0.f;
     acc.bad = 0.f;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x * K;
-    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * K; base < n; base += step) {
-        if constexpr (K > 1) {
-          if (base + K <= n) {
-            float ls[3][K], lg[K], dc[3][K], sq[K], v[K];
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * 4;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; base < n; base += step) {
+        if (VEC && base + 4 <= n) {
+            float px[4], py[4], pz[4], l[3][4], lg[4], dc[3][4], sq[4], v[4];
+            Row4<float>::load(pos, base, px);
+            Row4<float>::load(pos + stride, base, py);
+            Row4<float>::load(pos + 2 * stride, base, pz);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) RowLoad<AT, K>::load(attr + r * stride, base, ls[r]);
-            RowLoad<AT, K>::load(attr + 7 * stride, base, lg);
+            for (int r = 0; r < 3; ++r) Row4<AT>::load(attr + r * stride, base, l[r]);
+            Row4<AT>::load(attr + 7 * stride, base, lg);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) RowLoad<AT, K>::load(attr + (8 + r) * stride, base, dc[r]);
+            for (int r = 0; r < 3; ++r) Row4<AT>::load(attr + (8 + r) * stride, base, dc[r]);
 #pragma unroll
-            for (int k = 0; k < K; ++k)
+            for (int k = 0; k < 4; ++k)
                 sq[k] = fmaf(dc[0][k], dc[0][k], fmaf(dc[1][k], dc[1][k], dc[2][k] * dc[2][k]));
-#pragma unroll 5
+#pragma unroll 15
             for (int r = 11; r < 56; ++r) {
-                RowLoad<AT, K>::load(attr + r * stride, base, v);
+                Row4<AT>::load(attr + r * stride, base, v);
 #pragma unroll
-                for (int k = 0; k < K; ++k) sq[k] = fmaf(v[k], v[k], sq[k]);
+                for (int k = 0; k < 4; ++k) sq[k] = fmaf(v[k], v[k], sq[k]);
             }
-            float mc[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                feat_accumulate(acc, ls[0][k], ls[1][k], ls[2][k], lg[k], dc[0][k], dc[1][k],
-                                dc[2][k], sq[k], eta, l0, l1, l2, mc[k]);
-                acc.bad = fmaf(sq[k], 0.f, acc.bad);
-            }
-#pragma unroll
-            for (int k = 0; k < K; ++k) m_col[base + k] = mc[k];
-            continue;
-          }
-        }
-        {
-            for (int64_t i = base; i < n && i < base + K; ++i) {
+            float4 mc;
+            mc.x = feat_one(acc, px[0], py[0], pz[0], l[0][0], l[1][0], l[2][0], lg[0], dc[0][0], dc[1][0], dc[2][0],
+                            sq[0], eta, l0, l1, l2);
+            mc.y = feat_one(acc, px[1], py[1], pz[1], l[0][1], l[1][1], l[2][1], lg[1], dc[0][1], dc[1][1], dc[2][1],
+                            sq[1], eta, l0, l1, l2);
+            mc.z = feat_one(acc, px[2], py[2], pz[2], l[0][2], l[1][2], l[2][2], lg[2], dc[0][2], dc[1][2], dc[2][2],
+                            sq[2], eta, l0, l1, l2);
+            mc.w = feat_one(acc, px[3], py[3], pz[3], l[0][3], l[1][3], l[2][3], lg[3], dc[0][3], dc[1][3], dc[2][3],
+                            sq[3], eta, l0, l1, l2);
+            *reinterpret_cast<float4 *>(m_col + base) = mc;
+        } else {
+            for (int64_t i = base; i < n && i < base + 4; ++i) {
                 float sq = 0.f;
                 for (int r = 8; r < 56; ++r) {
-                    float x = ld_attr(attr + r * stride + i);
+                    const float x = ld_attr(attr + r * stride + i);
                     sq = fmaf(x, x, sq);
                 }
-                float mc;
-                feat_accumulate(acc, ld_attr(attr + i), ld_attr(attr + stride + i),
-                                ld_attr(attr + 2 * stride + i), ld_attr(attr + 7 * stride + i),
-                                ld_attr(attr + 8 * stride + i), ld_attr(attr + 9 * stride + i),
-                                ld_attr(attr + 10 * stride + i), sq, eta, l0, l1, l2, mc);
-                acc.bad = fmaf(sq, 0.f, acc.bad);
-                m_col[i] = mc;
+                m_col[i] = feat_one(acc, __ldg(pos + i), __ldg(pos + stride + i), __ldg(pos + 2 * stride + i),
+                                    ld_attr(attr + i), ld_attr(attr + stride + i), ld_attr(attr + 2 * stride + i),
+                                    ld_attr(attr + 7 * stride + i), ld_attr(attr + 8 * stride + i),
+                                    ld_attr(attr + 9 * stride + i), ld_attr(attr + 10 * stride + i), sq, eta,
+                                    l0, l1, l2);
             }
         }
     }
@@ -189,41 +201,42 @@ __global__ void __launch_bounds__(kFeatThreads) k_features(const AT *__restrict_
     if (threadIdx.x < kFeatSums) partials[(int64_t)blockIdx.x * kFeatSums + threadIdx.x] = red[threadIdx.x][0];
 }
 
-int feature_blocks(int64_t n, int dtype)
+int feature_blocks(int64_t n)
 {
-    const int64_t per_block = (int64_t)kFeatThreads * (dtype == REFINE_BF16 ? 8 : 4) * 4;
+    const int64_t per_block = (int64_t)kFeatThreads * 4 * 2;
     int64_t b = (n + per_block - 1) / per_block;
     if (b < 1) b = 1;
     if (b > 1024) b = 1024;
     return (int)b;
 }
 
-cudaError_t launch_features(const void *attr, int dtype, int64_t stride, int64_t n, float eta,
-                            const float luma[3], float *m_col, double *partials, bool vec,
+cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
+                            float eta, const float luma[3], float *m_col, double *partials, bool vec,
                             int *status, cudaStream_t s)
 {
-    int nb = feature_blocks(n, dtype);
+    const int nb = feature_blocks(n);
     if (dtype == REFINE_BF16) {
         const __nv_bfloat16 *a = static_cast<const __nv_bfloat16 *>(attr);
         if (vec)
-            k_features<__nv_bfloat16, 8><<<nb, kFeatThreads, 0, s>>>(a, stride, n, eta, luma[0], luma[1],
-                                                                      luma[2], m_col, partials, status);
+            k_features<__nv_bfloat16, true><<<nb, kFeatThreads, 0, s>>>(pos, a, stride, n, eta, luma[0], luma[1],
+                                                                       luma[2], m_col, partials, status);
         else
-            k_features<__nv_bfloat16, 1><<<nb, kFeatThreads, 0, s>>>(a, stride, n, eta, luma[0], luma[1],
-                                                                      luma[2], m_col, partials, status);
+            k_features<__nv_bfloat16, false><<<nb, kFeatThreads, 0, s>>>(pos, a, stride, n, eta, luma[0], luma[1],
+                                                                        luma[2], m_col, partials, status);
     } else {
         const float *a = static_cast<const float *>(attr);
         if (vec)
-            k_features<float, 4><<<nb, kFeatThreads, 0, s>>>(a, stride, n, eta, luma[0], luma[1], luma[2],
-                                                             m_col, partials, status);
+            k_features<float, true><<<nb, kFeatThreads, 0, s>>>(pos, a, stride, n, eta, luma[0], luma[1], luma[2],
+                                                               m_col, partials, status);
         else
-            k_features<float, 1><<<nb, kFeatThreads, 0, s>>>(a, stride, n, eta, luma[0], luma[1], luma[2],
-                                                             m_col, partials, status);
+            k_features<float, false><<<nb, kFeatThreads, 0, s>>>(pos, a, stride, n, eta, luma[0], luma[1],
+                                                                luma[2], m_col, partials, status);
     }
     return cudaGetLastError();
 }
 
-// Eq. (features) -> Eq. 18 -> Eq. 19, in double, one block.
+// Eq. (features) -> Eq. 18 -> Eq. 19 in double, one block; also the grid box
+// (mean +- 3 sigma of the means) of the processing order.
 __global__ void k_features_finalize(const double *__restrict__ partials, int nblocks, int64_t n,
                                     refine_params p, SceneConsts *consts, SceneStats *stats)
 {
@@ -246,7 +259,7 @@ __global__ void k_features_finalize(const double *__restrict__ partials, int nbl
     if (threadIdx.x != 0) return;
     const double N = (double)n;
     SceneStats st;
-    double ybar = red[0][0] / N;
+    const double ybar = red[0][0] / N;
     st.F_col = red[1][0] / N - ybar * ybar;
     if (st.F_col < 0.0) st.F_col = 0.0;
     st.F_opa = red[2][0] / N;
@@ -262,13 +275,17 @@ __global__ void k_features_finalize(const double *__restrict__ partials, int nbl
     }
     SceneConsts c;
     for (int k = 0; k < 3; ++k) {
-        st.lambda[k] = ((p.flags & REFINE_FLAG_EQUAL_LAMBDA) || tot == 0.0) ? 1.0 / 3.0
-                                                                             : st.lambda_t[k] / tot;
+        st.lambda[k] = ((p.flags & REFINE_FLAG_EQUAL_LAMBDA) || tot == 0.0) ? 1.0 / 3.0 : st.lambda_t[k] / tot;
         double kap = st.lambda[k];
         if (p.flags & REFINE_FLAG_NORM_ATTR) kap = st.mean_m[k] > 0.0 ? st.lambda[k] / st.mean_m[k] : 0.0;
         c.kappa[k] = (float)kap;
+        const double mean = red[7 + k][0] / N;
+        double var = red[10 + k][0] / N - mean * mean;
+        const double sd = var > 0.0 ? sqrt(var) : 0.0;
+        c.lo[k] = (float)(mean - 3.0 * sd);
+        c.qscale[k] = sd > 0.0 && isfinite(sd) ? (float)((1 << kCellBits) / (6.0 * sd)) : 0.f;
+        c.pad[k] = 0.f;
     }
-    c.pad = 0.f;
     *consts = c;
     if (stats) *stats = st;
 }
@@ -282,81 +299,391 @@ cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_
 }
 
 // ---------------------------------------------------------------------
+// Processing order.  Primitives are bucketed by a 64^3 Morton-numbered grid
+// (counting sort) so that the 32 lanes of a warp hold nearby primitives and
+// tend to take the same side of each view's frustum edges.  The order only
+// affects speed: every primitive's score is computed by one thread with the
+// views in a fixed order, whatever its position.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint32_t spread3(uint32_t x)
+{
+    uint32_t r = 0;
+#pragma unroll
+    for (int b = 0; b < kCellBits; ++b) r |= ((x >> b) & 1u) << (3 * b);
+    return r;
+}
+
+__device__ __forceinline__ uint32_t quantise(float x, float lo, float qs)
+{
+    const float q = fminf(fmaxf((x - lo) * qs, 0.f), (float)((1 << kCellBits) - 1));
+    return (uint32_t)q;
+}
+
+__global__ void k_cells(const float *__restrict__ pos, int64_t stride, int64_t n,
+                        const SceneConsts *__restrict__ consts, uint32_t *__restrict__ cell,
+                        unsigned *__restrict__ counts)
+{
+    const SceneConsts c = *consts;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t id = spread3(quantise(__ldg(pos + i), c.lo[0], c.qscale[0])) |
+                            (spread3(quantise(__ldg(pos + stride + i), c.lo[1], c.qscale[1])) << 1) |
+                            (spread3(quantise(__ldg(pos + 2 * stride + i), c.lo[2], c.qscale[2])) << 2);
+        cell[i] = id;
+        atomicAdd(&counts[id], 1u);
+    }
+}
+
+cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, const SceneConsts *consts,
+                         uint32_t *cell, unsigned *counts, int num_sms, cudaStream_t s)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
+    if (g < 1) g = 1;
+    k_cells<<<(int)g, 256, 0, s>>>(pos, stride, n, consts, cell, counts);
+    return cudaGetLastError();
+}
+
+// Exclusive scan of the cell counts: local offsets within blocks of 1024
+// cells, then the last block turns the block totals into block offsets.
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned s = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned x = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += x;
+    }
+    if (lane == 31) wsum[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned x = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += x;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const unsigned r = s - v + (warp > 0 ? wsum[warp - 1] : 0u);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan(const unsigned *__restrict__ counts,
+                                                            unsigned *__restrict__ off_local,
+                                                            unsigned *bsum, unsigned *done)
+{
+    __shared__ unsigned wsum[32];
+    __shared__ unsigned is_last, carry;
+    const int c = blockIdx.x * kScanThreads + threadIdx.x;
+    const unsigned v = counts[c];
+    const unsigned ex = block_excl_scan(v, wsum);
+    off_local[c] = ex;
+    if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = ex + v;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(done, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) carry = 0u;
+    __syncthreads();
+    for (int b0 = 0; b0 < kScanBlocks; b0 += kScanThreads) {
+        const unsigned b = atomicAdd(&bsum[b0 + threadIdx.x], 0u);
+        const unsigned bex = block_excl_scan(b, wsum) + carry;
+        __syncthreads();
+        bsum[b0 + threadIdx.x] = bex;
+        if (threadIdx.x == kScanThreads - 1) carry = bex + b;
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done,
+                             cudaStream_t s)
+{
+    static_assert(kScanBlocks % kScanThreads == 0, "block totals are scanned in full chunks");
+    k_cell_scan<<<kScanBlocks, kScanThreads, 0, s>>>(counts, off_local, bsum, done);
+    return cudaGetLastError();
+}
+
+__global__ void k_cell_scatter(const uint32_t *__restrict__ cell, int64_t n, unsigned *counts,
+                               const unsigned *__restrict__ off_local, const unsigned *__restrict__ boff,
+                               uint32_t *__restrict__ perm)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = cell[i];
+        const unsigned slot = boff[c / kScanThreads] + off_local[c] + atomicSub(&counts[c], 1u) - 1u;
+        perm[slot] = (uint32_t)i;
+    }
+}
+
+cudaError_t launch_cell_scatter(const uint32_t *cell, int64_t n, unsigned *counts,
+                                const unsigned *off_local, const unsigned *bsum, uint32_t *perm,
+                                int num_sms, cudaStream_t s)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
+    if (g < 1) g = 1;
+    k_cell_scatter<<<(int)g, 256, 0, s>>>(cell, n, counts, off_local, bsum, perm);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------
 // The N x V importance kernel.
 //
-// One thread owns GPT primitives and walks every camera of the pass, the
-// camera records staged once per CTA into shared memory by a TMA bulk copy.
-// For primitive i and view v (Eq. 13-14, Eq. 17, Eq. 20):
-//   (U, V, z) = P mu + p                                (homogeneous pixel)
-//   g0 = z P0 - U P2,  g1 = z P1 - V P2                 (z^2 J W rows)
-//   Qx = |L g0|^2 = 9 z^4 S_xx,  Qy = |L g1|^2 = 9 z^4 S_yy
-//        with L = 3 diag(s) R^T, i.e. Sigma2D = J W Sigma W^T J^T formed
-//        through the square root of Sigma (well conditioned in float)
-//   the 3-sigma box meets [0,w] x [0,h]  <=>  (d_u z^2)^2 <= Qx and
-//        (d_v z^2)^2 <= Qy, d_u = max(0, -u, u - w) written as
-//        max(0, -U, U - w z) / z, so no division is needed
-//   det Sigma2D = |L g0 x L g1|^2 / (81 z^8) > 0 holds whenever all three
-//        scales are nonzero (L invertible, g0 and g1 independent); only a
-//        warp holding a primitive with an underflowed scale evaluates it
-//   term = vis / (z^2 + eta)                            (Eq. 17, one MUFU)
-// Views are summed in blocks of 16 into a running total (fixed order).
-// The epilogue forms D_i = alpha_i S_i / |V| * sum_k lambda^k G~_i^k.
+// One thread owns two primitives (the lanes of a warp hold 64 consecutive
+// primitives of the processing order, a "tile") and walks every camera of
+// the pass; the camera records are staged once per CTA into shared memory by
+// a TMA bulk copy.  For primitive i and view v (Eq. 13-14, Eq. 17, Eq. 20):
+//   (U, V, z) = P mu + p                  homogeneous pixel, u = U / z
+//   d_u z = max(-U, U - w z)              distance of the centre outside
+//   d_v z = max(-V, V - h z)              [0,w] x [0,h], times z
+//   in range: znear < z < zfar
+//   3-sigma box meets the image  <=>  (max(d_u z, 0) z)^2 <= Qx  and
+//                                     (max(d_v z, 0) z)^2 <= Qy
+//     with g0 = z P0 - U P2, g1 = z P1 - V P2 (the rows of z^2 J W) and
+//     Qx = |L g0|^2 = 9 z^4 S_xx, Qy = |L g1|^2 = 9 z^4 S_yy, L = 3 diag(s)
+//     R(q)^T, i.e. Sigma2D = J W Sigma W^T J^T formed through the square
+//     root of Sigma (well conditioned in float).
+//   det Sigma2D = |L g0 x L g1|^2 / (81 z^8) > 0 whenever all three scales
+//     are nonzero (L invertible, g0 and g1 independent); a warp holding a
+//     primitive with an underflowed scale evaluates it on every pair.
+//   term = vis / (z^2 + eta)              (Eq. 17, one MUFU reciprocal)
+//
+// Work is skipped only where the outcome is already implied, so every
+// decision equals the full test's, bit for bit:
+//  * per tile (the bounding box of its 64 centres) and view, a lane classifies
+//    one view (32 views at a time) with interval bounds of the linear forms
+//    U, V, z, U - w z, V - h z, fx x, fy y over the box, plus a 2^-14
+//    relative slack that covers float32 rounding:
+//      IN   every centre is in range and inside the image: vis = 1 for all
+//      OUT  every centre is out of range, or outside an image edge by more
+//           than the footprint bound below: vis = 0, the view is skipped
+//      MIXED otherwise: decided pair by pair;
+//  * pair by pair, in two warp-uniform stages entered only when some lane
+//    needs them: a centre inside the image is visible whatever Sigma2D; a
+//    centre outside is first tested against Qx <= 9 s_max^2 ((U - cx z)^2 +
+//    fx^2 z^2) (as |g0|^2 = fx^2 (x^2 + z^2); inflated by 2^-10), and only
+//    lanes passing that bound need Qx and Qy.
+// Views are summed in blocks of 16 into a running total, in view order (an
+// invisible or skipped view adds +0, which changes nothing), so a
+// primitive's sum does not depend on the tile it is in.
+// The epilogue forms D_i = alpha_i S_i / |V| * sum_k lambda^k G~_i^k (Eq. 7).
 // ---------------------------------------------------------------------
-template <bool NOPROJ, bool DET>
-__device__ __forceinline__ float pair_term(const float4 &c0, const float4 &c1, const float4 &c2,
-                                           const float4 &lim, float mx, float my, float mz,
-                                           const float (&L)[9], float eta)
+struct PairIn {
+    float mx, my, mz;
+    float L[9];
+    float b2;  // 9 s_max^2 (1 + 2^-10)
+};
+
+struct TileBox {
+    float cx, cy, cz;  // centre of the box of the tile's centres
+    float hx, hy, hz;  // half extents
+    float mx, my, mz;  // |centre| + half extent (magnitude bound)
+    float b2;          // max over the tile of 9 s_max^2 (1 + 2^-10)
+};
+
+constexpr float kTileSlack = 6.103515625e-05f;  // 2^-14
+
+struct Range {
+    float lo, hi;
+};
+
+// [lo, hi] of a . mu + a0 over the tile box, widened by the slack.
+__device__ __forceinline__ Range form_range(const float4 &a, const TileBox &t)
 {
-    const float U = fmaf(c0.x, mx, fmaf(c0.y, my, fmaf(c0.z, mz, c0.w)));
-    const float V = fmaf(c1.x, mx, fmaf(c1.y, my, fmaf(c1.z, mz, c1.w)));
-    const float z = fmaf(c2.x, mx, fmaf(c2.y, my, fmaf(c2.z, mz, c2.w)));
-    const float g0x = fmaf(-U, c2.x, z * c0.x), g0y = fmaf(-U, c2.y, z * c0.y),
-                g0z = fmaf(-U, c2.z, z * c0.z);
-    const float g1x = fmaf(-V, c2.x, z * c1.x), g1y = fmaf(-V, c2.y, z * c1.y),
-                g1z = fmaf(-V, c2.z, z * c1.z);
-    const float a0 = fmaf(L[0], g0x, fmaf(L[1], g0y, L[2] * g0z));
-    const float a1 = fmaf(L[3], g0x, fmaf(L[4], g0y, L[5] * g0z));
-    const float a2 = fmaf(L[6], g0x, fmaf(L[7], g0y, L[8] * g0z));
-    const float b0 = fmaf(L[0], g1x, fmaf(L[1], g1y, L[2] * g1z));
-    const float b1 = fmaf(L[3], g1x, fmaf(L[4], g1y, L[5] * g1z));
-    const float b2 = fmaf(L[6], g1x, fmaf(L[7], g1y, L[8] * g1z));
+    const float mid = fmaf(a.x, t.cx, fmaf(a.y, t.cy, fmaf(a.z, t.cz, a.w)));
+    const float rad = fmaf(fabsf(a.x), t.hx, fmaf(fabsf(a.y), t.hy, fabsf(a.z) * t.hz));
+    const float mag = fmaf(fabsf(a.x), t.mx, fmaf(fabsf(a.y), t.my, fmaf(fabsf(a.z), t.mz, fabsf(a.w))));
+    const float sl = kTileSlack * mag;
+    return {mid - rad - sl, mid + rad + sl};
+}
+
+// 0 = MIXED, 1 = IN, 2 = OUT for one view and one tile.
+__device__ __forceinline__ int classify(const CamRec &c, const TileBox &t)
+{
+    const Range z = form_range(c.r2, t);
+    if (z.hi < c.lim.z || z.lo > c.lim.w) return 2;
+    const Range U = form_range(c.r0, t), V = form_range(c.r1, t);
+    const Range UW = form_range(c.uw, t), VH = form_range(c.vh, t);
+    if (z.lo > c.lim.z && z.hi < c.lim.w && U.lo > 0.f && UW.hi < 0.f && V.lo > 0.f && VH.hi < 0.f) return 1;
+    if (!(z.lo > 0.f)) return 0;
+    // outside an edge by more than the footprint bound (times z^2)
+    const Range TX = form_range(c.tx, t), TY = form_range(c.ty, t);
+    const float tx2 = fmaxf(TX.lo * TX.lo, TX.hi * TX.hi), ty2 = fmaxf(TY.lo * TY.lo, TY.hi * TY.hi);
+    const float zz = z.hi * z.hi;
+    const float bx = t.b2 * fmaf(c.k.x, zz, tx2) * 1.00390625f;  // (1 + 2^-8)
+    const float by = t.b2 * fmaf(c.k.y, zz, ty2) * 1.00390625f;
+    const float dl = fmaxf(-U.hi, UW.lo) * z.lo;  // > 0 when the box is left or right of the image
+    const float dt = fmaxf(-V.hi, VH.lo) * z.lo;
+    if ((dl > 0.f && dl * dl > bx) || (dt > 0.f && dt * dt > by)) return 2;
+    return 0;
+}
+
+template <bool DET>
+__device__ __forceinline__ bool exact_box(const float4 &c0, const float4 &c1, const float4 &c2, float U, float V,
+                                          float z, float ex2, float ey2, const PairIn &p)
+{
+    const float g0x = fmaf(-U, c2.x, z * c0.x), g0y = fmaf(-U, c2.y, z * c0.y), g0z = fmaf(-U, c2.z, z * c0.z);
+    const float g1x = fmaf(-V, c2.x, z * c1.x), g1y = fmaf(-V, c2.y, z * c1.y), g1z = fmaf(-V, c2.z, z * c1.z);
+    const float a0 = fmaf(p.L[0], g0x, fmaf(p.L[1], g0y, p.L[2] * g0z));
+    const float a1 = fmaf(p.L[3], g0x, fmaf(p.L[4], g0y, p.L[5] * g0z));
+    const float a2 = fmaf(p.L[6], g0x, fmaf(p.L[7], g0y, p.L[8] * g0z));
+    const float b0 = fmaf(p.L[0], g1x, fmaf(p.L[1], g1y, p.L[2] * g1z));
+    const float b1 = fmaf(p.L[3], g1x, fmaf(p.L[4], g1y, p.L[5] * g1z));
+    const float b2 = fmaf(p.L[6], g1x, fmaf(p.L[7], g1y, p.L[8] * g1z));
     const float Qx = fmaf(a0, a0, fmaf(a1, a1, a2 * a2));
     const float Qy = fmaf(b0, b0, fmaf(b1, b1, b2 * b2));
-    const float du = fmaxf(fmaxf(-U, fmaf(-lim.x, z, U)), 0.f) * z;
-    const float dv = fmaxf(fmaxf(-V, fmaf(-lim.y, z, V)), 0.f) * z;
-    bool vis = (z > lim.z) & (z < lim.w) & (du * du <= Qx) & (dv * dv <= Qy);
+    bool ok = (ex2 <= Qx) & (ey2 <= Qy);
     if (DET) {
         const float x0 = a1 * b2 - a2 * b1, x1 = a2 * b0 - a0 * b2, x2 = a0 * b1 - a1 * b0;
-        vis = vis & ((x0 != 0.f) | (x1 != 0.f) | (x2 != 0.f));
+        ok = ok & ((x0 != 0.f) | (x1 != 0.f) | (x2 != 0.f));
     }
-    const float w = NOPROJ ? 1.f : rcp_approx(fmaf(z, z, eta));
-    return vis ? w : 0.f;
+    return ok;
 }
 
-template <int GPT, bool NOPROJ, bool DET>
-__device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float eta,
-                                          const float (&mx)[GPT], const float (&my)[GPT],
-                                          const float (&mz)[GPT], const float (&L)[GPT][9],
-                                          float (&acc)[GPT])
+struct PairGeom {
+    float U, V, z, ex2, ey2;
+    bool inz, inside;
+};
+
+__device__ __forceinline__ PairGeom pair_geom(const float4 &c0, const float4 &c1, const float4 &c2, const float4 &lim,
+                                              const PairIn &p)
 {
-    for (int v0 = 0; v0 < vcount; v0 += 16) {
-        const int vend = min(v0 + 16, vcount);
-        float part[GPT];
+    PairGeom r;
+    r.U = fmaf(c0.x, p.mx, fmaf(c0.y, p.my, fmaf(c0.z, p.mz, c0.w)));
+    r.V = fmaf(c1.x, p.mx, fmaf(c1.y, p.my, fmaf(c1.z, p.mz, c1.w)));
+    r.z = fmaf(c2.x, p.mx, fmaf(c2.y, p.my, fmaf(c2.z, p.mz, c2.w)));
+    const float du = fmaxf(-r.U, fmaf(-lim.x, r.z, r.U));
+    const float dv = fmaxf(-r.V, fmaf(-lim.y, r.z, r.V));
+    r.inz = (r.z > lim.z) & (r.z < lim.w);
+    r.inside = r.inz & (du <= 0.f) & (dv <= 0.f);
+    const float ex = fmaxf(du, 0.f) * r.z, ey = fmaxf(dv, 0.f) * r.z;
+    r.ex2 = ex * ex;
+    r.ey2 = ey * ey;
+    return r;
+}
+
+template <bool NOPROJ>
+__device__ __forceinline__ float weight(float z, float eta)
+{
+    return NOPROJ ? 1.f : rcp_approx(fmaf(z, z, eta));
+}
+
+template <bool NOPROJ, bool DET, bool COUNT>
+__device__ __forceinline__ void mixed_view(const CamRec &c, float eta, const PairIn (&p)[kScoreGPT],
+                                           const bool (&valid)[kScoreGPT], float (&part)[kScoreGPT],
+                                           unsigned long long (&cnt)[kCountSlots])
+{
+    const float4 c0 = c.r0, c1 = c.r1, c2 = c.r2, lim = c.lim;
+    PairGeom q[kScoreGPT];
+    bool vis[kScoreGPT], out = false;
 #pragma unroll
-        for (int g = 0; g < GPT; ++g) part[g] = 0.f;
-#pragma unroll 2
-        for (int v = v0; v < vend; ++v) {
-            const float4 c0 = cs[v].r0, c1 = cs[v].r1, c2 = cs[v].r2, lim = cs[v].lim;
+    for (int g = 0; g < kScoreGPT; ++g) {
+        q[g] = pair_geom(c0, c1, c2, lim, p[g]);
+        vis[g] = q[g].inside;
+        out |= q[g].inz & !q[g].inside;
+        if (COUNT) cnt[kCntMixedPairs] += valid[g] ? 1 : 0;
+    }
+    if (DET || __any_sync(0xffffffffu, out)) {
+        const float4 k = c.k;
+        bool nearq = false, nq[kScoreGPT];
 #pragma unroll
-            for (int g = 0; g < GPT; ++g)
-                part[g] += pair_term<NOPROJ, DET>(c0, c1, c2, lim, mx[g], my[g], mz[g], L[g], eta);
+        for (int g = 0; g < kScoreGPT; ++g) {
+            const float tx = fmaf(-k.z, q[g].z, q[g].U), ty = fmaf(-k.w, q[g].z, q[g].V);
+            const float zz = q[g].z * q[g].z;
+            const bool o = q[g].inz & !q[g].inside;
+            nq[g] = o & (q[g].ex2 <= p[g].b2 * fmaf(k.x, zz, tx * tx)) & (q[g].ey2 <= p[g].b2 * fmaf(k.y, zz, ty * ty));
+            nearq |= nq[g];
+            if (COUNT) {
+                cnt[kCntBoundPairs] += (valid[g] && o) ? 1 : 0;
+                cnt[kCntExactPairs] += (valid[g] && nq[g]) ? 1 : 0;
+            }
         }
+        if (DET || __any_sync(0xffffffffu, nearq)) {
 #pragma unroll
-        for (int g = 0; g < GPT; ++g) acc[g] += part[g];
+            for (int g = 0; g < kScoreGPT; ++g)
+                vis[g] = q[g].inz & exact_box<DET>(c0, c1, c2, q[g].U, q[g].V, q[g].z, q[g].ex2, q[g].ey2, p[g]);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < kScoreGPT; ++g) part[g] += vis[g] ? weight<NOPROJ>(q[g].z, eta) : 0.f;
+}
+
+template <bool NOPROJ, bool DET, bool COUNT>
+__device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float eta, const PairIn (&p)[kScoreGPT],
+                                          const bool (&valid)[kScoreGPT], const TileBox &tb,
+                                          float (&acc)[kScoreGPT], unsigned long long (&cnt)[kCountSlots])
+{
+    const int lane = threadIdx.x & 31;
+    int nvalid = 0;
+#pragma unroll
+    for (int g = 0; g < kScoreGPT; ++g) nvalid += __popc(__ballot_sync(0xffffffffu, valid[g]));
+    for (int vb = 0; vb < vcount; vb += 32) {
+        const int nv = min(32, vcount - vb);
+        const unsigned vmask = nv == 32 ? 0xffffffffu : ((1u << nv) - 1u);
+        unsigned in_m = 0u, out_m = 0u;
+        if (!DET) {
+            const int cls = lane < nv ? classify(cs[vb + lane], tb) : 0;
+            in_m = __ballot_sync(0xffffffffu, cls == 1);
+            out_m = __ballot_sync(0xffffffffu, cls == 2);
+            if (COUNT && lane == 0) {
+                cnt[kCntTiles] += nv;
+                cnt[kCntInPairs] += (unsigned long long)__popc(in_m & vmask) * nvalid;
+                cnt[kCntOutPairs] += (unsigned long long)__popc(out_m & vmask) * nvalid;
+            }
+        }
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            const unsigned hm = (half ? 0xffff0000u : 0x0000ffffu) & vmask;
+            if (!hm) break;
+            float part[kScoreGPT];
+#pragma unroll
+            for (int g = 0; g < kScoreGPT; ++g) part[g] = 0.f;
+            unsigned todo = hm & ~out_m;
+            while (todo) {
+                const int b = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const CamRec &c = cs[vb + b];
+                if ((in_m >> b) & 1u) {
+                    const float4 c2 = c.r2;
+#pragma unroll
+                    for (int g = 0; g < kScoreGPT; ++g) {
+                        const float z = fmaf(c2.x, p[g].mx, fmaf(c2.y, p[g].my, fmaf(c2.z, p[g].mz, c2.w)));
+                        part[g] += weight<NOPROJ>(z, eta);
+                    }
+                } else {
+                    mixed_view<NOPROJ, DET, COUNT>(c, eta, p, valid, part, cnt);
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < kScoreGPT; ++g) acc[g] += part[g];
+        }
     }
 }
 
-template <typename AT, int GPT, bool NOPROJ>
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+template <typename AT, bool NOPROJ, bool COUNT>
 __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -371,7 +698,7 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
         mbar_init(&bar, 1);
         mbar_expect_tx(&bar, bytes);
         for (uint32_t off = 0; off < bytes; off += 16384u) {
-            uint32_t len = bytes - off < 16384u ? bytes - off : 16384u;
+            const uint32_t len = bytes - off < 16384u ? bytes - off : 16384u;
             bulk_g2s(smem_raw + off, reinterpret_cast<const unsigned char *>(a.cams) + off, len, &bar);
         }
     }
@@ -382,20 +709,48 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
         return;
     }
 
-    const int64_t tile = (int64_t)blockDim.x * GPT;
-    for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile) {
-        float mx[GPT], my[GPT], mz[GPT], L[GPT][9], acc[GPT];
-        bool degen = false;
+    unsigned long long cnt[kCountSlots];
 #pragma unroll
-        for (int g = 0; g < GPT; ++g) {
-            const int64_t i = base + threadIdx.x + (int64_t)g * blockDim.x;
-            float ls0 = 0.f, ls1 = 0.f, ls2 = 0.f, qw = 1.f, qx = 0.f, qy = 0.f, qz = 0.f;
-            mx[g] = my[g] = mz[g] = 0.f;
+    for (int k = 0; k < kCountSlots; ++k) cnt[k] = 0;
+    const SceneConsts sc = *a.consts;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t tile = (int64_t)blockDim.x * kScoreGPT;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile) {
+        // pull the next tile's primitives towards L2 while this one computes
+        const int64_t nbase = base + (int64_t)gridDim.x * tile;
+#pragma unroll
+        for (int g = 0; g < kScoreGPT; ++g) {
+            const int64_t j = nbase + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
+            if (j < a.n) {
+                const int64_t i = __ldg(a.perm + j);
+                prefetch_l2(a.pos + i);
+                prefetch_l2(a.pos + S + i);
+                prefetch_l2(a.pos + 2 * S + i);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) prefetch_l2(attr + r * S + i);
+                prefetch_l2(a.m_col + i);
+            }
+        }
+        PairIn p[kScoreGPT];
+        float acc[kScoreGPT], alpha[kScoreGPT], mg[kScoreGPT];
+        int64_t idx[kScoreGPT];
+        bool valid[kScoreGPT];
+        bool degen = false;
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, b2 = 0.f;
+#pragma unroll
+        for (int g = 0; g < kScoreGPT; ++g) {
+            const int64_t j = base + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
+            float ls0 = 0.f, ls1 = 0.f, ls2 = 0.f, qw = 1.f, qx = 0.f, qy = 0.f, qz = 0.f, lg = 0.f;
+            p[g].mx = p[g].my = p[g].mz = 0.f;
+            idx[g] = -1;
             acc[g] = 0.f;
-            if (i < a.n) {
-                mx[g] = __ldg(a.pos + i);
-                my[g] = __ldg(a.pos + S + i);
-                mz[g] = __ldg(a.pos + 2 * S + i);
+            valid[g] = j < a.n;
+            if (valid[g]) {
+                const int64_t i = __ldg(a.perm + j);
+                idx[g] = i;
+                p[g].mx = __ldg(a.pos + i);
+                p[g].my = __ldg(a.pos + S + i);
+                p[g].mz = __ldg(a.pos + 2 * S + i);
                 ls0 = ld_attr(attr + i);
                 ls1 = ld_attr(attr + S + i);
                 ls2 = ld_attr(attr + 2 * S + i);
@@ -403,86 +758,118 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
                 qx = ld_attr(attr + 4 * S + i);
                 qy = ld_attr(attr + 5 * S + i);
                 qz = ld_attr(attr + 6 * S + i);
+                lg = ld_attr(attr + 7 * S + i);
                 if (!a.first) acc[g] = a.running[i];
-                float chk = fmaf(mx[g] + my[g] + mz[g] + ls0 + ls1 + ls2 + qw + qx + qy + qz, 0.f, 0.f);
-                if (!isfinite(chk)) set_status(a.status, kEnonfinite);
+                if (!isfinite(fmaf(qw + qx + qy + qz, 0.f, 0.f))) set_status(a.status, kEnonfinite);
             }
             const float qn2 = fmaf(qw, qw, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
             if (!(qn2 > 0.f)) {
-                if (i < a.n) set_status(a.status, kEinval);
+                if (valid[g]) set_status(a.status, kEinval);
                 qw = 1.f; qx = qy = qz = 0.f;
             } else {
                 const float r = rsqrtf(qn2);
                 qw *= r; qx *= r; qy *= r; qz *= r;
             }
-            const float s0 = 3.f * expf(ls0), s1 = 3.f * expf(ls1), s2 = 3.f * expf(ls2);
+            const float e0 = expf(ls0), e1 = expf(ls1), e2 = expf(ls2);
+            alpha[g] = 1.f / (1.f + expf(-lg));
+            mg[g] = fmaxf(fmaxf(e0 * e1, e0 * e2), e1 * e2);
+            const float s0 = 3.f * e0, s1 = 3.f * e1, s2 = 3.f * e2;
+            const float smax = fmaxf(s0, fmaxf(s1, s2));
+            p[g].b2 = smax * smax * 1.0009765625f;
             degen |= (s0 == 0.f) | (s1 == 0.f) | (s2 == 0.f);
-            // columns of R(q) scaled by 3 s_k form the rows of L
-            L[g][0] = s0 * (1.f - 2.f * (qy * qy + qz * qz));
-            L[g][1] = s0 * (2.f * (qx * qy + qw * qz));
-            L[g][2] = s0 * (2.f * (qx * qz - qw * qy));
-            L[g][3] = s1 * (2.f * (qx * qy - qw * qz));
-            L[g][4] = s1 * (1.f - 2.f * (qx * qx + qz * qz));
-            L[g][5] = s1 * (2.f * (qy * qz + qw * qx));
-            L[g][6] = s2 * (2.f * (qx * qz + qw * qy));
-            L[g][7] = s2 * (2.f * (qy * qz - qw * qx));
-            L[g][8] = s2 * (1.f - 2.f * (qx * qx + qy * qy));
+            // the rows of L are the columns of R(q) scaled by 3 s_k
+            p[g].L[0] = s0 * (1.f - 2.f * (qy * qy + qz * qz));
+            p[g].L[1] = s0 * (2.f * (qx * qy + qw * qz));
+            p[g].L[2] = s0 * (2.f * (qx * qz - qw * qy));
+            p[g].L[3] = s1 * (2.f * (qx * qy - qw * qz));
+            p[g].L[4] = s1 * (1.f - 2.f * (qx * qx + qz * qz));
+            p[g].L[5] = s1 * (2.f * (qy * qz + qw * qx));
+            p[g].L[6] = s2 * (2.f * (qx * qz + qw * qy));
+            p[g].L[7] = s2 * (2.f * (qy * qz - qw * qx));
+            p[g].L[8] = s2 * (1.f - 2.f * (qx * qx + qy * qy));
+            if (valid[g]) {
+                lo[0] = fminf(lo[0], p[g].mx); hi[0] = fmaxf(hi[0], p[g].mx);
+                lo[1] = fminf(lo[1], p[g].my); hi[1] = fmaxf(hi[1], p[g].my);
+                lo[2] = fminf(lo[2], p[g].mz); hi[2] = fmaxf(hi[2], p[g].mz);
+                b2 = fmaxf(b2, p[g].b2);
+            }
+        }
+        if (!__any_sync(0xffffffffu, valid[0])) continue;  // warp past the end
+
+        TileBox tb;
+        {
+            const float l0 = warp_min(lo[0]), l1 = warp_min(lo[1]), l2 = warp_min(lo[2]);
+            const float h0 = warp_max(hi[0]), h1 = warp_max(hi[1]), h2 = warp_max(hi[2]);
+            tb.b2 = warp_max(b2);
+            tb.cx = 0.5f * (l0 + h0); tb.hx = 0.5f * (h0 - l0);
+            tb.cy = 0.5f * (l1 + h1); tb.hy = 0.5f * (h1 - l1);
+            tb.cz = 0.5f * (l2 + h2); tb.hz = 0.5f * (h2 - l2);
+            tb.mx = fabsf(tb.cx) + tb.hx;
+            tb.my = fabsf(tb.cy) + tb.hy;
+            tb.mz = fabsf(tb.cz) + tb.hz;
         }
 
         if (__any_sync(0xffffffffu, degen))
-            view_loop<GPT, NOPROJ, true>(cs, a.vcount, a.eta, mx, my, mz, L, acc);
+            view_loop<NOPROJ, true, COUNT>(cs, a.vcount, a.eta, p, valid, tb, acc, cnt);
         else
-            view_loop<GPT, NOPROJ, false>(cs, a.vcount, a.eta, mx, my, mz, L, acc);
+            view_loop<NOPROJ, false, COUNT>(cs, a.vcount, a.eta, p, valid, tb, acc, cnt);
 
 #pragma unroll
-        for (int g = 0; g < GPT; ++g) {
-            const int64_t i = base + threadIdx.x + (int64_t)g * blockDim.x;
-            if (i >= a.n) continue;
+        for (int g = 0; g < kScoreGPT; ++g) {
+            const int64_t i = idx[g];
+            if (i < 0) continue;
             if (!a.last) {
                 a.running[i] = acc[g];
                 continue;
             }
             const float Ssum = acc[g];
             if (a.view_sum) a.view_sum[i] = Ssum;
-            const float e0 = expf(ld_attr(attr + i)), e1 = expf(ld_attr(attr + S + i)),
-                        e2 = expf(ld_attr(attr + 2 * S + i));
-            const float alpha = 1.f / (1.f + expf(-ld_attr(attr + 7 * S + i)));
-            const float mg = fmaxf(fmaxf(e0 * e1, e0 * e2), e1 * e2);
-            const SceneConsts c = *a.consts;
-            const float coupled = fmaf(c.kappa[0], mg, fmaf(c.kappa[1], a.m_col[i], c.kappa[2] * alpha));
-            const float A = ((a.flags & REFINE_FLAG_NO_VIS) ? 1.f : alpha) * (Ssum * a.inv_views);
+            const float coupled =
+                fmaf(sc.kappa[0], mg[g], fmaf(sc.kappa[1], __ldg(a.m_col + i), sc.kappa[2] * alpha[g]));
+            const float A = ((a.flags & REFINE_FLAG_NO_VIS) ? 1.f : alpha[g]) * (Ssum * a.inv_views);
             a.scores[i] = A * coupled;
+        }
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int k = 0; k < kCountSlots; ++k) {
+            unsigned long long v = cnt[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && v) atomicAdd(&a.need[k], v);
         }
     }
 }
 
-template <typename AT, int GPT, bool NOPROJ>
+template <typename AT, bool NOPROJ, bool COUNT>
 static const void *score_fn()
 {
-    return reinterpret_cast<const void *>(&k_score<AT, GPT, NOPROJ>);
+    return reinterpret_cast<const void *>(&k_score<AT, NOPROJ, COUNT>);
 }
 
-static const void *pick_score(int dtype, int gpt, bool noproj)
+static const void *pick_score(int dtype, bool noproj, bool count)
 {
     if (dtype == REFINE_BF16) {
-        if (gpt == 2) return noproj ? score_fn<__nv_bfloat16, 2, true>() : score_fn<__nv_bfloat16, 2, false>();
-        return noproj ? score_fn<__nv_bfloat16, 1, true>() : score_fn<__nv_bfloat16, 1, false>();
+        if (count) return noproj ? score_fn<__nv_bfloat16, true, true>() : score_fn<__nv_bfloat16, false, true>();
+        return noproj ? score_fn<__nv_bfloat16, true, false>() : score_fn<__nv_bfloat16, false, false>();
     }
-    if (gpt == 2) return noproj ? score_fn<float, 2, true>() : score_fn<float, 2, false>();
-    return noproj ? score_fn<float, 1, true>() : score_fn<float, 1, false>();
+    if (count) return noproj ? score_fn<float, true, true>() : score_fn<float, false, true>();
+    return noproj ? score_fn<float, true, false>() : score_fn<float, false, false>();
 }
 
-int score_grid(int num_sms, int64_t n, int vcount, int gpt)
+int score_grid(int num_sms, int64_t n, int vcount)
 {
-    // Persistent grid: as many CTAs as fit per SM (occupancy query), capped
-    // by the number of tiles.
+    // Persistent grid: as many CTAs as fit per SM, capped by the tile count.
     int per_sm = 0;
-    const void *fn = pick_score(REFINE_F32, gpt, false);
-    size_t smem = (size_t)vcount * sizeof(CamRec);
+    const size_t smem = (size_t)vcount * sizeof(CamRec);
+    const void *fn = pick_score(REFINE_F32, false, false);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kScoreThreads, smem) != cudaSuccess ||
-        per_sm < 1)
+        per_sm < 1) {
+        cudaGetLastError();
         per_sm = 1;
-    int64_t tiles = (n + (int64_t)kScoreThreads * gpt - 1) / ((int64_t)kScoreThreads * gpt);
+    }
+    const int64_t tiles = (n + (int64_t)kScoreThreads * kScoreGPT - 1) / ((int64_t)kScoreThreads * kScoreGPT);
     int64_t g = (int64_t)num_sms * per_sm;
     if (g > tiles) g = tiles;
     if (g < 1) g = 1;
@@ -491,10 +878,10 @@ int score_grid(int num_sms, int64_t n, int vcount, int gpt)
 
 cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s)
 {
-    const void *fn = pick_score(a.dtype, a.gpt, (a.flags & REFINE_FLAG_NO_PROJ) != 0);
-    size_t smem = (size_t)a.vcount * sizeof(CamRec);
+    const void *fn = pick_score(a.dtype, (a.flags & REFINE_FLAG_NO_PROJ) != 0, a.need != nullptr);
+    const size_t smem = (size_t)a.vcount * sizeof(CamRec);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     ScoreLaunch arg = a;

@@ -1,6 +1,7 @@
 // C ABI of librefine: argument validation, context scratch, launches.
 #include <math.h>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -16,6 +17,9 @@ enum KClass {
     K_CAM_PREP = 0,
     K_FEATURES,
     K_FEAT_FINAL,
+    K_CELLS,
+    K_CELL_SCAN,
+    K_CELL_SCATTER,
     K_SCORE,
     K_SEL_PASS,
     K_SEL_TIES,
@@ -25,9 +29,10 @@ enum KClass {
     K_CMP_SCATTER,
     K_NCLASS
 };
-const char *const kClassName[K_NCLASS] = {"cam_prep",    "features",  "features_finalize",
-                                          "score",       "select_pass", "select_ties",
-                                          "select_mask", "mask_fill", "compact_count",
+const char *const kClassName[K_NCLASS] = {"cam_prep",      "features",     "features_finalize",
+                                          "cells",         "cell_scan",    "cell_scatter",
+                                          "score",         "select_pass",  "select_ties",
+                                          "select_mask",   "mask_fill",    "compact_count",
                                           "compact_scatter"};
 
 struct Arena {
@@ -219,7 +224,7 @@ refine_status read_status(refine_ctx *c, cudaStream_t s)
 // ------------------------------------------------------------------ score
 refine_status score_impl(refine_ctx *c, const refine_scene *sc, const refine_camera *cams, int V,
                          const refine_params *pin, float *scores, float *view_sum, SceneStats **stats_dev,
-                         cudaStream_t s)
+                         unsigned long long **need_dev, cudaStream_t s)
 {
     refine_params p;
     if (pin) p = *pin; else refine_params_default(&p);
@@ -232,29 +237,50 @@ refine_status score_impl(refine_ctx *c, const refine_scene *sc, const refine_cam
     if (!scores) return fail(c, REFINE_EINVAL, "scores_dev is NULL");
     const int64_t n = sc->n;
     const bool multipass = V > kViewsPerPass;
-    const int nb = feature_blocks(n, sc->dtype);
+    const int nb = feature_blocks(n);
     size_t need = carve_size({sizeof(CamRec) * (size_t)V, sizeof(float) * (size_t)n,
                               sizeof(double) * kFeatSums * 1024, sizeof(SceneConsts), sizeof(SceneStats),
+                              sizeof(uint32_t) * (size_t)n, sizeof(unsigned) * (kCells + 64),
+                              sizeof(unsigned) * kCells, sizeof(unsigned) * kScanBlocks,
+                              sizeof(uint32_t) * (size_t)n, kCountSlots * sizeof(unsigned long long),
                               multipass ? sizeof(float) * (size_t)n : 0});
     if ((st = ensure(c, c->score, need))) return st;
     Carver cv(c->score.p);
-    CamRec *recs = cv.take<CamRec>(V);
+    CamRec *recs_cam = cv.take<CamRec>(V);
     float *m_col = cv.take<float>(n);
     double *partials = cv.take<double>(kFeatSums * 1024);
     SceneConsts *consts = cv.take<SceneConsts>(1);
     SceneStats *stats = cv.take<SceneStats>(1);
+    uint32_t *cell = cv.take<uint32_t>(n);
+    unsigned *counts = cv.take<unsigned>(kCells + 64);  // the last words hold the scan's done counter
+    unsigned *off_local = cv.take<unsigned>(kCells);
+    unsigned *bsum = cv.take<unsigned>(kScanBlocks);
+    uint32_t *perm = cv.take<uint32_t>(n);
+    unsigned long long *need_ctr = cv.take<unsigned long long>(kCountSlots);
     float *running = multipass ? cv.take<float>(n) : nullptr;
     if (stats_dev) *stats_dev = stats;
+    if (need_dev) *need_dev = need_ctr;
 
-    if ((st = launch(c, K_CAM_PREP, s, [&] { return launch_cam_prep(cams, V, recs, c->d_status, s); }))) return st;
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned) * (kCells + 64), s);
+    if (e == cudaSuccess && need_dev) e = cudaMemsetAsync(need_ctr, 0, kCountSlots * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+    if ((st = launch(c, K_CAM_PREP, s, [&] { return launch_cam_prep(cams, V, recs_cam, c->d_status, s); }))) return st;
     const bool vec = scene_vec_ok(sc);
     if ((st = launch(c, K_FEATURES, s, [&] {
-             return launch_features(sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, m_col, partials, vec,
-                                    c->d_status, s);
+             return launch_features(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, m_col, partials,
+                                    vec, c->d_status, s);
          })))
         return st;
     if ((st = launch(c, K_FEAT_FINAL, s,
                      [&] { return launch_features_finalize(partials, nb, n, &p, consts, stats, s); })))
+        return st;
+    if ((st = launch(c, K_CELLS, s,
+                     [&] { return launch_cells(sc->pos, sc->row_stride, n, consts, cell, counts, c->num_sms, s); })))
+        return st;
+    if ((st = launch(c, K_CELL_SCAN, s, [&] { return launch_cell_scan(counts, off_local, bsum, counts + kCells, s); })))
+        return st;
+    if ((st = launch(c, K_CELL_SCATTER, s,
+                     [&] { return launch_cell_scatter(cell, n, counts, off_local, bsum, perm, c->num_sms, s); })))
         return st;
     for (int v0 = 0; v0 < V; v0 += kViewsPerPass) {
         ScoreLaunch a;
@@ -262,8 +288,10 @@ refine_status score_impl(refine_ctx *c, const refine_scene *sc, const refine_cam
         a.attr = sc->attr;
         a.dtype = sc->dtype;
         a.stride = sc->row_stride;
+        a.perm = perm;
+        a.m_col = m_col;
         a.n = n;
-        a.cams = recs + v0;
+        a.cams = recs_cam + v0;
         a.vcount = V - v0 < kViewsPerPass ? V - v0 : kViewsPerPass;
         a.first = v0 == 0;
         a.last = v0 + a.vcount >= V;
@@ -271,13 +299,12 @@ refine_status score_impl(refine_ctx *c, const refine_scene *sc, const refine_cam
         a.inv_views = 1.0f / (float)V;
         a.flags = p.flags;
         a.consts = consts;
-        a.m_col = m_col;
         a.running = running;
         a.scores = scores;
         a.view_sum = view_sum;
+        a.need = need_dev ? need_ctr : nullptr;
         a.status = c->d_status;
-        a.gpt = c->score_gpt;
-        a.grid = score_grid(c->num_sms, n, a.vcount, a.gpt);
+        a.grid = score_grid(c->num_sms, n, a.vcount);
         if ((st = launch(c, K_SCORE, s, [&] { return launch_score(a, s); }))) return st;
     }
     return REFINE_OK;
@@ -460,19 +487,32 @@ refine_status refine_score_ex(refine_ctx *c, const refine_scene *scene, const re
     if (st) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     SceneStats *sd = nullptr;
-    if ((st = score_impl(c, scene, cams_dev, n_views, params, scores_dev, view_sum_dev, &sd, s))) return st;
+    unsigned long long *nd = nullptr;
+    if ((st = score_impl(c, scene, cams_dev, n_views, params, scores_dev, view_sum_dev, &sd,
+                         stats_out ? &nd : nullptr, s)))
+        return st;
     if (stats_out) {
+        memset(stats_out, 0, sizeof *stats_out);
         if (scene->n == 0) {
-            memset(stats_out, 0, sizeof *stats_out);
             for (int k = 0; k < 3; ++k) stats_out->lambda[k] = 1.0 / 3.0;
             return REFINE_OK;
         }
         SceneStats *h = reinterpret_cast<SceneStats *>(static_cast<char *>(c->h_small) + 256);
+        unsigned long long *hn = reinterpret_cast<unsigned long long *>(static_cast<char *>(c->h_small) + 1024);
         cudaError_t e = cudaMemcpyAsync(h, sd, sizeof(SceneStats), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hn, nd, kCountSlots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(c, e, "stats read-back");
         if ((st = read_status(c, s))) return st;
-        static_assert(sizeof(SceneStats) == sizeof(refine_scene_stats), "stats layout");
-        memcpy(stats_out, h, sizeof *stats_out);
+        static_assert(offsetof(refine_scene_stats, pairs) == sizeof(SceneStats), "stats layout");
+        memcpy(stats_out, h, sizeof(SceneStats));
+        stats_out->pairs = scene->n * (int64_t)n_views;
+        stats_out->tile_views = (int64_t)hn[kCntTiles];
+        stats_out->in_pairs = (int64_t)hn[kCntInPairs];
+        stats_out->out_pairs = (int64_t)hn[kCntOutPairs];
+        stats_out->mixed_pairs = (int64_t)hn[kCntMixedPairs];
+        stats_out->bound_pairs = (int64_t)hn[kCntBoundPairs];
+        stats_out->footprint_pairs = (int64_t)hn[kCntExactPairs];
     }
     return REFINE_OK;
 }
@@ -568,7 +608,7 @@ refine_status refine_prune_host(refine_ctx *c, int64_t n, int32_t dtype, const f
     sc.pos = d_pos;
     sc.attr = d_attr;
     sc.row_stride = n;
-    if ((st = score_impl(c, &sc, d_cams, n_views, params, d_scores, nullptr, nullptr, s))) return st;
+    if ((st = score_impl(c, &sc, d_cams, n_views, params, d_scores, nullptr, nullptr, nullptr, s))) return st;
     unsigned int *kd = nullptr;
     int64_t nk = 0;
     if ((st = select_impl(c, d_scores, n, ratio, d_mask, &kd, &nk, s))) return st;
