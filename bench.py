@@ -38,11 +38,11 @@ FP32_LANES_PER_SM = 128
 METRIC = "Gaussian×view pairs/s"
 
 
-def workload(name: str, rank: int = 0):
+def workload(name: str, rank: int = 0, storage: str = "f32"):
     from paper_2606_09074_gb300 import synth
     if name == "c2":
-        w = synth.config2(seed=replica_seed(2, rank))
-        w.name = "core-shell N=3.5M V=250 1600x1063, FP32, ratio 0.5"
+        w = synth.config2(seed=replica_seed(2, rank), dtype=storage)
+        w.name = f"core-shell N=3.5M V=250 1600x1063, {storage.upper()} storage, ratio 0.5"
     elif name == "c1":
         w = synth.config1(seed=replica_seed(1, rank))
         w.ratios = (0.5,)
@@ -234,16 +234,19 @@ def run_ours(args, rank: int, world: int):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
-    w = workload(args.workload, rank)
+    w = workload(args.workload, rank, args.storage)
     n, V, ratio = w.scene.n, len(w.cams), w.ratios[0]
     pos = torch.from_numpy(w.scene.pos).to(dev)
-    attr = torch.from_numpy(w.scene.attr).to(dev)
+    if w.scene.dtype == "bf16":
+        attr = torch.from_numpy(w.scene.attr.view(np.int16)).to(dev).view(torch.bfloat16)
+    else:
+        attr = torch.from_numpy(w.scene.attr).to(dev)
     cams = rb.cameras_to_device(w.cams, dev)
     n_keep = n - math.floor(ratio * n)
     scores = torch.empty(n, dtype=torch.float32, device=dev)
     mask = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
     out_pos = torch.empty((3, n_keep), dtype=torch.float32, device=dev)
-    out_attr = torch.empty((56, n_keep), dtype=torch.float32, device=dev)
+    out_attr = torch.empty((56, n_keep), dtype=attr.dtype, device=dev)
     kept = torch.empty(n_keep, dtype=torch.int32, device=dev)
     ctx = rb.Context(local)
     stream = torch.cuda.current_stream(dev)
@@ -311,9 +314,9 @@ def run_ours(args, rank: int, world: int):
         e2e = None
         if not args.no_e2e:
             pos_h = torch.from_numpy(w.scene.pos).pin_memory()
-            attr_h = torch.from_numpy(w.scene.attr).pin_memory()
+            attr_h = attr.cpu().pin_memory()
             outs = {"out_pos": torch.empty((3, n_keep), dtype=torch.float32, pin_memory=True),
-                    "out_attr": torch.empty((56, n_keep), dtype=torch.float32, pin_memory=True),
+                    "out_attr": torch.empty((56, n_keep), dtype=attr.dtype, pin_memory=True),
                     "idx": torch.empty(n_keep, dtype=torch.int32, pin_memory=True)}
             for _ in range(2):
                 ctx.prune_host(pos_h, attr_h, w.cams, ratio, out=outs, stream=stream)
@@ -322,8 +325,9 @@ def run_ours(args, rank: int, world: int):
             for _ in range(k_e2e):
                 ctx.prune_host(pos_h, attr_h, w.cams, ratio, out=outs, stream=stream)
             dt = (time.perf_counter() - t0) / k_e2e
-            e2e = {"value": pairs / dt, "unit": "pairs/s", "h2d_bytes_per_step": 12 * n + 224 * n + 80 * V,
-                   "d2h_bytes_per_step": (12 + 224 + 4) * n_keep + 4 + 4, "ms_per_step": dt * 1000,
+            asz = attr.element_size() * 56
+            e2e = {"value": pairs / dt, "unit": "pairs/s", "h2d_bytes_per_step": 12 * n + asz * n + 80 * V,
+                   "d2h_bytes_per_step": (12 + asz + 4) * n_keep + 4 + 4, "ms_per_step": dt * 1000,
                    "steps": k_e2e, "api": "refine_prune_host (pinned host buffers)"}
         cpu = None
         if not args.no_cpu_baseline:
@@ -333,23 +337,61 @@ def run_ours(args, rank: int, world: int):
             cpu = {"value": rate, "unit": "pairs/s", "cores": oracle.num_threads(), "kind": "oracle",
                    "sample": f"{m} of {n} primitives (seeded permutation) x all {V} views, "
                              f"score+select+compact, {dt:.1f} s"}
+        acc = accuracy_report(ctx, w, pos, attr, cams, ratio, stream) if args.accuracy else None
         lat = sorted(per_step)
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": w.name, "n": n, "views": V, "ratio": ratio, "storage": "f32",
+                "config": {"workload": w.name, "n": n, "views": V, "ratio": ratio, "storage": w.scene.dtype,
                            "l2": f"inputs larger than L2 ({(236 * n) / 1e6:.0f} MB scene), no flush",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "scenes_per_s": world * 1000.0 / ms_step,
                 "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clock_summary, "gpu": props.name}
+        if acc is not None:
+            line["accuracy"] = acc
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     ctx.close()
     return line
+
+
+def accuracy_report(ctx, w, pos, attr, cams, ratio, stream):
+    """Scores against the FP64 oracle: max / p99 relative error on a seeded
+    100k-primitive sample (statistics from the whole scene), against the same
+    stored numbers and, for BF16 storage, against the float32 scene they were
+    rounded from; and keep-mask agreement with the oracle's full-scene
+    selection on the float32 scene."""
+    import oracle
+    from paper_2606_09074_gb300 import synth
+    sc = ctx.score(pos, attr, cams, stream=stream)
+    mask, _, _ = ctx.select(sc, ratio, stream=stream)
+    s = sc.cpu().numpy().astype(np.float64)
+    got = np.unpackbits(mask.cpu().numpy().view(np.uint8), bitorder="little")[: w.scene.n].astype(bool)
+    oracle.set_threads(os.cpu_count() or 1)
+    idx = np.sort(np.random.default_rng(7).choice(w.scene.n, min(100_000, w.scene.n), replace=False))
+    rep = {"sample": int(idx.size)}
+
+    def rel(ref):
+        clean = (ref["nborder"] == 0) & (ref["scores"] > 0)
+        r = np.abs(s[idx][clean] - ref["scores"][clean]) / ref["scores"][clean]
+        return {"max": float(r.max()), "p99": float(np.quantile(r, 0.99)), "mean": float(r.mean()),
+                "checked": int(clean.sum())}
+
+    rep["vs_oracle_same_inputs"] = rel(oracle.score_subset(w.scene.params_f64(), idx, w.cams))
+    src = w.scene
+    if w.scene.dtype == "bf16":
+        src = synth.config2(seed=2, dtype="f32").scene
+        rep["vs_oracle_fp32_source"] = rel(oracle.score_subset(src.params_f64(), idx, w.cams))
+    ref = oracle.score(src.params_f64(), w.cams, detail=False)
+    m_ref, _, _ = oracle.select(ref["scores"], ratio)
+    want = np.unpackbits(m_ref.view(np.uint8), bitorder="little")[: w.scene.n].astype(bool)
+    rep["mask_agreement_vs_oracle"] = float((got == want).mean())
+    rep["mask_agreement_reference"] = "FP64 oracle on the float32 scene, full N"
+    return rep
 
 
 def main(argv=None):
@@ -361,6 +403,9 @@ def main(argv=None):
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--accuracy", action="store_true",
+                    help="also report error and mask agreement against the FP64 oracle")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -107,13 +107,19 @@ struct CmpState {
     unsigned int ok;
     long long total;
 };
-constexpr int kCmpSeg = 2048;  // elements per compaction segment (64 mask words)
+constexpr int kCmpSeg = 256;  // elements per compaction segment (8 mask words)
 cudaError_t launch_compact_count(const uint32_t *mask, int64_t n, unsigned *seg_cnt,
                                  unsigned long long *seg_off, CmpState *cs, int64_t out_stride,
                                  int grid, int *status, cudaStream_t s);
-cudaError_t launch_compact_scatter(const refine_scene &in, const uint32_t *mask,
-                                   const unsigned long long *seg_off, const CmpState *cs,
-                                   float *out_pos, void *out_attr, int64_t out_stride,
-                                   int32_t *out_idx, bool vec, int grid, cudaStream_t s);
+int compact_stream_blocks(int num_sms, int dtype);
+cudaError_t launch_compact_stream(const refine_scene &in, const uint32_t *mask, const unsigned long long *seg_off,
+                                  const CmpState *cs, float *out_pos, void *out_attr, int64_t out_stride,
+                                  int32_t *out_idx, bool tma, int grid, int *status, cudaStream_t s);
+
+// TMA-fed feature pass (rows 16-byte aligned); same sums as launch_features.
+int feature_tma_blocks(int num_sms, int dtype);
+cudaError_t launch_features_tma(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
+                                float eta, const float luma[3], float *m_col, double *partials, int nblocks,
+                                int *status, cudaStream_t s);
 
 }  // namespace refine

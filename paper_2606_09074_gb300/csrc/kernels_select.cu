@@ -318,11 +318,12 @@ cudaError_t launch_mask_fill(uint32_t *mask, int64_t n, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------
-// Compaction.  Segment s covers elements [s*kCmpSeg, (s+1)*kCmpSeg), i.e.
-// 64 mask words.  Pass 1 counts kept elements per segment and the last CTA
-// turns the counts into exclusive offsets; pass 2 scatters every row.
+// Compaction, pass 1.  Segment s covers elements [s*kCmpSeg, (s+1)*kCmpSeg)
+// (8 mask words).  Kept elements are counted per segment and the last CTA
+// turns the counts into exclusive offsets; the scatter of every row is
+// k_compact_stream.
 // ---------------------------------------------------------------------
-constexpr int kCmpThreads = 256;
+constexpr int kCmpThreads = 1024;
 
 __global__ void __launch_bounds__(kCmpThreads) k_compact_count(const uint32_t *__restrict__ mask, int64_t n,
                                                                unsigned *seg_cnt, unsigned long long *seg_off,
@@ -332,17 +333,21 @@ __global__ void __launch_bounds__(kCmpThreads) k_compact_count(const uint32_t *_
     __shared__ unsigned int is_last;
     const int64_t words = (n + 31) / 32;
     const int64_t nseg = (n + kCmpSeg - 1) / kCmpSeg;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t sg = warp0; sg < nseg; sg += nwarps) {
-        unsigned int c = 0;
-        for (int k = lane; k < kCmpSeg / 32; k += 32) {
-            const int64_t w = sg * (kCmpSeg / 32) + k;
-            if (w < words) c += __popc(__ldg(mask + w));
+    constexpr int kWords = kCmpSeg / 32;
+    for (int64_t sg = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; sg < nseg;
+         sg += (int64_t)gridDim.x * blockDim.x) {
+        unsigned c = 0;
+#pragma unroll
+        for (int k = 0; k < kWords; ++k) {
+            const int64_t w = sg * kWords + k;
+            if (w < words) {
+                uint32_t word = __ldg(mask + w);
+                const int64_t valid = n - w * 32;  // bits past n do not count
+                if (valid < 32) word &= (1u << valid) - 1u;
+                c += __popc(word);
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-        if (lane == 0) seg_cnt[sg] = c;
+        seg_cnt[sg] = c;
     }
     __threadfence();
     __syncthreads();
@@ -375,103 +380,6 @@ cudaError_t launch_compact_count(const uint32_t *mask, int64_t n, unsigned *seg_
                                  int grid, int *status, cudaStream_t s)
 {
     k_compact_count<<<grid, kCmpThreads, 0, s>>>(mask, n, seg_cnt, seg_off, cs, out_stride, status);
-    return cudaGetLastError();
-}
-
-// Thread t of a segment owns elements 8t .. 8t+7 (mask byte t of the
-// segment).  Its output slot is the segment offset plus the popcount of the
-// segment's mask bytes before its own (block scan).
-template <typename T>
-__device__ __forceinline__ void gather8(const T *__restrict__ row, int64_t e0, int64_t n, bool vec,
-                                        T (&v)[8])
-{
-    if (vec && e0 + 8 <= n) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(row + e0);
-        if (sizeof(T) == 4) {
-            uint4 q0 = __ldg(p), q1 = __ldg(p + 1);
-            uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-#pragma unroll
-            for (int k = 0; k < 8; ++k) memcpy(&v[k], &w[k], 4);
-        } else {
-            uint4 q = __ldg(p);
-            uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint16_t lo = (uint16_t)(w[k] & 0xffffu), hi = (uint16_t)(w[k] >> 16);
-                memcpy(&v[2 * k], &lo, 2);
-                memcpy(&v[2 * k + 1], &hi, 2);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (e0 + k < n) v[k] = row[e0 + k];
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void put_kept(T *__restrict__ out, unsigned long long slot, uint32_t bits,
-                                         const T (&v)[8])
-{
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        if (bits & (1u << k)) out[slot++] = v[k];
-    }
-}
-
-template <typename AT>
-__global__ void __launch_bounds__(kCmpThreads) k_compact_scatter(
-    const float *__restrict__ pos, const AT *__restrict__ attr, int64_t stride, int64_t n,
-    const uint32_t *__restrict__ mask, const unsigned long long *__restrict__ seg_off, const CmpState *cs,
-    float *__restrict__ out_pos, AT *__restrict__ out_attr, int64_t out_stride, int32_t *__restrict__ out_idx,
-    bool vec)
-{
-    __shared__ unsigned long long wsum[32];
-    if (!cs->ok) return;
-    const int64_t nseg = (n + kCmpSeg - 1) / kCmpSeg;
-    const int64_t words = (n + 31) / 32;
-    for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
-        const int64_t w = sg * (kCmpSeg / 32) + (threadIdx.x >> 2);
-        const uint32_t word = w < words ? __ldg(mask + w) : 0u;
-        const uint32_t bits = (word >> ((threadIdx.x & 3) * 8)) & 0xffu;
-        const unsigned long long incl = block_prefix_sum((unsigned long long)__popc(bits), wsum);
-        const unsigned long long slot = seg_off[sg] + incl - __popc(bits);
-        const int64_t e0 = sg * (int64_t)kCmpSeg + 8 * (int64_t)threadIdx.x;
-        if (bits == 0u) continue;
-        if (out_idx) {
-            unsigned long long sl = slot;
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (bits & (1u << k)) out_idx[sl++] = (int32_t)(e0 + k);
-        }
-#pragma unroll 1
-        for (int r = 0; r < 3; ++r) {
-            float v[8];
-            gather8<float>(pos + r * stride, e0, n, vec, v);
-            put_kept<float>(out_pos + r * out_stride, slot, bits, v);
-        }
-#pragma unroll 2
-        for (int r = 0; r < 56; ++r) {
-            AT v[8];
-            gather8<AT>(attr + r * stride, e0, n, vec, v);
-            put_kept<AT>(out_attr + r * out_stride, slot, bits, v);
-        }
-    }
-}
-
-cudaError_t launch_compact_scatter(const refine_scene &in, const uint32_t *mask,
-                                   const unsigned long long *seg_off, const CmpState *cs,
-                                   float *out_pos, void *out_attr, int64_t out_stride,
-                                   int32_t *out_idx, bool vec, int grid, cudaStream_t s)
-{
-    if (in.dtype == REFINE_BF16)
-        k_compact_scatter<__nv_bfloat16><<<grid, kCmpThreads, 0, s>>>(
-            in.pos, static_cast<const __nv_bfloat16 *>(in.attr), in.row_stride, in.n, mask, seg_off, cs,
-            out_pos, static_cast<__nv_bfloat16 *>(out_attr), out_stride, out_idx, vec);
-    else
-        k_compact_scatter<float><<<grid, kCmpThreads, 0, s>>>(
-            in.pos, static_cast<const float *>(in.attr), in.row_stride, in.n, mask, seg_off, cs, out_pos,
-            static_cast<float *>(out_attr), out_stride, out_idx, vec);
     return cudaGetLastError();
 }
 

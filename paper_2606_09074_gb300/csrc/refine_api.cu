@@ -237,7 +237,13 @@ refine_status score_impl(refine_ctx *c, const refine_scene *sc, const refine_cam
     if (!scores) return fail(c, REFINE_EINVAL, "scores_dev is NULL");
     const int64_t n = sc->n;
     const bool multipass = V > kViewsPerPass;
-    const int nb = feature_blocks(n);
+    const bool vec = scene_vec_ok(sc);
+    int nb = feature_blocks(n);
+    if (vec) {
+        const int64_t chunks = n / 256 + 1;
+        nb = feature_tma_blocks(c->num_sms, sc->dtype);
+        if (nb > chunks) nb = (int)chunks;
+    }
     size_t need = carve_size({sizeof(CamRec) * (size_t)V, sizeof(float) * (size_t)n,
                               sizeof(double) * kFeatSums * 1024, sizeof(SceneConsts), sizeof(SceneStats),
                               sizeof(uint32_t) * (size_t)n, sizeof(unsigned) * (kCells + 64),
@@ -265,10 +271,12 @@ refine_status score_impl(refine_ctx *c, const refine_scene *sc, const refine_cam
     if (e == cudaSuccess && need_dev) e = cudaMemsetAsync(need_ctr, 0, kCountSlots * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
     if ((st = launch(c, K_CAM_PREP, s, [&] { return launch_cam_prep(cams, V, recs_cam, c->d_status, s); }))) return st;
-    const bool vec = scene_vec_ok(sc);
     if ((st = launch(c, K_FEATURES, s, [&] {
+             if (vec)
+                 return launch_features_tma(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, m_col,
+                                            partials, nb, c->d_status, s);
              return launch_features(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, m_col, partials,
-                                    vec, c->d_status, s);
+                                    false, c->d_status, s);
          })))
         return st;
     if ((st = launch(c, K_FEAT_FINAL, s,
@@ -382,18 +390,19 @@ refine_status compact_impl(refine_ctx *c, const refine_scene *in, const uint32_t
     unsigned long long *seg_off = cv.take<unsigned long long>(nseg);
     cudaError_t e = cudaMemsetAsync(cs, 0, sizeof(CmpState), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
-    int64_t cgrid = (nseg + 7) / 8;
-    if (cgrid > 2 * c->num_sms) cgrid = 2 * c->num_sms;
+    int64_t cgrid = (nseg + 1023) / 1024;
+    if (cgrid > c->num_sms) cgrid = c->num_sms;
     if (cgrid < 1) cgrid = 1;
     if ((st = launch(c, K_CMP_COUNT, s, [&] {
              return launch_compact_count(mask, n, seg_cnt, seg_off, cs, out_stride, (int)cgrid, c->d_status, s);
          })))
         return st;
-    int64_t sgrid = nseg < (int64_t)c->num_sms * 8 ? nseg : (int64_t)c->num_sms * 8;
-    const bool vec = scene_vec_ok(in);
+    const bool tma = scene_vec_ok(in);
+    int64_t sgrid = tma ? compact_stream_blocks(c->num_sms, in->dtype) : (int64_t)c->num_sms * 4;
+    if (sgrid > nseg) sgrid = nseg;
     if ((st = launch(c, K_CMP_SCATTER, s, [&] {
-             return launch_compact_scatter(*in, mask, seg_off, cs, out_pos, out_attr, out_stride, idx, vec,
-                                           (int)sgrid, s);
+             return launch_compact_stream(*in, mask, seg_off, cs, out_pos, out_attr, out_stride, idx, tma,
+                                          (int)sgrid, c->d_status, s);
          })))
         return st;
     *total_dev = &cs->total;
