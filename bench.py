@@ -394,6 +394,89 @@ def accuracy_report(ctx, w, pos, attr, cams, ratio, stream):
     return rep
 
 
+def run_batch_mode(args):
+    """64 scenes (seeds 100..163: N log-uniform in [50k, 2M], V in 50..300,
+    three resolutions, ratio 0.66): the batched BF16 form against per-scene
+    calls of the plain path (FP32, and BF16 for reference)."""
+    import torch
+    from paper_2606_09074_gb300 import binding as rb
+    from paper_2606_09074_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    seeds = list(range(100, 100 + args.scenes))
+    scenes = []
+    for sd in seeds:
+        w = synth.batch_scene(sd, dtype="f32")
+        pos = torch.from_numpy(w.scene.pos).to(dev)
+        a32 = torch.from_numpy(w.scene.attr).to(dev)
+        a16 = torch.from_numpy(synth.f32_to_bf16_bits(w.scene.attr).view(np.int16)).to(dev).view(torch.bfloat16)
+        scenes.append({"pos": pos, "a32": a32, "a16": a16, "cams": rb.cameras_to_device(w.cams, dev),
+                       "n": w.scene.n, "V": len(w.cams), "ratio": 0.66})
+    pairs = sum(x["n"] * x["V"] for x in scenes)
+    ctx = rb.Context(0)
+    stream = torch.cuda.current_stream(dev)
+
+    def plain(key):
+        outs = []
+        for x in scenes:
+            nk = x["n"] - math.floor(x["ratio"] * x["n"])
+            outs.append({"scores": torch.empty(x["n"], device=dev),
+                         "mask": torch.empty((x["n"] + 31) // 32, dtype=torch.int32, device=dev),
+                         "op": torch.empty((3, nk), device=dev),
+                         "oa": torch.empty((56, nk), dtype=x[key].dtype, device=dev), "nk": nk})
+
+        def step():
+            for x, o in zip(scenes, outs):
+                ctx.score(x["pos"], x[key], x["cams"], scores=o["scores"], stream=stream)
+                ctx.select(o["scores"], x["ratio"], mask=o["mask"], threshold=False, stream=stream)
+                ctx.compact(x["pos"], x[key], o["mask"], o["nk"], out_pos=o["op"], out_attr=o["oa"],
+                            kept_idx=False, out_row_stride=o["nk"], stream=stream)
+        return step
+
+    def timed(step, k):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(k):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / k, (time.perf_counter() - t0) * 1000 / k
+
+    res = {}
+    for key, name in (("a32", "plain_f32"), ("a16", "plain_bf16")):
+        dev_ms, wall_ms = timed(plain(key), args.batch_steps)
+        res[name] = {"ms_per_batch": dev_ms, "wall_ms_per_batch": wall_ms,
+                     "scenes_per_s": len(scenes) * 1000 / wall_ms, "pairs_per_s": pairs * 1000 / wall_ms}
+    batch = rb.Batch(ctx, [{"pos": x["pos"], "attr": x["a16"], "cams": x["cams"], "ratio": x["ratio"]}
+                           for x in scenes])
+    dev_ms, wall_ms = timed(lambda: batch.run(stream), args.batch_steps)
+    res["batched_bf16"] = {"ms_per_batch": dev_ms, "wall_ms_per_batch": wall_ms,
+                           "scenes_per_s": len(scenes) * 1000 / wall_ms, "pairs_per_s": pairs * 1000 / wall_ms,
+                           "kernels_per_run": batch.launches()}
+    # the batched scores equal the per-scene BF16 path bit for bit
+    plain(key="a16")  # allocate nothing new; check a few scenes directly
+    same = True
+    for k in (0, len(scenes) // 2, len(scenes) - 1):
+        x = scenes[k]
+        s = ctx.score(x["pos"], x["a16"], x["cams"])
+        same &= bool(torch.equal(s, batch.outputs[k]["scores"]))
+    ctx.check()
+    line = {"mode": "batch", "metric": "scenes/s", "value": res["batched_bf16"]["scenes_per_s"],
+            "unit": "scenes/s", "n_gpus": 1, "steps": args.batch_steps, "warmup": args.warmup,
+            "scenes": len(scenes), "pairs_per_batch": pairs, "primitives": sum(x["n"] for x in scenes),
+            "speedup_vs_plain_f32": res["plain_f32"]["wall_ms_per_batch"] / res["batched_bf16"]["wall_ms_per_batch"],
+            "speedup_vs_plain_bf16": res["plain_bf16"]["wall_ms_per_batch"] / res["batched_bf16"]["wall_ms_per_batch"],
+            "batched_scores_equal_plain": same, "results": res, "data": "synthetic",
+            "config": {"workload": "64 scenes, seeds 100-163, N log-uniform 50k-2M, V 50-300, ratio 0.66"}}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    ctx.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,6 +487,10 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--mode", default="single", choices=["single", "batch"],
+                    help="single: the default workload; batch: 64 scenes, batched vs per-scene")
+    ap.add_argument("--scenes", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--accuracy", action="store_true",
                     help="also report error and mask agreement against the FP64 oracle")
     args = ap.parse_args(argv)
@@ -413,6 +500,8 @@ def main(argv=None):
     world = int(os.environ.get("WORLD_SIZE", str(1)))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "batch":
+        run_batch_mode(args)
     else:
         run_ours(args, rank, world)
 

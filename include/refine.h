@@ -228,6 +228,57 @@ refine_status refine_prune_host(refine_ctx *ctx, int64_t n, int32_t dtype,
                                 int64_t *n_keep_out, float *threshold_out,
                                 refine_stream_t stream);
 
+/* ------------------------------------------------------------ batches
+ * Many scenes in one go: per-scene preparation (content features, lambda,
+ * processing order) and per-scene selection and compaction run on parallel
+ * streams, and all scenes are scored by ONE persistent kernel launch over a
+ * (scene, tile) work list.  The whole batch is captured into a CUDA graph
+ * on its first run and replayed afterwards, so a run costs one graph launch.
+ * Scores, masks and compacted outputs are bit-identical to the per-scene
+ * entry points. */
+
+/* One scene of a batch; every pointer is device memory owned by the caller
+ * and must stay valid (and unchanged in address) for the batch's life. */
+typedef struct refine_job {
+    refine_scene scene;            /* primitives (see refine_scene)                      */
+    const refine_camera *cams_dev; /* n_views camera records                             */
+    int32_t n_views;               /* 1 .. 512 in a batch                                */
+    int32_t reserved;
+    double ratio;                  /* pruning ratio in [0, 1)                             */
+    float *scores_dev;             /* [n] written                                         */
+    uint32_t *keep_mask_dev;       /* [ceil(n/32)] written                                */
+    float *out_pos_dev;            /* [3][out_row_stride] or NULL to skip compaction      */
+    void *out_attr_dev;            /* [56][out_row_stride] in scene.dtype                 */
+    int64_t out_row_stride;        /* >= n - floor(ratio n)                               */
+    int32_t *kept_idx_dev;         /* [n_keep] or NULL                                    */
+} refine_job;
+
+typedef struct refine_batch refine_batch;
+
+/* Builds a batch of n_jobs scenes (1 <= n_jobs <= 4096, one storage dtype,
+ * n >= 1 each, n_views <= 512 each; the jobs array is copied).  Allocates
+ * all scratch up front (released by refine_batch_destroy).  EINVAL on a bad
+ * job (refine_last_error(ctx) names it), ENOMEM if the scratch does not fit. */
+refine_status refine_batch_create(refine_ctx *ctx, const refine_job *jobs, int32_t n_jobs,
+                                  const refine_params *params, refine_batch **out);
+
+/* Enqueues a run of the whole batch on `stream` (asynchronous).  The first
+ * run records the CUDA graph (it must not be called while `stream` is being
+ * captured); later runs launch it. */
+refine_status refine_batch_run(refine_batch *batch, refine_stream_t stream);
+
+/* Synchronises `stream` and returns, per job, the kept count and the
+ * threshold of the last run (either pointer may be NULL), plus any device
+ * error recorded since the last check. */
+refine_status refine_batch_results(refine_batch *batch, int64_t *n_keep_out, float *threshold_out,
+                                   refine_stream_t stream);
+
+/* Number of kernels one run launches. */
+int64_t refine_batch_launches(const refine_batch *batch);
+
+/* Releases the batch (synchronising its device first).  NULL is a no-op. */
+void refine_batch_destroy(refine_batch *batch);
+
 /* Ratio pruning without any allocation.  The paper has no counterpart; this
  * entry point exists for callers that cannot allocate device memory -- code
  * recording a CUDA graph that must not contain allocation nodes, plug-ins

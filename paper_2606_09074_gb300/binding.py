@@ -79,7 +79,14 @@ class refine_scene_stats(C.Structure):
                 "bound_pairs": self.bound_pairs, "footprint_pairs": self.footprint_pairs}
 
 
-assert C.sizeof(refine_camera) == 80 and C.sizeof(refine_scene) == 40
+class refine_job(C.Structure):
+    _fields_ = [("scene", refine_scene), ("cams_dev", C.c_void_p), ("n_views", C.c_int32),
+                ("reserved", C.c_int32), ("ratio", C.c_double), ("scores_dev", C.c_void_p),
+                ("keep_mask_dev", C.c_void_p), ("out_pos_dev", C.c_void_p), ("out_attr_dev", C.c_void_p),
+                ("out_row_stride", C.c_int64), ("kept_idx_dev", C.c_void_p)]
+
+
+assert C.sizeof(refine_camera) == 80 and C.sizeof(refine_scene) == 40 and C.sizeof(refine_job) == 112
 assert C.sizeof(refine_params) == 48
 
 _P = C.c_void_p
@@ -102,6 +109,12 @@ _SIGNATURES = {
                                     C.POINTER(C.c_int64), C.POINTER(C.c_float), _P]),
     "refine_select_noalloc": (C.c_int, [_P, C.c_int64, C.c_double, _P, C.POINTER(C.c_float),
                                         C.POINTER(C.c_int64), C.c_char_p, C.c_size_t, _P]),
+    "refine_batch_create": (C.c_int, [_P, C.POINTER(refine_job), C.c_int32, C.POINTER(refine_params),
+                                      C.POINTER(C.c_void_p)]),
+    "refine_batch_run": (C.c_int, [_P, _P]),
+    "refine_batch_results": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_float), _P]),
+    "refine_batch_launches": (C.c_int64, [_P]),
+    "refine_batch_destroy": (None, [_P]),
     "refine_ctx_check": (C.c_int, [_P, _P]),
     "refine_ctx_set_timing": (C.c_int, [_P, C.c_int]),
     "refine_ctx_kernel_times": (C.c_int, [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -320,3 +333,73 @@ class Context:
 
     def launch_count(self) -> int:
         return int(refine_ctx_launch_count(self.handle))  # noqa: F821
+
+
+class Batch:
+    """A batch of scenes scored by one persistent launch and replayed as a
+    CUDA graph (refine_batch_*).  ``jobs`` is a list of dicts with device
+    tensors: pos, attr, cams, ratio and optionally ``compact=False``.  The
+    batch allocates scores, masks and compaction outputs and keeps every
+    tensor alive for its lifetime."""
+
+    def __init__(self, ctx: Context, jobs, params=None, compact=True):
+        import torch
+        self.ctx = ctx
+        self.keep = []
+        self.outputs = []
+        arr = (refine_job * len(jobs))()
+        for k, jd in enumerate(jobs):
+            pos, attr, cams = jd["pos"], jd["attr"], jd["cams"]
+            n = pos.shape[1]
+            ratio = float(jd["ratio"])
+            n_keep = n - int(np.floor(ratio * n))
+            out = {"scores": torch.empty(n, dtype=torch.float32, device=ctx.device),
+                   "mask": torch.empty((n + 31) // 32, dtype=torch.int32, device=ctx.device)}
+            j = arr[k]
+            j.scene = make_scene(pos, attr)
+            j.cams_dev = cams.data_ptr()
+            j.n_views = cams.numel() // 80
+            j.ratio = ratio
+            j.scores_dev = out["scores"].data_ptr()
+            j.keep_mask_dev = out["mask"].data_ptr()
+            if compact and jd.get("compact", True):
+                out["out_pos"] = torch.empty((3, max(n_keep, 1)), dtype=torch.float32, device=ctx.device)
+                out["out_attr"] = torch.empty((56, max(n_keep, 1)), dtype=attr.dtype, device=ctx.device)
+                out["idx"] = torch.empty(max(n_keep, 1), dtype=torch.int32, device=ctx.device)
+                j.out_pos_dev = out["out_pos"].data_ptr()
+                j.out_attr_dev = out["out_attr"].data_ptr()
+                j.out_row_stride = max(n_keep, 1)
+                j.kept_idx_dev = out["idx"].data_ptr()
+            out["n_keep"] = n_keep
+            self.outputs.append(out)
+            self.keep.append((pos, attr, cams))
+        self.n = len(jobs)
+        h = C.c_void_p()
+        rc = refine_batch_create(ctx.handle, arr, len(jobs), C.byref(params) if params is not None else None,  # noqa: F821
+                                 C.byref(h))
+        _check(ctx.handle, rc)
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(self.ctx.handle, refine_batch_run(self.handle, _stream_handle(stream, self.ctx.device)))  # noqa: F821
+
+    def results(self, stream=None):
+        nk = (C.c_int64 * self.n)()
+        thr = (C.c_float * self.n)()
+        _check(self.ctx.handle, refine_batch_results(self.handle, nk, thr,  # noqa: F821
+                                                     _stream_handle(stream, self.ctx.device)))
+        return list(nk), list(thr)
+
+    def launches(self) -> int:
+        return int(refine_batch_launches(self.handle))  # noqa: F821
+
+    def close(self):
+        if self.handle:
+            refine_batch_destroy(self.handle)  # noqa: F821
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

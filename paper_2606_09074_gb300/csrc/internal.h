@@ -18,12 +18,20 @@ constexpr int kScoreThreads = 256;
 constexpr int kScoreGPT = 2;          // primitives per thread in k_score
 constexpr int kFeatThreads = 256;
 
-// Spatial cells for the processing order of k_score: a 128^3 grid over the
-// scene's mean +- 3 sigma box, numbered in Morton order.
-constexpr int kCellBits = 7;
-constexpr int kCells = 1 << (3 * kCellBits);
+// Spatial cells for the processing order of k_score: a 2^b x 2^b x 2^b grid
+// over the scene's mean +- 3 sigma box, numbered in Morton order, with b
+// chosen from n (cell_bits_for) between 4 and kMaxCellBits.
+constexpr int kMinCellBits = 4;
+constexpr int kMaxCellBits = 7;
+constexpr int kMaxCells = 1 << (3 * kMaxCellBits);
 constexpr int kScanThreads = 1024;
-constexpr int kScanBlocks = kCells / kScanThreads;
+inline int cell_bits_for(int64_t n)
+{
+    int b = 4;
+    while (b < kMaxCellBits && (int64_t(1) << (3 * (b + 1))) * 16 <= n * 2) ++b;  // ~16-32 per cell
+    return b;
+}
+inline int cell_count(int bits) { return 1 << (3 * bits); }
 
 // Diagnostic counters of k_score (written only when ScoreLaunch::need is set).
 enum {
@@ -66,17 +74,31 @@ cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64
                             float eta, const float luma[3], float *m_col, double *partials, bool vec,
                             int *status, cudaStream_t s);
 cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_t n,
-                                     const refine_params *p, SceneConsts *consts,
+                                     const refine_params *p, int cell_bits, SceneConsts *consts,
                                      SceneStats *stats, cudaStream_t s);
-cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, const SceneConsts *consts,
+cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, int cell_bits, const SceneConsts *consts,
                          uint32_t *cell, unsigned *counts, int num_sms, cudaStream_t s);
-cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done,
+cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done, int cell_bits,
                              cudaStream_t s);
 cudaError_t launch_cell_scatter(const uint32_t *cell, int64_t n, unsigned *counts,
                                 const unsigned *off_local, const unsigned *bsum, uint32_t *perm,
                                 int num_sms, cudaStream_t s);
 cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s);
 int score_grid(int num_sms, int64_t n, int vcount);
+
+// Batched score launch over the tiles of many scenes (each scene a single
+// pass of at most kViewsPerPass views, one storage type per batch).
+struct BatchLaunch {
+    const ScoreLaunch *scenes;       // device [n_scenes]
+    const long long *tile_begin;     // device [n_scenes + 1], first tile of each scene
+    int n_scenes;
+    long long total_tiles;
+    unsigned long long *counter;     // device, zero before the launch
+    int *status;
+};
+int score_batch_grid(int num_sms, int dtype, bool noproj, int max_vcount);
+cudaError_t launch_score_batch(const BatchLaunch &b, int dtype, bool noproj, int max_vcount, int grid,
+                               cudaStream_t s);
 
 // ------------------------------------------------------------- select
 struct SelState {

@@ -238,7 +238,7 @@ cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64
 // Eq. (features) -> Eq. 18 -> Eq. 19 in double, one block; also the grid box
 // (mean +- 3 sigma of the means) of the processing order.
 __global__ void k_features_finalize(const double *__restrict__ partials, int nblocks, int64_t n,
-                                    refine_params p, SceneConsts *consts, SceneStats *stats)
+                                    refine_params p, int cell_bits, SceneConsts *consts, SceneStats *stats)
 {
     __shared__ double red[kFeatSums][256];
     double loc[kFeatSums];
@@ -283,7 +283,7 @@ __global__ void k_features_finalize(const double *__restrict__ partials, int nbl
         double var = red[10 + k][0] / N - mean * mean;
         const double sd = var > 0.0 ? sqrt(var) : 0.0;
         c.lo[k] = (float)(mean - 3.0 * sd);
-        c.qscale[k] = sd > 0.0 && isfinite(sd) ? (float)((1 << kCellBits) / (6.0 * sd)) : 0.f;
+        c.qscale[k] = sd > 0.0 && isfinite(sd) ? (float)((1 << cell_bits) / (6.0 * sd)) : 0.f;
         c.pad[k] = 0.f;
     }
     *consts = c;
@@ -291,10 +291,10 @@ __global__ void k_features_finalize(const double *__restrict__ partials, int nbl
 }
 
 cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_t n,
-                                     const refine_params *p, SceneConsts *consts,
+                                     const refine_params *p, int cell_bits, SceneConsts *consts,
                                      SceneStats *stats, cudaStream_t s)
 {
-    k_features_finalize<<<1, 256, 0, s>>>(partials, nblocks, n, *p, consts, stats);
+    k_features_finalize<<<1, 256, 0, s>>>(partials, nblocks, n, *p, cell_bits, consts, stats);
     return cudaGetLastError();
 }
 
@@ -309,37 +309,37 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x)
 {
     uint32_t r = 0;
 #pragma unroll
-    for (int b = 0; b < kCellBits; ++b) r |= ((x >> b) & 1u) << (3 * b);
+    for (int b = 0; b < kMaxCellBits; ++b) r |= ((x >> b) & 1u) << (3 * b);
     return r;
 }
 
-__device__ __forceinline__ uint32_t quantise(float x, float lo, float qs)
+__device__ __forceinline__ uint32_t quantise(float x, float lo, float qs, float top)
 {
-    const float q = fminf(fmaxf((x - lo) * qs, 0.f), (float)((1 << kCellBits) - 1));
-    return (uint32_t)q;
+    return (uint32_t)fminf(fmaxf((x - lo) * qs, 0.f), top);
 }
 
-__global__ void k_cells(const float *__restrict__ pos, int64_t stride, int64_t n,
+__global__ void k_cells(const float *__restrict__ pos, int64_t stride, int64_t n, int cell_bits,
                         const SceneConsts *__restrict__ consts, uint32_t *__restrict__ cell,
                         unsigned *__restrict__ counts)
 {
     const SceneConsts c = *consts;
+    const float top = (float)((1 << cell_bits) - 1);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t id = spread3(quantise(__ldg(pos + i), c.lo[0], c.qscale[0])) |
-                            (spread3(quantise(__ldg(pos + stride + i), c.lo[1], c.qscale[1])) << 1) |
-                            (spread3(quantise(__ldg(pos + 2 * stride + i), c.lo[2], c.qscale[2])) << 2);
+        const uint32_t id = spread3(quantise(__ldg(pos + i), c.lo[0], c.qscale[0], top)) |
+                            (spread3(quantise(__ldg(pos + stride + i), c.lo[1], c.qscale[1], top)) << 1) |
+                            (spread3(quantise(__ldg(pos + 2 * stride + i), c.lo[2], c.qscale[2], top)) << 2);
         cell[i] = id;
         atomicAdd(&counts[id], 1u);
     }
 }
 
-cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, const SceneConsts *consts,
+cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, int cell_bits, const SceneConsts *consts,
                          uint32_t *cell, unsigned *counts, int num_sms, cudaStream_t s)
 {
     int64_t g = (n + 255) / 256;
     if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
     if (g < 1) g = 1;
-    k_cells<<<(int)g, 256, 0, s>>>(pos, stride, n, consts, cell, counts);
+    k_cells<<<(int)g, 256, 0, s>>>(pos, stride, n, cell_bits, consts, cell, counts);
     return cudaGetLastError();
 }
 
@@ -377,6 +377,7 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(const unsigned *__re
 {
     __shared__ unsigned wsum[32];
     __shared__ unsigned is_last, carry;
+    const int nblocks = gridDim.x;
     const int c = blockIdx.x * kScanThreads + threadIdx.x;
     const unsigned v = counts[c];
     const unsigned ex = block_excl_scan(v, wsum);
@@ -390,21 +391,22 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(const unsigned *__re
     __threadfence();
     if (threadIdx.x == 0) carry = 0u;
     __syncthreads();
-    for (int b0 = 0; b0 < kScanBlocks; b0 += kScanThreads) {
-        const unsigned b = atomicAdd(&bsum[b0 + threadIdx.x], 0u);
+    for (int b0 = 0; b0 < nblocks; b0 += kScanThreads) {
+        const int bi = b0 + threadIdx.x;
+        const unsigned b = bi < nblocks ? atomicAdd(&bsum[bi], 0u) : 0u;
         const unsigned bex = block_excl_scan(b, wsum) + carry;
         __syncthreads();
-        bsum[b0 + threadIdx.x] = bex;
+        if (bi < nblocks) bsum[bi] = bex;
         if (threadIdx.x == kScanThreads - 1) carry = bex + b;
         __syncthreads();
     }
 }
 
-cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done,
+cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done, int cell_bits,
                              cudaStream_t s)
 {
-    static_assert(kScanBlocks % kScanThreads == 0, "block totals are scanned in full chunks");
-    k_cell_scan<<<kScanBlocks, kScanThreads, 0, s>>>(counts, off_local, bsum, done);
+    const int cells = 1 << (3 * cell_bits);
+    k_cell_scan<<<cells / kScanThreads, kScanThreads, 0, s>>>(counts, off_local, bsum, done);
     return cudaGetLastError();
 }
 
@@ -683,14 +685,142 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+__device__ __forceinline__ void fence_proxy_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Scores one tile of kScoreThreads * kScoreGPT primitives of the processing
+// order starting at `base`; `next_base` (or -1) is the tile this CTA takes
+// next, whose primitives are pulled towards L2 meanwhile.
+template <typename AT, bool NOPROJ, bool COUNT>
+__device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *cs, const SceneConsts &sc,
+                                           int64_t base, int64_t next_base, unsigned long long (&cnt)[kCountSlots])
+{
+    const AT *attr = static_cast<const AT *>(a.attr);
+    const int64_t S = a.stride;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (next_base >= 0) {
+#pragma unroll
+        for (int g = 0; g < kScoreGPT; ++g) {
+            const int64_t j = next_base + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
+            if (j < a.n) {
+                const int64_t i = __ldg(a.perm + j);
+                prefetch_l2(a.pos + i);
+                prefetch_l2(a.pos + S + i);
+                prefetch_l2(a.pos + 2 * S + i);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) prefetch_l2(attr + r * S + i);
+                prefetch_l2(a.m_col + i);
+            }
+        }
+    }
+    PairIn p[kScoreGPT];
+    float acc[kScoreGPT], alpha[kScoreGPT], mg[kScoreGPT];
+    int64_t idx[kScoreGPT];
+    bool valid[kScoreGPT];
+    bool degen = false;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, b2 = 0.f;
+#pragma unroll
+    for (int g = 0; g < kScoreGPT; ++g) {
+        const int64_t j = base + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
+        float ls0 = 0.f, ls1 = 0.f, ls2 = 0.f, qw = 1.f, qx = 0.f, qy = 0.f, qz = 0.f, lg = 0.f;
+        p[g].mx = p[g].my = p[g].mz = 0.f;
+        idx[g] = -1;
+        acc[g] = 0.f;
+        valid[g] = j < a.n;
+        if (valid[g]) {
+            const int64_t i = __ldg(a.perm + j);
+            idx[g] = i;
+            p[g].mx = __ldg(a.pos + i);
+            p[g].my = __ldg(a.pos + S + i);
+            p[g].mz = __ldg(a.pos + 2 * S + i);
+            ls0 = ld_attr(attr + i);
+            ls1 = ld_attr(attr + S + i);
+            ls2 = ld_attr(attr + 2 * S + i);
+            qw = ld_attr(attr + 3 * S + i);
+            qx = ld_attr(attr + 4 * S + i);
+            qy = ld_attr(attr + 5 * S + i);
+            qz = ld_attr(attr + 6 * S + i);
+            lg = ld_attr(attr + 7 * S + i);
+            if (!a.first) acc[g] = a.running[i];
+            if (!isfinite(fmaf(qw + qx + qy + qz, 0.f, 0.f))) set_status(a.status, kEnonfinite);
+        }
+        const float qn2 = fmaf(qw, qw, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+        if (!(qn2 > 0.f)) {
+            if (valid[g]) set_status(a.status, kEinval);
+            qw = 1.f; qx = qy = qz = 0.f;
+        } else {
+            const float r = rsqrtf(qn2);
+            qw *= r; qx *= r; qy *= r; qz *= r;
+        }
+        const float e0 = expf(ls0), e1 = expf(ls1), e2 = expf(ls2);
+        alpha[g] = 1.f / (1.f + expf(-lg));
+        mg[g] = fmaxf(fmaxf(e0 * e1, e0 * e2), e1 * e2);
+        const float s0 = 3.f * e0, s1 = 3.f * e1, s2 = 3.f * e2;
+        const float smax = fmaxf(s0, fmaxf(s1, s2));
+        p[g].b2 = smax * smax * 1.0009765625f;
+        degen |= (s0 == 0.f) | (s1 == 0.f) | (s2 == 0.f);
+        // the rows of L are the columns of R(q) scaled by 3 s_k
+        p[g].L[0] = s0 * (1.f - 2.f * (qy * qy + qz * qz));
+        p[g].L[1] = s0 * (2.f * (qx * qy + qw * qz));
+        p[g].L[2] = s0 * (2.f * (qx * qz - qw * qy));
+        p[g].L[3] = s1 * (2.f * (qx * qy - qw * qz));
+        p[g].L[4] = s1 * (1.f - 2.f * (qx * qx + qz * qz));
+        p[g].L[5] = s1 * (2.f * (qy * qz + qw * qx));
+        p[g].L[6] = s2 * (2.f * (qx * qz + qw * qy));
+        p[g].L[7] = s2 * (2.f * (qy * qz - qw * qx));
+        p[g].L[8] = s2 * (1.f - 2.f * (qx * qx + qy * qy));
+        if (valid[g]) {
+            lo[0] = fminf(lo[0], p[g].mx); hi[0] = fmaxf(hi[0], p[g].mx);
+            lo[1] = fminf(lo[1], p[g].my); hi[1] = fmaxf(hi[1], p[g].my);
+            lo[2] = fminf(lo[2], p[g].mz); hi[2] = fmaxf(hi[2], p[g].mz);
+            b2 = fmaxf(b2, p[g].b2);
+        }
+    }
+    if (!__any_sync(0xffffffffu, valid[0])) return;  // warp past the end
+
+    TileBox tb;
+    {
+        const float l0 = warp_min(lo[0]), l1 = warp_min(lo[1]), l2 = warp_min(lo[2]);
+        const float h0 = warp_max(hi[0]), h1 = warp_max(hi[1]), h2 = warp_max(hi[2]);
+        tb.b2 = warp_max(b2);
+        tb.cx = 0.5f * (l0 + h0); tb.hx = 0.5f * (h0 - l0);
+        tb.cy = 0.5f * (l1 + h1); tb.hy = 0.5f * (h1 - l1);
+        tb.cz = 0.5f * (l2 + h2); tb.hz = 0.5f * (h2 - l2);
+        tb.mx = fabsf(tb.cx) + tb.hx;
+        tb.my = fabsf(tb.cy) + tb.hy;
+        tb.mz = fabsf(tb.cz) + tb.hz;
+    }
+
+    if (__any_sync(0xffffffffu, degen))
+        view_loop<NOPROJ, true, COUNT>(cs, a.vcount, a.eta, p, valid, tb, acc, cnt);
+    else
+        view_loop<NOPROJ, false, COUNT>(cs, a.vcount, a.eta, p, valid, tb, acc, cnt);
+
+#pragma unroll
+    for (int g = 0; g < kScoreGPT; ++g) {
+        const int64_t i = idx[g];
+        if (i < 0) continue;
+        if (!a.last) {
+            a.running[i] = acc[g];
+            continue;
+        }
+        const float Ssum = acc[g];
+        if (a.view_sum) a.view_sum[i] = Ssum;
+        const float coupled =
+            fmaf(sc.kappa[0], mg[g], fmaf(sc.kappa[1], __ldg(a.m_col + i), sc.kappa[2] * alpha[g]));
+        const float A = ((a.flags & REFINE_FLAG_NO_VIS) ? 1.f : alpha[g]) * (Ssum * a.inv_views);
+        a.scores[i] = A * coupled;
+    }
+}
+
 template <typename AT, bool NOPROJ, bool COUNT>
 __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     CamRec *cs = reinterpret_cast<CamRec *>(smem_raw);
-    const AT *attr = static_cast<const AT *>(a.attr);
-    const int64_t S = a.stride;
 
     // Stage this pass's cameras once per CTA (TMA bulk copy, mbarrier).
     const uint32_t bytes = (uint32_t)a.vcount * (uint32_t)sizeof(CamRec);
@@ -713,124 +843,11 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 #pragma unroll
     for (int k = 0; k < kCountSlots; ++k) cnt[k] = 0;
     const SceneConsts sc = *a.consts;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t tile = (int64_t)blockDim.x * kScoreGPT;
-    for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile) {
-        // pull the next tile's primitives towards L2 while this one computes
-        const int64_t nbase = base + (int64_t)gridDim.x * tile;
-#pragma unroll
-        for (int g = 0; g < kScoreGPT; ++g) {
-            const int64_t j = nbase + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
-            if (j < a.n) {
-                const int64_t i = __ldg(a.perm + j);
-                prefetch_l2(a.pos + i);
-                prefetch_l2(a.pos + S + i);
-                prefetch_l2(a.pos + 2 * S + i);
-#pragma unroll
-                for (int r = 0; r < 8; ++r) prefetch_l2(attr + r * S + i);
-                prefetch_l2(a.m_col + i);
-            }
-        }
-        PairIn p[kScoreGPT];
-        float acc[kScoreGPT], alpha[kScoreGPT], mg[kScoreGPT];
-        int64_t idx[kScoreGPT];
-        bool valid[kScoreGPT];
-        bool degen = false;
-        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, b2 = 0.f;
-#pragma unroll
-        for (int g = 0; g < kScoreGPT; ++g) {
-            const int64_t j = base + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
-            float ls0 = 0.f, ls1 = 0.f, ls2 = 0.f, qw = 1.f, qx = 0.f, qy = 0.f, qz = 0.f, lg = 0.f;
-            p[g].mx = p[g].my = p[g].mz = 0.f;
-            idx[g] = -1;
-            acc[g] = 0.f;
-            valid[g] = j < a.n;
-            if (valid[g]) {
-                const int64_t i = __ldg(a.perm + j);
-                idx[g] = i;
-                p[g].mx = __ldg(a.pos + i);
-                p[g].my = __ldg(a.pos + S + i);
-                p[g].mz = __ldg(a.pos + 2 * S + i);
-                ls0 = ld_attr(attr + i);
-                ls1 = ld_attr(attr + S + i);
-                ls2 = ld_attr(attr + 2 * S + i);
-                qw = ld_attr(attr + 3 * S + i);
-                qx = ld_attr(attr + 4 * S + i);
-                qy = ld_attr(attr + 5 * S + i);
-                qz = ld_attr(attr + 6 * S + i);
-                lg = ld_attr(attr + 7 * S + i);
-                if (!a.first) acc[g] = a.running[i];
-                if (!isfinite(fmaf(qw + qx + qy + qz, 0.f, 0.f))) set_status(a.status, kEnonfinite);
-            }
-            const float qn2 = fmaf(qw, qw, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
-            if (!(qn2 > 0.f)) {
-                if (valid[g]) set_status(a.status, kEinval);
-                qw = 1.f; qx = qy = qz = 0.f;
-            } else {
-                const float r = rsqrtf(qn2);
-                qw *= r; qx *= r; qy *= r; qz *= r;
-            }
-            const float e0 = expf(ls0), e1 = expf(ls1), e2 = expf(ls2);
-            alpha[g] = 1.f / (1.f + expf(-lg));
-            mg[g] = fmaxf(fmaxf(e0 * e1, e0 * e2), e1 * e2);
-            const float s0 = 3.f * e0, s1 = 3.f * e1, s2 = 3.f * e2;
-            const float smax = fmaxf(s0, fmaxf(s1, s2));
-            p[g].b2 = smax * smax * 1.0009765625f;
-            degen |= (s0 == 0.f) | (s1 == 0.f) | (s2 == 0.f);
-            // the rows of L are the columns of R(q) scaled by 3 s_k
-            p[g].L[0] = s0 * (1.f - 2.f * (qy * qy + qz * qz));
-            p[g].L[1] = s0 * (2.f * (qx * qy + qw * qz));
-            p[g].L[2] = s0 * (2.f * (qx * qz - qw * qy));
-            p[g].L[3] = s1 * (2.f * (qx * qy - qw * qz));
-            p[g].L[4] = s1 * (1.f - 2.f * (qx * qx + qz * qz));
-            p[g].L[5] = s1 * (2.f * (qy * qz + qw * qx));
-            p[g].L[6] = s2 * (2.f * (qx * qz + qw * qy));
-            p[g].L[7] = s2 * (2.f * (qy * qz - qw * qx));
-            p[g].L[8] = s2 * (1.f - 2.f * (qx * qx + qy * qy));
-            if (valid[g]) {
-                lo[0] = fminf(lo[0], p[g].mx); hi[0] = fmaxf(hi[0], p[g].mx);
-                lo[1] = fminf(lo[1], p[g].my); hi[1] = fmaxf(hi[1], p[g].my);
-                lo[2] = fminf(lo[2], p[g].mz); hi[2] = fmaxf(hi[2], p[g].mz);
-                b2 = fmaxf(b2, p[g].b2);
-            }
-        }
-        if (!__any_sync(0xffffffffu, valid[0])) continue;  // warp past the end
-
-        TileBox tb;
-        {
-            const float l0 = warp_min(lo[0]), l1 = warp_min(lo[1]), l2 = warp_min(lo[2]);
-            const float h0 = warp_max(hi[0]), h1 = warp_max(hi[1]), h2 = warp_max(hi[2]);
-            tb.b2 = warp_max(b2);
-            tb.cx = 0.5f * (l0 + h0); tb.hx = 0.5f * (h0 - l0);
-            tb.cy = 0.5f * (l1 + h1); tb.hy = 0.5f * (h1 - l1);
-            tb.cz = 0.5f * (l2 + h2); tb.hz = 0.5f * (h2 - l2);
-            tb.mx = fabsf(tb.cx) + tb.hx;
-            tb.my = fabsf(tb.cy) + tb.hy;
-            tb.mz = fabsf(tb.cz) + tb.hz;
-        }
-
-        if (__any_sync(0xffffffffu, degen))
-            view_loop<NOPROJ, true, COUNT>(cs, a.vcount, a.eta, p, valid, tb, acc, cnt);
-        else
-            view_loop<NOPROJ, false, COUNT>(cs, a.vcount, a.eta, p, valid, tb, acc, cnt);
-
-#pragma unroll
-        for (int g = 0; g < kScoreGPT; ++g) {
-            const int64_t i = idx[g];
-            if (i < 0) continue;
-            if (!a.last) {
-                a.running[i] = acc[g];
-                continue;
-            }
-            const float Ssum = acc[g];
-            if (a.view_sum) a.view_sum[i] = Ssum;
-            const float coupled =
-                fmaf(sc.kappa[0], mg[g], fmaf(sc.kappa[1], __ldg(a.m_col + i), sc.kappa[2] * alpha[g]));
-            const float A = ((a.flags & REFINE_FLAG_NO_VIS) ? 1.f : alpha[g]) * (Ssum * a.inv_views);
-            a.scores[i] = A * coupled;
-        }
-    }
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile)
+        score_tile<AT, NOPROJ, COUNT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
     if (COUNT) {
+        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int k = 0; k < kCountSlots; ++k) {
             unsigned long long v = cnt[k];
@@ -838,6 +855,71 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0 && v) atomicAdd(&a.need[k], v);
         }
+    }
+}
+
+// The batched form: one persistent launch over the tiles of many scenes.
+// CTAs take (scene, tile) items from an atomic counter (items are ordered
+// by scene); when a CTA moves to another scene it restages that scene's
+// cameras by TMA.  Every tile is scored by score_tile exactly as in
+// k_score, so a scene's scores are the same alone and in a batch.
+template <typename AT, bool NOPROJ>
+__global__ void __launch_bounds__(kScoreThreads, 3) k_score_batch(BatchLaunch b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_scene;
+    __shared__ long long s_base;
+    CamRec *cs = reinterpret_cast<CamRec *>(smem_raw);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    unsigned long long cnt[kCountSlots];
+    int cur = -1;
+    uint32_t phase = 0;
+    const int64_t tile = (int64_t)blockDim.x * kScoreGPT;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long item = atomicAdd(b.counter, 1ull);
+            int sidx = -1;
+            long long base = 0;
+            if ((long long)item < b.total_tiles) {
+                int lo = 0, hi = b.n_scenes - 1;  // last scene whose first tile <= item
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (b.tile_begin[mid] <= (long long)item) lo = mid; else hi = mid - 1;
+                }
+                sidx = lo;
+                base = ((long long)item - b.tile_begin[lo]) * tile;
+            }
+            s_scene = sidx;
+            s_base = base;
+        }
+        __syncthreads();
+        const int sidx = s_scene;
+        const int64_t base = s_base;
+        if (sidx < 0) break;
+        const ScoreLaunch &a = b.scenes[sidx];
+        if (sidx != cur) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async_shared();
+                const uint32_t bytes = (uint32_t)a.vcount * (uint32_t)sizeof(CamRec);
+                mbar_expect_tx(&bar, bytes);
+                for (uint32_t off = 0; off < bytes; off += 16384u) {
+                    const uint32_t len = bytes - off < 16384u ? bytes - off : 16384u;
+                    bulk_g2s(smem_raw + off, reinterpret_cast<const unsigned char *>(a.cams) + off, len, &bar);
+                }
+            }
+            if (!mbar_wait_bounded(&bar, phase)) {
+                set_status(b.status, kEtimeout);
+                mbar_wait_bounded(&bar, phase);
+                return;
+            }
+            phase ^= 1u;
+            cur = sidx;
+        }
+        const SceneConsts sc = *a.consts;
+        score_tile<AT, NOPROJ, false>(a, cs, sc, base, -1, cnt);
+        __syncthreads();  // the cameras and s_scene are free again
     }
 }
 
@@ -887,6 +969,40 @@ cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s)
     ScoreLaunch arg = a;
     void *args[] = {&arg};
     return cudaLaunchKernel(fn, dim3(a.grid), dim3(kScoreThreads), args, smem, s);
+}
+
+template <typename AT, bool NOPROJ>
+static const void *batch_fn()
+{
+    return reinterpret_cast<const void *>(&k_score_batch<AT, NOPROJ>);
+}
+
+int score_batch_grid(int num_sms, int dtype, bool noproj, int max_vcount)
+{
+    const void *fn = dtype == REFINE_BF16 ? (noproj ? batch_fn<__nv_bfloat16, true>() : batch_fn<__nv_bfloat16, false>())
+                                          : (noproj ? batch_fn<float, true>() : batch_fn<float, false>());
+    const size_t smem = (size_t)max_vcount * sizeof(CamRec);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kScoreThreads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return num_sms * per_sm;
+}
+
+cudaError_t launch_score_batch(const BatchLaunch &b, int dtype, bool noproj, int max_vcount, int grid, cudaStream_t s)
+{
+    const void *fn = dtype == REFINE_BF16 ? (noproj ? batch_fn<__nv_bfloat16, true>() : batch_fn<__nv_bfloat16, false>())
+                                          : (noproj ? batch_fn<float, true>() : batch_fn<float, false>());
+    const size_t smem = (size_t)max_vcount * sizeof(CamRec);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    BatchLaunch arg = b;
+    void *args[] = {&arg};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kScoreThreads), args, smem, s);
 }
 
 }  // namespace refine

@@ -5,6 +5,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -222,134 +224,223 @@ refine_status read_status(refine_ctx *c, cudaStream_t s)
 }
 
 // ------------------------------------------------------------------ score
+// Scratch layout of one scene's score pass.
+struct ScenePlan {
+    int64_t n = 0;
+    int V = 0;
+    bool multipass = false;
+    bool vec = false;
+    int nb = 1;    // feature-pass blocks
+    int bits = 4;  // processing-order grid resolution
+};
+
+struct SceneScratch {
+    CamRec *cams;
+    float *m_col;
+    double *partials;
+    SceneConsts *consts;
+    SceneStats *stats;
+    uint32_t *cell;
+    unsigned *counts;  // cell_count(bits) + 64 words; the last ones hold the scan's done counter
+    unsigned *off_local;
+    unsigned *bsum;
+    uint32_t *perm;
+    unsigned long long *need;
+    float *running;
+};
+
+ScenePlan plan_scene(const refine_ctx *c, const refine_scene *sc, int V)
+{
+    ScenePlan pl;
+    pl.n = sc->n;
+    pl.V = V;
+    pl.multipass = V > kViewsPerPass;
+    pl.vec = scene_vec_ok(sc);
+    pl.nb = feature_blocks(pl.n);
+    if (pl.vec) {
+        const int64_t chunks = pl.n / 256 + 1;
+        pl.nb = feature_tma_blocks(c->num_sms, sc->dtype);
+        if (pl.nb > chunks) pl.nb = (int)chunks;
+    }
+    pl.bits = cell_bits_for(pl.n);
+    return pl;
+}
+
+size_t scene_bytes(const ScenePlan &pl)
+{
+    const size_t n = (size_t)pl.n, cells = (size_t)cell_count(pl.bits);
+    return carve_size({sizeof(CamRec) * (size_t)pl.V, sizeof(float) * n, sizeof(double) * kFeatSums * 1024,
+                       sizeof(SceneConsts), sizeof(SceneStats), sizeof(uint32_t) * n,
+                       sizeof(unsigned) * (cells + 64), sizeof(unsigned) * cells,
+                       sizeof(unsigned) * (cells / kScanThreads), sizeof(uint32_t) * n,
+                       kCountSlots * sizeof(unsigned long long), pl.multipass ? sizeof(float) * n : 0});
+}
+
+SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
+{
+    const int64_t n = pl.n;
+    const int cells = cell_count(pl.bits);
+    SceneScratch x;
+    x.cams = cv.take<CamRec>(pl.V);
+    x.m_col = cv.take<float>(n);
+    x.partials = cv.take<double>(kFeatSums * 1024);
+    x.consts = cv.take<SceneConsts>(1);
+    x.stats = cv.take<SceneStats>(1);
+    x.cell = cv.take<uint32_t>(n);
+    x.counts = cv.take<unsigned>(cells + 64);
+    x.off_local = cv.take<unsigned>(cells);
+    x.bsum = cv.take<unsigned>(cells / kScanThreads);
+    x.perm = cv.take<uint32_t>(n);
+    x.need = cv.take<unsigned long long>(kCountSlots);
+    x.running = pl.multipass ? cv.take<float>(n) : nullptr;
+    return x;
+}
+
+// Camera records, content features and lambda, processing order.
+template <typename L>
+refine_status enqueue_prep(refine_ctx *c, L &&run, const refine_scene *sc, const refine_camera *cams,
+                           const ScenePlan &pl, const SceneScratch &x, const refine_params &p, bool count,
+                           int *status, cudaStream_t s)
+{
+    const int64_t n = pl.n;
+    const int cells = cell_count(pl.bits);
+    cudaError_t e = cudaMemsetAsync(x.counts, 0, sizeof(unsigned) * (cells + 64), s);
+    if (e == cudaSuccess && count) e = cudaMemsetAsync(x.need, 0, kCountSlots * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+    refine_status st;
+    if ((st = run(K_CAM_PREP, [&] { return launch_cam_prep(cams, pl.V, x.cams, status, s); }))) return st;
+    if ((st = run(K_FEATURES, [&] {
+             if (pl.vec)
+                 return launch_features_tma(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, x.m_col,
+                                            x.partials, pl.nb, status, s);
+             return launch_features(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, x.m_col,
+                                    x.partials, false, status, s);
+         })))
+        return st;
+    if ((st = run(K_FEAT_FINAL,
+                  [&] { return launch_features_finalize(x.partials, pl.nb, n, &p, pl.bits, x.consts, x.stats, s); })))
+        return st;
+    if ((st = run(K_CELLS, [&] {
+             return launch_cells(sc->pos, sc->row_stride, n, pl.bits, x.consts, x.cell, x.counts, c->num_sms, s);
+         })))
+        return st;
+    if ((st = run(K_CELL_SCAN,
+                  [&] { return launch_cell_scan(x.counts, x.off_local, x.bsum, x.counts + cells, pl.bits, s); })))
+        return st;
+    return run(K_CELL_SCATTER,
+               [&] { return launch_cell_scatter(x.cell, n, x.counts, x.off_local, x.bsum, x.perm, c->num_sms, s); });
+}
+
+ScoreLaunch make_score_launch(const refine_scene *sc, const ScenePlan &pl, const SceneScratch &x,
+                              const refine_params &p, int v0, float *scores, float *view_sum, bool count, int *status)
+{
+    ScoreLaunch a;
+    a.pos = sc->pos;
+    a.attr = sc->attr;
+    a.dtype = sc->dtype;
+    a.stride = sc->row_stride;
+    a.perm = x.perm;
+    a.m_col = x.m_col;
+    a.n = pl.n;
+    a.cams = x.cams + v0;
+    a.vcount = pl.V - v0 < kViewsPerPass ? pl.V - v0 : kViewsPerPass;
+    a.first = v0 == 0;
+    a.last = v0 + a.vcount >= pl.V;
+    a.eta = p.eta;
+    a.inv_views = 1.0f / (float)pl.V;
+    a.flags = p.flags;
+    a.consts = x.consts;
+    a.running = x.running;
+    a.scores = scores;
+    a.view_sum = view_sum;
+    a.need = count ? x.need : nullptr;
+    a.status = status;
+    a.grid = 0;
+    return a;
+}
+
+refine_status check_score_args(refine_ctx *c, const refine_scene *sc, const refine_camera *cams, int V,
+                               const refine_params &p, const float *scores)
+{
+    refine_status st = check_scene(c, sc);
+    if (st) return st;
+    if (V < 1 || V > 65535) return fail(c, REFINE_EINVAL, "n_views=%d out of [1, 65535]", V);
+    if (!cams) return fail(c, REFINE_EINVAL, "cams_dev is NULL");
+    if ((st = check_params(c, &p))) return st;
+    if (sc->n > 0 && !scores) return fail(c, REFINE_EINVAL, "scores_dev is NULL");
+    return REFINE_OK;
+}
+
 refine_status score_impl(refine_ctx *c, const refine_scene *sc, const refine_camera *cams, int V,
                          const refine_params *pin, float *scores, float *view_sum, SceneStats **stats_dev,
                          unsigned long long **need_dev, cudaStream_t s)
 {
     refine_params p;
     if (pin) p = *pin; else refine_params_default(&p);
-    refine_status st = check_scene(c, sc);
-    if (st) return st;
-    if (V < 1 || V > 65535) return fail(c, REFINE_EINVAL, "n_views=%d out of [1, 65535]", V);
-    if (!cams) return fail(c, REFINE_EINVAL, "cams_dev is NULL");
-    if ((st = check_params(c, &p))) return st;
-    if (sc->n == 0) return REFINE_OK;
-    if (!scores) return fail(c, REFINE_EINVAL, "scores_dev is NULL");
-    const int64_t n = sc->n;
-    const bool multipass = V > kViewsPerPass;
-    const bool vec = scene_vec_ok(sc);
-    int nb = feature_blocks(n);
-    if (vec) {
-        const int64_t chunks = n / 256 + 1;
-        nb = feature_tma_blocks(c->num_sms, sc->dtype);
-        if (nb > chunks) nb = (int)chunks;
-    }
-    size_t need = carve_size({sizeof(CamRec) * (size_t)V, sizeof(float) * (size_t)n,
-                              sizeof(double) * kFeatSums * 1024, sizeof(SceneConsts), sizeof(SceneStats),
-                              sizeof(uint32_t) * (size_t)n, sizeof(unsigned) * (kCells + 64),
-                              sizeof(unsigned) * kCells, sizeof(unsigned) * kScanBlocks,
-                              sizeof(uint32_t) * (size_t)n, kCountSlots * sizeof(unsigned long long),
-                              multipass ? sizeof(float) * (size_t)n : 0});
-    if ((st = ensure(c, c->score, need))) return st;
+    refine_status st = check_score_args(c, sc, cams, V, p, scores);
+    if (st || sc->n == 0) return st;
+    const ScenePlan pl = plan_scene(c, sc, V);
+    if ((st = ensure(c, c->score, scene_bytes(pl)))) return st;
     Carver cv(c->score.p);
-    CamRec *recs_cam = cv.take<CamRec>(V);
-    float *m_col = cv.take<float>(n);
-    double *partials = cv.take<double>(kFeatSums * 1024);
-    SceneConsts *consts = cv.take<SceneConsts>(1);
-    SceneStats *stats = cv.take<SceneStats>(1);
-    uint32_t *cell = cv.take<uint32_t>(n);
-    unsigned *counts = cv.take<unsigned>(kCells + 64);  // the last words hold the scan's done counter
-    unsigned *off_local = cv.take<unsigned>(kCells);
-    unsigned *bsum = cv.take<unsigned>(kScanBlocks);
-    uint32_t *perm = cv.take<uint32_t>(n);
-    unsigned long long *need_ctr = cv.take<unsigned long long>(kCountSlots);
-    float *running = multipass ? cv.take<float>(n) : nullptr;
-    if (stats_dev) *stats_dev = stats;
-    if (need_dev) *need_dev = need_ctr;
-
-    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned) * (kCells + 64), s);
-    if (e == cudaSuccess && need_dev) e = cudaMemsetAsync(need_ctr, 0, kCountSlots * sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
-    if ((st = launch(c, K_CAM_PREP, s, [&] { return launch_cam_prep(cams, V, recs_cam, c->d_status, s); }))) return st;
-    if ((st = launch(c, K_FEATURES, s, [&] {
-             if (vec)
-                 return launch_features_tma(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, m_col,
-                                            partials, nb, c->d_status, s);
-             return launch_features(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, m_col, partials,
-                                    false, c->d_status, s);
-         })))
-        return st;
-    if ((st = launch(c, K_FEAT_FINAL, s,
-                     [&] { return launch_features_finalize(partials, nb, n, &p, consts, stats, s); })))
-        return st;
-    if ((st = launch(c, K_CELLS, s,
-                     [&] { return launch_cells(sc->pos, sc->row_stride, n, consts, cell, counts, c->num_sms, s); })))
-        return st;
-    if ((st = launch(c, K_CELL_SCAN, s, [&] { return launch_cell_scan(counts, off_local, bsum, counts + kCells, s); })))
-        return st;
-    if ((st = launch(c, K_CELL_SCATTER, s,
-                     [&] { return launch_cell_scatter(cell, n, counts, off_local, bsum, perm, c->num_sms, s); })))
-        return st;
+    const SceneScratch x = carve_scene(cv, pl);
+    if (stats_dev) *stats_dev = x.stats;
+    if (need_dev) *need_dev = x.need;
+    auto run = [&](int cls, auto &&f) { return launch(c, cls, s, f); };
+    if ((st = enqueue_prep(c, run, sc, cams, pl, x, p, need_dev != nullptr, c->d_status, s))) return st;
     for (int v0 = 0; v0 < V; v0 += kViewsPerPass) {
-        ScoreLaunch a;
-        a.pos = sc->pos;
-        a.attr = sc->attr;
-        a.dtype = sc->dtype;
-        a.stride = sc->row_stride;
-        a.perm = perm;
-        a.m_col = m_col;
-        a.n = n;
-        a.cams = recs_cam + v0;
-        a.vcount = V - v0 < kViewsPerPass ? V - v0 : kViewsPerPass;
-        a.first = v0 == 0;
-        a.last = v0 + a.vcount >= V;
-        a.eta = p.eta;
-        a.inv_views = 1.0f / (float)V;
-        a.flags = p.flags;
-        a.consts = consts;
-        a.running = running;
-        a.scores = scores;
-        a.view_sum = view_sum;
-        a.need = need_dev ? need_ctr : nullptr;
-        a.status = c->d_status;
-        a.grid = score_grid(c->num_sms, n, a.vcount);
+        ScoreLaunch a = make_score_launch(sc, pl, x, p, v0, scores, view_sum, need_dev != nullptr, c->d_status);
+        a.grid = score_grid(c->num_sms, pl.n, a.vcount);
         if ((st = launch(c, K_SCORE, s, [&] { return launch_score(a, s); }))) return st;
     }
     return REFINE_OK;
 }
 
 // ----------------------------------------------------------------- select
-refine_status select_impl(refine_ctx *c, const float *scores, int64_t n, double ratio, uint32_t *mask,
-                          unsigned int **kstar_dev, int64_t *n_keep, cudaStream_t s)
+size_t select_bytes(int64_t n)
 {
-    if (n < 0 || n > INT32_MAX) return fail(c, REFINE_EINVAL, "select: n=%lld out of range", (long long)n);
-    if (!(ratio >= 0.0 && ratio < 1.0)) return fail(c, REFINE_EINVAL, "select: ratio must lie in [0, 1)");
-    const int64_t n_prune = (int64_t)floor(ratio * (double)n);
-    *n_keep = n - n_prune;
+    return carve_size({sizeof(SelState), sizeof(unsigned) * (size_t)((n + kTieSeg - 1) / kTieSeg)});
+}
+
+// Radix select into the given state; *kstar_dev is NULL when nothing is pruned.
+template <typename L>
+refine_status enqueue_select(refine_ctx *c, L &&run, const float *scores, int64_t n, int64_t n_keep,
+                             uint32_t *mask, void *scratch, unsigned int **kstar_dev, int *status, cudaStream_t s)
+{
     *kstar_dev = nullptr;
     if (n == 0) return REFINE_OK;
-    if (!scores || !mask) return fail(c, REFINE_EINVAL, "select: NULL scores or mask");
-    refine_status st;
-    if (n_prune == 0)
-        return launch(c, K_MASK_FILL, s, [&] { return launch_mask_fill(mask, n, s); });
-    const int64_t nseg = (n + kTieSeg - 1) / kTieSeg;
-    if ((st = ensure(c, c->select, carve_size({sizeof(SelState), sizeof(unsigned) * (size_t)nseg})))) return st;
-    Carver cv(c->select.p);
+    if (n_keep == n) return run(K_MASK_FILL, [&] { return launch_mask_fill(mask, n, s); });
+    Carver cv(scratch);
     SelState *ss = cv.take<SelState>(1);
-    unsigned *seg = cv.take<unsigned>(nseg);
+    unsigned *seg = cv.take<unsigned>((n + kTieSeg - 1) / kTieSeg);
     cudaError_t e = cudaMemsetAsync(ss, 0, sizeof(SelState), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
     const bool vec = aligned16(scores);
     const int grid = select_grid(c->num_sms, n);
+    refine_status st;
     for (int pass = 0; pass < 3; ++pass)
-        if ((st = launch(c, K_SEL_PASS, s, [&] {
-                 return launch_select_pass(pass, scores, n, (uint32_t)*n_keep, ss, vec, grid, c->d_status, s);
+        if ((st = run(K_SEL_PASS, [&] {
+                 return launch_select_pass(pass, scores, n, (uint32_t)n_keep, ss, vec, grid, status, s);
              })))
             return st;
-    if ((st = launch(c, K_SEL_TIES, s, [&] { return launch_select_ties(scores, n, ss, seg, grid, s); }))) return st;
-    if ((st = launch(c, K_SEL_MASK, s, [&] { return launch_select_mask(scores, n, ss, mask, grid, s); }))) return st;
+    if ((st = run(K_SEL_TIES, [&] { return launch_select_ties(scores, n, ss, seg, grid, s); }))) return st;
+    if ((st = run(K_SEL_MASK, [&] { return launch_select_mask(scores, n, ss, mask, grid, s); }))) return st;
     *kstar_dev = &ss->kstar;
     return REFINE_OK;
+}
+
+refine_status select_impl(refine_ctx *c, const float *scores, int64_t n, double ratio, uint32_t *mask,
+                          unsigned int **kstar_dev, int64_t *n_keep, cudaStream_t s)
+{
+    *kstar_dev = nullptr;
+    if (n < 0 || n > INT32_MAX) return fail(c, REFINE_EINVAL, "select: n=%lld out of range", (long long)n);
+    if (!(ratio >= 0.0 && ratio < 1.0)) return fail(c, REFINE_EINVAL, "select: ratio must lie in [0, 1)");
+    *n_keep = n - (int64_t)floor(ratio * (double)n);
+    if (n == 0) return REFINE_OK;
+    if (!scores || !mask) return fail(c, REFINE_EINVAL, "select: NULL scores or mask");
+    refine_status st;
+    if ((st = ensure(c, c->select, select_bytes(n)))) return st;
+    auto run = [&](int cls, auto &&f) { return launch(c, cls, s, f); };
+    return enqueue_select(c, run, scores, n, *n_keep, mask, c->select.p, kstar_dev, c->d_status, s);
 }
 
 refine_status read_threshold(refine_ctx *c, unsigned int *kstar_dev, float *thr, cudaStream_t s)
@@ -368,6 +459,45 @@ refine_status read_threshold(refine_ctx *c, unsigned int *kstar_dev, float *thr,
 }
 
 // ---------------------------------------------------------------- compact
+size_t compact_bytes(int64_t n)
+{
+    const size_t nseg = (size_t)((n + kCmpSeg - 1) / kCmpSeg);
+    return carve_size({sizeof(CmpState), sizeof(unsigned) * nseg, sizeof(unsigned long long) * nseg});
+}
+
+template <typename L>
+refine_status enqueue_compact(refine_ctx *c, L &&run, const refine_scene *in, const uint32_t *mask, float *out_pos,
+                              void *out_attr, int64_t out_stride, int32_t *idx, void *scratch, long long **total_dev,
+                              int *status, cudaStream_t s)
+{
+    const int64_t n = in->n;
+    const int64_t nseg = (n + kCmpSeg - 1) / kCmpSeg;
+    Carver cv(scratch);
+    CmpState *cs = cv.take<CmpState>(1);
+    unsigned *seg_cnt = cv.take<unsigned>(nseg);
+    unsigned long long *seg_off = cv.take<unsigned long long>(nseg);
+    cudaError_t e = cudaMemsetAsync(cs, 0, sizeof(CmpState), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+    int64_t cgrid = (nseg + 1023) / 1024;
+    if (cgrid > c->num_sms) cgrid = c->num_sms;
+    if (cgrid < 1) cgrid = 1;
+    refine_status st;
+    if ((st = run(K_CMP_COUNT, [&] {
+             return launch_compact_count(mask, n, seg_cnt, seg_off, cs, out_stride, (int)cgrid, status, s);
+         })))
+        return st;
+    const bool tma = scene_vec_ok(in);
+    int64_t sgrid = tma ? compact_stream_blocks(c->num_sms, in->dtype) : (int64_t)c->num_sms * 4;
+    if (sgrid > nseg) sgrid = nseg;
+    if ((st = run(K_CMP_SCATTER, [&] {
+             return launch_compact_stream(*in, mask, seg_off, cs, out_pos, out_attr, out_stride, idx, tma, (int)sgrid,
+                                          status, s);
+         })))
+        return st;
+    *total_dev = &cs->total;
+    return REFINE_OK;
+}
+
 refine_status compact_impl(refine_ctx *c, const refine_scene *in, const uint32_t *mask, float *out_pos,
                            void *out_attr, int64_t out_stride, int32_t *idx, long long **total_dev,
                            cudaStream_t s)
@@ -378,35 +508,10 @@ refine_status compact_impl(refine_ctx *c, const refine_scene *in, const uint32_t
     if (in->n == 0) return REFINE_OK;
     if (!mask || !out_pos || !out_attr) return fail(c, REFINE_EINVAL, "compact: NULL mask or output");
     if (out_stride < 0) return fail(c, REFINE_EINVAL, "compact: negative out_row_stride");
-    const int64_t n = in->n;
-    const int64_t nseg = (n + kCmpSeg - 1) / kCmpSeg;
-    if ((st = ensure(c, c->compact,
-                     carve_size({sizeof(CmpState), sizeof(unsigned) * (size_t)nseg,
-                                 sizeof(unsigned long long) * (size_t)nseg}))))
-        return st;
-    Carver cv(c->compact.p);
-    CmpState *cs = cv.take<CmpState>(1);
-    unsigned *seg_cnt = cv.take<unsigned>(nseg);
-    unsigned long long *seg_off = cv.take<unsigned long long>(nseg);
-    cudaError_t e = cudaMemsetAsync(cs, 0, sizeof(CmpState), s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
-    int64_t cgrid = (nseg + 1023) / 1024;
-    if (cgrid > c->num_sms) cgrid = c->num_sms;
-    if (cgrid < 1) cgrid = 1;
-    if ((st = launch(c, K_CMP_COUNT, s, [&] {
-             return launch_compact_count(mask, n, seg_cnt, seg_off, cs, out_stride, (int)cgrid, c->d_status, s);
-         })))
-        return st;
-    const bool tma = scene_vec_ok(in);
-    int64_t sgrid = tma ? compact_stream_blocks(c->num_sms, in->dtype) : (int64_t)c->num_sms * 4;
-    if (sgrid > nseg) sgrid = nseg;
-    if ((st = launch(c, K_CMP_SCATTER, s, [&] {
-             return launch_compact_stream(*in, mask, seg_off, cs, out_pos, out_attr, out_stride, idx, tma,
-                                          (int)sgrid, c->d_status, s);
-         })))
-        return st;
-    *total_dev = &cs->total;
-    return REFINE_OK;
+    if ((st = ensure(c, c->compact, compact_bytes(in->n)))) return st;
+    auto run = [&](int cls, auto &&f) { return launch(c, cls, s, f); };
+    return enqueue_compact(c, run, in, mask, out_pos, out_attr, out_stride, idx, c->compact.p, total_dev,
+                           c->d_status, s);
 }
 
 }  // namespace
@@ -688,5 +793,270 @@ refine_status refine_ctx_kernel_times(refine_ctx *c, const char **names, double 
 }
 
 int64_t refine_ctx_launch_count(const refine_ctx *c) { return c ? c->launch_count : -1; }
+
+}  // extern "C"
+
+// ==================================================================== batch
+
+struct refine_batch {
+    refine_ctx *ctx = nullptr;
+    std::vector<refine_job> jobs;
+    refine_params params;
+    int dtype = REFINE_F32;
+    std::vector<ScenePlan> plans;
+    std::vector<SceneScratch> sx;
+    std::vector<void *> sel_scr, cmp_scr;
+    std::vector<int64_t> n_keep;
+    std::vector<unsigned int *> kstar;
+    std::vector<long long *> total;
+    void *scratch = nullptr;
+    void *h_res = nullptr;  // pinned read-back area
+    ScoreLaunch *d_launch = nullptr;
+    long long *d_tile_begin = nullptr;
+    unsigned long long *d_counter = nullptr;
+    long long total_tiles = 0;
+    int max_v = 0;
+    int grid = 1;
+    cudaStream_t main = nullptr;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> events;  // fork, join[lanes], fork2, join2[lanes]
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches_per_run = 0;
+};
+
+namespace {
+
+refine_status batch_record(refine_batch *b)
+{
+    refine_ctx *c = b->ctx;
+    const int S = (int)b->jobs.size(), L = (int)b->lanes.size();
+    cudaStream_t m = b->main;
+    int64_t launches = 0;
+    auto counted = [&](cudaStream_t) {
+        return [&launches, c](int, auto &&f) -> refine_status {
+            const cudaError_t e = f();
+            if (e != cudaSuccess) return cuda_fail(c, e, "batch launch");
+            ++launches;
+            return REFINE_OK;
+        };
+    };
+    cudaError_t e = cudaStreamBeginCapture(m, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
+    refine_status st = REFINE_OK;
+    cudaEvent_t fork = b->events[0], fork2 = b->events[1 + L];
+    e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), m);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, m);
+    for (int l = 0; l < L && e == cudaSuccess && !st; ++l) {
+        cudaStream_t ls = b->lanes[l];
+        e = cudaStreamWaitEvent(ls, fork, 0);
+        for (int j = l; j < S && e == cudaSuccess && !st; j += L)
+            st = enqueue_prep(c, counted(ls), &b->jobs[j].scene, b->jobs[j].cams_dev, b->plans[j], b->sx[j],
+                              b->params, false, c->d_status, ls);
+        if (e == cudaSuccess && !st) e = cudaEventRecord(b->events[1 + l], ls);
+    }
+    for (int l = 0; l < L && e == cudaSuccess && !st; ++l) e = cudaStreamWaitEvent(m, b->events[1 + l], 0);
+    if (e == cudaSuccess && !st) {
+        BatchLaunch bl;
+        bl.scenes = b->d_launch;
+        bl.tile_begin = b->d_tile_begin;
+        bl.n_scenes = S;
+        bl.total_tiles = b->total_tiles;
+        bl.counter = b->d_counter;
+        bl.status = c->d_status;
+        e = launch_score_batch(bl, b->dtype, (b->params.flags & REFINE_FLAG_NO_PROJ) != 0, b->max_v, b->grid, m);
+        if (e == cudaSuccess) ++launches;
+    }
+    if (e == cudaSuccess && !st) e = cudaEventRecord(fork2, m);
+    for (int l = 0; l < L && e == cudaSuccess && !st; ++l) {
+        cudaStream_t ls = b->lanes[l];
+        e = cudaStreamWaitEvent(ls, fork2, 0);
+        for (int j = l; j < S && e == cudaSuccess && !st; j += L) {
+            const refine_job &jb = b->jobs[j];
+            st = enqueue_select(c, counted(ls), jb.scores_dev, jb.scene.n, b->n_keep[j], jb.keep_mask_dev,
+                                b->sel_scr[j], &b->kstar[j], c->d_status, ls);
+            if (!st && jb.out_pos_dev)
+                st = enqueue_compact(c, counted(ls), &jb.scene, jb.keep_mask_dev, jb.out_pos_dev, jb.out_attr_dev,
+                                     jb.out_row_stride, jb.kept_idx_dev, b->cmp_scr[j], &b->total[j], c->d_status,
+                                     ls);
+        }
+        if (e == cudaSuccess && !st) e = cudaEventRecord(b->events[2 + L + l], ls);
+    }
+    for (int l = 0; l < L && e == cudaSuccess && !st; ++l) e = cudaStreamWaitEvent(m, b->events[2 + L + l], 0);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(m, &g);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e != cudaSuccess ? e : e2, "batch capture");
+    }
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    b->graph = g;
+    b->launches_per_run = launches;
+    return REFINE_OK;
+}
+
+void batch_free(refine_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t s : b->lanes) cudaStreamDestroy(s);
+    if (b->main) cudaStreamDestroy(b->main);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    if (b->scratch) cudaFree(b->scratch);
+    if (b->h_res) cudaFreeHost(b->h_res);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+refine_status refine_batch_create(refine_ctx *c, const refine_job *jobs, int32_t n_jobs,
+                                  const refine_params *params, refine_batch **out)
+{
+    if (!c || !out) return REFINE_EINVAL;
+    *out = nullptr;
+    refine_status st = use_device(c);
+    if (st) return st;
+    if (!jobs || n_jobs < 1 || n_jobs > 4096) return fail(c, REFINE_EINVAL, "batch: n_jobs must lie in [1, 4096]");
+    refine_params p;
+    if (params) p = *params; else refine_params_default(&p);
+    if ((st = check_params(c, &p))) return st;
+    const int S = n_jobs;
+    refine_batch *b = new refine_batch();
+    b->ctx = c;
+    b->params = p;
+    b->jobs.assign(jobs, jobs + S);
+    b->dtype = jobs[0].scene.dtype;
+    size_t total = carve_size({sizeof(ScoreLaunch) * (size_t)S, sizeof(long long) * (size_t)(S + 1),
+                               sizeof(unsigned long long)});
+    for (int j = 0; j < S; ++j) {
+        const refine_job &jb = jobs[j];
+        if ((st = check_score_args(c, &jb.scene, jb.cams_dev, jb.n_views, p, jb.scores_dev))) {
+            delete b;
+            return fail(c, st, "batch job %d: %s", j, std::string(c->err).c_str());
+        }
+        if (jb.scene.n < 1 || jb.scene.dtype != b->dtype || jb.n_views > kViewsPerPass || !jb.keep_mask_dev ||
+            !(jb.ratio >= 0.0 && jb.ratio < 1.0)) {
+            delete b;
+            return fail(c, REFINE_EINVAL,
+                        "batch job %d: needs n >= 1, one dtype for all jobs, n_views <= %d, a keep mask and a ratio "
+                        "in [0, 1)",
+                        j, kViewsPerPass);
+        }
+        const int64_t nk = jb.scene.n - (int64_t)floor(jb.ratio * (double)jb.scene.n);
+        if (jb.out_pos_dev && (!jb.out_attr_dev || jb.out_row_stride < nk)) {
+            delete b;
+            return fail(c, REFINE_EINVAL, "batch job %d: compaction output missing or shorter than n_keep", j);
+        }
+        b->n_keep.push_back(nk);
+        b->plans.push_back(plan_scene(c, &jb.scene, jb.n_views));
+        total += scene_bytes(b->plans.back()) + select_bytes(jb.scene.n) + compact_bytes(jb.scene.n) + 768;
+        b->max_v = std::max(b->max_v, jb.n_views);
+    }
+    cudaError_t e = cudaMalloc(&b->scratch, total);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(c, e, "batch scratch");
+    }
+    if ((e = cudaMallocHost(&b->h_res, (size_t)S * 16 + 64)) != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(c, e, "batch pinned read-back");
+    }
+    Carver cv(b->scratch);
+    b->d_launch = cv.take<ScoreLaunch>(S);
+    b->d_tile_begin = cv.take<long long>(S + 1);
+    b->d_counter = cv.take<unsigned long long>(1);
+    std::vector<ScoreLaunch> hl(S);
+    std::vector<long long> tb(S + 1, 0);
+    const long long tile = (long long)kScoreThreads * kScoreGPT;
+    for (int j = 0; j < S; ++j) {
+        b->sx.push_back(carve_scene(cv, b->plans[j]));
+        b->sel_scr.push_back(cv.take<char>(select_bytes(jobs[j].scene.n)));
+        b->cmp_scr.push_back(cv.take<char>(compact_bytes(jobs[j].scene.n)));
+        hl[j] = make_score_launch(&jobs[j].scene, b->plans[j], b->sx[j], p, 0, jobs[j].scores_dev, nullptr, false,
+                                  c->d_status);
+        tb[j + 1] = tb[j] + (jobs[j].scene.n + tile - 1) / tile;
+    }
+    b->kstar.assign(S, nullptr);
+    b->total.assign(S, nullptr);
+    b->total_tiles = tb[S];
+    e = cudaMemcpy(b->d_launch, hl.data(), sizeof(ScoreLaunch) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_tile_begin, tb.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice);
+    b->grid = score_batch_grid(c->num_sms, b->dtype, (p.flags & REFINE_FLAG_NO_PROJ) != 0, b->max_v);
+    if (b->grid > b->total_tiles) b->grid = (int)b->total_tiles;
+    const int L = std::min(8, S);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking);
+    for (int l = 0; l < L && e == cudaSuccess; ++l) {
+        cudaStream_t ls = nullptr;
+        e = cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->lanes.push_back(ls);
+    }
+    for (int k = 0; k < 2 * L + 2 && e == cudaSuccess; ++k) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->events.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(c, e, "batch set-up");
+    }
+    *out = b;
+    return REFINE_OK;
+}
+
+refine_status refine_batch_run(refine_batch *b, refine_stream_t stream)
+{
+    if (!b) return REFINE_EINVAL;
+    refine_ctx *c = b->ctx;
+    refine_status st = use_device(c);
+    if (st) return st;
+    if (!b->exec && (st = batch_record(b))) return st;
+    const cudaError_t e = cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+    c->launch_count += b->launches_per_run;
+    return REFINE_OK;
+}
+
+refine_status refine_batch_results(refine_batch *b, int64_t *n_keep_out, float *threshold_out,
+                                   refine_stream_t stream)
+{
+    if (!b) return REFINE_EINVAL;
+    refine_ctx *c = b->ctx;
+    refine_status st = use_device(c);
+    if (st) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int S = (int)b->jobs.size();
+    unsigned int *hk = static_cast<unsigned int *>(b->h_res);
+    cudaError_t e = cudaSuccess;
+    if (threshold_out)
+        for (int j = 0; j < S && e == cudaSuccess; ++j)
+            if (b->kstar[j]) e = cudaMemcpyAsync(hk + j, b->kstar[j], sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch read-back");
+    if ((st = read_status(c, s))) return st;  // synchronises
+    for (int j = 0; j < S; ++j) {
+        if (n_keep_out) n_keep_out[j] = b->n_keep[j];
+        if (threshold_out) threshold_out[j] = b->kstar[j] ? key_to_score(hk[j]) : -INFINITY;
+    }
+    return REFINE_OK;
+}
+
+int64_t refine_batch_launches(const refine_batch *b) { return b ? b->launches_per_run : -1; }
+
+void refine_batch_destroy(refine_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    cudaDeviceSynchronize();
+    batch_free(b);
+}
 
 }  // extern "C"

@@ -1,0 +1,83 @@
+"""The batched form (one persistent score launch over many scenes, replayed
+as a CUDA graph) gives bit-identical scores, masks, thresholds and
+compacted scenes to the per-scene entry points, on every replay."""
+import numpy as np
+import pytest
+
+from paper_2606_09074_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_09074_gb300 import binding as rb
+    ctx = rb.Context(0)
+    yield torch, rb, ctx
+    ctx.close()
+
+
+def upload(torch, rb, w):
+    dev = torch.device("cuda", 0)
+    pos = torch.from_numpy(w.scene.pos).to(dev)
+    if w.scene.dtype == "bf16":
+        attr = torch.from_numpy(w.scene.attr.view(np.int16)).to(dev).view(torch.bfloat16)
+    else:
+        attr = torch.from_numpy(w.scene.attr).to(dev)
+    return pos, attr, rb.cameras_to_device(w.cams, dev)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batch_equals_single(env, dtype):
+    torch, rb, ctx = env
+    specs = [(11, 3000, 7), (12, 40_000, 50), (13, 257, 3), (14, 123_457, 120), (15, 1, 1), (16, 70_001, 300)]
+    ws = []
+    for seed, n, v in specs:
+        w = synth.random_scene(seed=seed, n=n, v=v, means="core_shell")
+        if dtype == "bf16":
+            w.scene = w.scene.to_bf16()
+        ws.append(w)
+    ratios = [0.5, 0.66, 0.9, 0.0, 0.5, 0.3]
+    up = [upload(torch, rb, w) for w in ws]
+    jobs = [{"pos": p, "attr": a, "cams": c, "ratio": r} for (p, a, c), r in zip(up, ratios)]
+    batch = rb.Batch(ctx, jobs)
+    for rep in range(2):
+        batch.run()
+        assert batch.launches() >= 6 * len(jobs)  # recorded on the first run
+        nk_b, thr_b = batch.results()
+        for k, ((p, a, c), r) in enumerate(zip(up, ratios)):
+            s = ctx.score(p, a, c)
+            m, thr, nk = ctx.select(s, r)
+            op, oa, idx = ctx.compact(p, a, m, nk)
+            out = batch.outputs[k]
+            assert torch.equal(out["scores"], s), (rep, k)
+            n = p.shape[1]
+            assert torch.equal(out["mask"][: (n + 31) // 32], m[: (n + 31) // 32])
+            assert nk_b[k] == nk and thr_b[k] == thr
+            assert torch.equal(out["idx"][:nk], idx)
+            assert torch.equal(out["out_pos"][:, :nk], op)
+            assert torch.equal(out["out_attr"][:, :nk], oa)
+    ctx.check()
+    batch.close()
+
+
+def test_batch_rejects_bad_jobs(env):
+    torch, rb, ctx = env
+    w1 = synth.random_scene(seed=1, n=100, v=4)
+    w2 = synth.random_scene(seed=2, n=100, v=600)  # more views than a batch takes
+    p1, a1, c1 = upload(torch, rb, w1)
+    p2, a2, c2 = upload(torch, rb, w2)
+    with pytest.raises(rb.RefineError):
+        rb.Batch(ctx, [{"pos": p1, "attr": a1, "cams": c1, "ratio": 0.5},
+                       {"pos": p2, "attr": a2, "cams": c2, "ratio": 0.5}])
+    w3 = synth.random_scene(seed=3, n=100, v=4)
+    w3.scene = w3.scene.to_bf16()
+    p3, a3, c3 = upload(torch, rb, w3)
+    with pytest.raises(rb.RefineError):  # mixed storage types
+        rb.Batch(ctx, [{"pos": p1, "attr": a1, "cams": c1, "ratio": 0.5},
+                       {"pos": p3, "attr": a3, "cams": c3, "ratio": 0.5}])
+    with pytest.raises(rb.RefineError):
+        rb.Batch(ctx, [{"pos": p1, "attr": a1, "cams": c1, "ratio": 1.0}])
