@@ -57,6 +57,67 @@ struct SceneStats {
 // y, y^2, a(1-a), gem ratio, m_gem, m_col, m_opa, mu (3), mu^2 (3).
 constexpr int kFeatSums = 13;
 
+// Per-thread content-feature sums (kFeatSums of them) and a non-finite trap.
+struct FeatSums {
+    float s[kFeatSums];
+    float bad;  // accumulates x * 0, which is NaN iff some x was not finite
+};
+
+// Activation of one primitive (Eq. 1) and its feature terms (the readings R1,
+// R3: y = C0 (l . dc) is the luma minus its constant offset 0.5 sum(l);
+// gem = max(s) / (min(s) + eta); m_gem = product of the two largest scales;
+// m_col = |SH|_2; m_opa = alpha).  Adds to the thirteen sums and returns the
+// primitive's record (layout: PrimRec in internal.h).  *zero_q is set for a
+// zero quaternion (then R = I).
+__device__ __forceinline__ void primitive_record(FeatSums &acc, float mx, float my, float mz, float ls0, float ls1,
+                                                 float ls2, float qw, float qx, float qy, float qz, float logit,
+                                                 float dc0, float dc1, float dc2, float sumsq, float eta, float l0,
+                                                 float l1, float l2, float4 &ra, float4 &rb, float4 &rc, float4 &rd,
+                                                 bool &zero_q)
+{
+    constexpr float kC0 = 0.28209479177387814f;  // 1 / (2 sqrt(pi))
+    const float e0 = expf(ls0), e1 = expf(ls1), e2 = expf(ls2);
+    const float alpha = 1.f / (1.f + expf(-logit));
+    const float y = kC0 * fmaf(l0, dc0, fmaf(l1, dc1, l2 * dc2));
+    const float smax = fmaxf(e0, fmaxf(e1, e2)), smin = fminf(e0, fminf(e1, e2));
+    const float mg = fmaxf(fmaxf(e0 * e1, e0 * e2), e1 * e2);
+    const float mc = sqrtf(sumsq);
+    acc.s[0] += y;
+    acc.s[1] = fmaf(y, y, acc.s[1]);
+    acc.s[2] = fmaf(alpha, 1.f - alpha, acc.s[2]);
+    acc.s[3] += smax / (smin + eta);
+    acc.s[4] += mg;
+    acc.s[5] += mc;
+    acc.s[6] += alpha;
+    acc.s[7] += mx;
+    acc.s[8] += my;
+    acc.s[9] += mz;
+    acc.s[10] = fmaf(mx, mx, acc.s[10]);
+    acc.s[11] = fmaf(my, my, acc.s[11]);
+    acc.s[12] = fmaf(mz, mz, acc.s[12]);
+    acc.bad = fmaf(mx + my + mz + ls0 + ls1 + ls2 + qw + qx + qy + qz + logit + sumsq, 0.f, acc.bad);
+
+    const float qn2 = fmaf(qw, qw, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+    if (!(qn2 > 0.f)) {
+        zero_q = true;
+        qw = 1.f; qx = qy = qz = 0.f;
+    } else {
+        const float r = rsqrtf(qn2);
+        qw *= r; qx *= r; qy *= r; qz *= r;
+    }
+    const float s0 = 3.f * e0, s1 = 3.f * e1, s2 = 3.f * e2;
+    const float sm = fmaxf(s0, fmaxf(s1, s2));
+    float b2 = sm * sm * 1.0009765625f;
+    if ((s0 == 0.f) | (s1 == 0.f) | (s2 == 0.f)) b2 = -(1.f + b2);
+    // the rows of L are the columns of R(q) scaled by 3 s_k
+    ra = make_float4(mx, my, mz, b2);
+    rb = make_float4(s0 * (1.f - 2.f * (qy * qy + qz * qz)), s0 * (2.f * (qx * qy + qw * qz)),
+                     s0 * (2.f * (qx * qz - qw * qy)), s1 * (2.f * (qx * qy - qw * qz)));
+    rc = make_float4(s1 * (1.f - 2.f * (qx * qx + qz * qz)), s1 * (2.f * (qy * qz + qw * qx)),
+                     s2 * (2.f * (qx * qz + qw * qy)), s2 * (2.f * (qy * qz - qw * qx)));
+    rd = make_float4(s2 * (1.f - 2.f * (qx * qx + qy * qy)), alpha, mg, mc);
+}
+
 // ---------------------------------------------------------------- loads
 __device__ __forceinline__ float ld_attr(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ld_attr(const __nv_bfloat16 *p)

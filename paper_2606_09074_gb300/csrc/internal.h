@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/refine.h"
+#include "refine.h"
 #include "common.cuh"
 
 namespace refine {
@@ -19,16 +19,18 @@ constexpr int kScoreGPT = 2;          // primitives per thread in k_score
 constexpr int kFeatThreads = 256;
 
 // Spatial cells for the processing order of k_score: a 2^b x 2^b x 2^b grid
-// over the scene's mean +- 3 sigma box, numbered in Morton order, with b
-// chosen from n (cell_bits_for) between 4 and kMaxCellBits.
+// over the scene's mean +- 3 sigma box, numbered in Morton order, with b the
+// largest value in [kMinCellBits, kMaxCellBits] that leaves ~0.5 primitives
+// per cell or more (cell_bits_for).  Fine cells keep the counting sort's
+// atomics spread out: dense scenes put hundreds of centres in one coarse
+// cell, and atomics on one address serialise.
 constexpr int kMinCellBits = 4;
 constexpr int kMaxCellBits = 7;
-constexpr int kMaxCells = 1 << (3 * kMaxCellBits);
 constexpr int kScanThreads = 1024;
 inline int cell_bits_for(int64_t n)
 {
-    int b = 4;
-    while (b < kMaxCellBits && (int64_t(1) << (3 * (b + 1))) * 16 <= n * 2) ++b;  // ~16-32 per cell
+    int b = kMinCellBits;
+    while (b < kMaxCellBits && (int64_t(1) << (3 * (b + 1))) <= n * 2) ++b;
     return b;
 }
 inline int cell_count(int bits) { return 1 << (3 * bits); }
@@ -44,14 +46,22 @@ enum {
     kCountSlots
 };
 
+// Per-primitive record written by the feature pass, in scene order (64 B):
+//   a = (mu.x, mu.y, mu.z, b2)   b2 = 9 s_max^2 (1 + 2^-10), the footprint
+//                                bound factor; -(1 + b2) when a scale
+//                                underflowed to 0
+//   b, c, d.x = L, row-major 3x3 with rows 3 s_k r_k (r_k the k-th column of
+//                R(q)), so that L^T L = 9 Sigma
+//   d.y = alpha, d.z = m_gem, d.w = m_col
+struct __align__(16) PrimRec {
+    float4 a, b, c, d;
+};
+static_assert(sizeof(PrimRec) == 64, "primitive record layout");
+
 struct ScoreLaunch {
-    const float *pos;
-    const void *attr;
-    int dtype;
-    int64_t stride;
+    const PrimRec *recs;        // records in scene order
     int64_t n;
     const uint32_t *perm;       // processing order (a permutation of 0..n-1)
-    const float *m_col;         // per-primitive |SH|_2 from the feature pass
     const CamRec *cams;         // this pass's cameras (device, 16-byte aligned)
     int vcount;                 // cameras in this pass
     int first, last;            // first / last pass of the view set
@@ -71,8 +81,8 @@ cudaError_t launch_cam_prep(const refine_camera *cams, int V, CamRec *out, int *
                             cudaStream_t s);
 int feature_blocks(int64_t n);
 cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
-                            float eta, const float luma[3], float *m_col, double *partials, bool vec,
-                            int *status, cudaStream_t s);
+                            float eta, const float luma[3], PrimRec *recs, double *partials, int *status,
+                            cudaStream_t s);
 cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_t n,
                                      const refine_params *p, int cell_bits, SceneConsts *consts,
                                      SceneStats *stats, cudaStream_t s);
@@ -133,15 +143,9 @@ constexpr int kCmpSeg = 256;  // elements per compaction segment (8 mask words)
 cudaError_t launch_compact_count(const uint32_t *mask, int64_t n, unsigned *seg_cnt,
                                  unsigned long long *seg_off, CmpState *cs, int64_t out_stride,
                                  int grid, int *status, cudaStream_t s);
-int compact_stream_blocks(int num_sms, int dtype);
-cudaError_t launch_compact_stream(const refine_scene &in, const uint32_t *mask, const unsigned long long *seg_off,
-                                  const CmpState *cs, float *out_pos, void *out_attr, int64_t out_stride,
-                                  int32_t *out_idx, bool tma, int grid, int *status, cudaStream_t s);
-
-// TMA-fed feature pass (rows 16-byte aligned); same sums as launch_features.
-int feature_tma_blocks(int num_sms, int dtype);
-cudaError_t launch_features_tma(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
-                                float eta, const float luma[3], float *m_col, double *partials, int nblocks,
-                                int *status, cudaStream_t s);
+int compact_grid(int num_sms, int64_t n);
+cudaError_t launch_compact_scatter(const refine_scene &in, const uint32_t *mask, const unsigned long long *seg_off,
+                                   const CmpState *cs, float *out_pos, void *out_attr, int64_t out_stride,
+                                   int32_t *out_idx, int grid, cudaStream_t s);
 
 }  // namespace refine

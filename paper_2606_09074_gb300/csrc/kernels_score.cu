@@ -7,9 +7,6 @@
 
 namespace refine {
 
-// Degree-0 real spherical-harmonic basis constant 1 / (2 sqrt(pi)).
-constexpr float kSH_C0 = 0.28209479177387814f;
-
 // ---------------------------------------------------------------------
 // Camera preparation: refine_camera -> CamRec (P = K W and p = K t formed
 // in double and rounded once), with validation.
@@ -63,175 +60,78 @@ cudaError_t launch_cam_prep(const refine_camera *cams, int V, CamRec *out, int *
 }
 
 // ---------------------------------------------------------------------
-// Content features.  Per primitive (the readings R1, R3):
-//   a = sigmoid(logit), s = exp(log-scale)
-//   y = C0 (l . dc)            luma minus its constant offset 0.5 sum(l)
-//   gem = max(s) / (min(s) + eta), m_gem = product of the two largest scales,
-//   m_col = |SH|_2 over 48 coefficients (written out), m_opa = a
-// Thirteen sums (the feature sums and the first two moments of the means)
-// are kept per thread in float and reduced per block in a fixed double tree;
-// the grid depends only on n, so the sums do too.
+// Content features.  One primitive per thread: its 59 attribute rows are
+// read with coalesced loads (all in flight at once), its record and its
+// feature terms formed (primitive_record), thirteen sums per thread kept in
+// float and reduced per block in a fixed double tree.
 // ---------------------------------------------------------------------
 template <typename AT>
-struct Row4;
-
-template <>
-struct Row4<float> {
-    __device__ static void load(const float *row, int64_t i, float (&v)[4])
-    {
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(row + i));
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-    }
-};
-
-template <>
-struct Row4<__nv_bfloat16> {
-    __device__ static void load(const __nv_bfloat16 *row, int64_t i, float (&v)[4])
-    {
-        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row + i));
-        v[0] = __uint_as_float(q.x << 16);
-        v[1] = __uint_as_float(q.x & 0xffff0000u);
-        v[2] = __uint_as_float(q.y << 16);
-        v[3] = __uint_as_float(q.y & 0xffff0000u);
-    }
-};
-
-struct FeatAcc {
-    float s[kFeatSums];
-    float bad;  // accumulates x * 0, which is NaN iff some x was not finite
-};
-
-__device__ __forceinline__ float feat_one(FeatAcc &acc, float mx, float my, float mz, float ls0, float ls1,
-                                          float ls2, float logit, float dc0, float dc1, float dc2, float sumsq,
-                                          float eta, float l0, float l1, float l2)
-{
-    const float e0 = expf(ls0), e1 = expf(ls1), e2 = expf(ls2);
-    const float alpha = 1.f / (1.f + expf(-logit));
-    const float y = kSH_C0 * fmaf(l0, dc0, fmaf(l1, dc1, l2 * dc2));
-    const float smax = fmaxf(e0, fmaxf(e1, e2)), smin = fminf(e0, fminf(e1, e2));
-    const float mg = fmaxf(fmaxf(e0 * e1, e0 * e2), e1 * e2);
-    const float mc = sqrtf(sumsq);
-    acc.s[0] += y;
-    acc.s[1] = fmaf(y, y, acc.s[1]);
-    acc.s[2] = fmaf(alpha, 1.f - alpha, acc.s[2]);
-    acc.s[3] += smax / (smin + eta);
-    acc.s[4] += mg;
-    acc.s[5] += mc;
-    acc.s[6] += alpha;
-    acc.s[7] += mx;
-    acc.s[8] += my;
-    acc.s[9] += mz;
-    acc.s[10] = fmaf(mx, mx, acc.s[10]);
-    acc.s[11] = fmaf(my, my, acc.s[11]);
-    acc.s[12] = fmaf(mz, mz, acc.s[12]);
-    acc.bad = fmaf(mx + my + mz + ls0 + ls1 + ls2 + logit + sumsq, 0.f, acc.bad);
-    return mc;
-}
-
-template <typename AT, bool VEC>
 __global__ void __launch_bounds__(kFeatThreads) k_features(const float *__restrict__ pos,
-                                                           const AT *__restrict__ attr, int64_t stride,
-                                                           int64_t n, float eta, float l0, float l1,
-                                                           float l2, float *__restrict__ m_col,
+                                                           const AT *__restrict__ attr, int64_t S, int64_t n,
+                                                           float eta, float l0, float l1, float l2,
+                                                           PrimRec *__restrict__ recs,
                                                            double *__restrict__ partials, int *status)
 {
-    FeatAcc acc;
+    FeatSums acc;
 #pragma unroll
     for (int k = 0; k < kFeatSums; ++k) acc.s[k] = 0.f;
     acc.bad = 0.f;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x * 4;
-    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; base < n; base += step) {
-        if (VEC && base + 4 <= n) {
-            float px[4], py[4], pz[4], l[3][4], lg[4], dc[3][4], sq[4], v[4];
-            Row4<float>::load(pos, base, px);
-            Row4<float>::load(pos + stride, base, py);
-            Row4<float>::load(pos + 2 * stride, base, pz);
+    bool zero_q = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float sq = 0.f;
 #pragma unroll
-            for (int r = 0; r < 3; ++r) Row4<AT>::load(attr + r * stride, base, l[r]);
-            Row4<AT>::load(attr + 7 * stride, base, lg);
-#pragma unroll
-            for (int r = 0; r < 3; ++r) Row4<AT>::load(attr + (8 + r) * stride, base, dc[r]);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                sq[k] = fmaf(dc[0][k], dc[0][k], fmaf(dc[1][k], dc[1][k], dc[2][k] * dc[2][k]));
-#pragma unroll 15
-            for (int r = 11; r < 56; ++r) {
-                Row4<AT>::load(attr + r * stride, base, v);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) sq[k] = fmaf(v[k], v[k], sq[k]);
-            }
-            float4 mc;
-            mc.x = feat_one(acc, px[0], py[0], pz[0], l[0][0], l[1][0], l[2][0], lg[0], dc[0][0], dc[1][0], dc[2][0],
-                            sq[0], eta, l0, l1, l2);
-            mc.y = feat_one(acc, px[1], py[1], pz[1], l[0][1], l[1][1], l[2][1], lg[1], dc[0][1], dc[1][1], dc[2][1],
-                            sq[1], eta, l0, l1, l2);
-            mc.z = feat_one(acc, px[2], py[2], pz[2], l[0][2], l[1][2], l[2][2], lg[2], dc[0][2], dc[1][2], dc[2][2],
-                            sq[2], eta, l0, l1, l2);
-            mc.w = feat_one(acc, px[3], py[3], pz[3], l[0][3], l[1][3], l[2][3], lg[3], dc[0][3], dc[1][3], dc[2][3],
-                            sq[3], eta, l0, l1, l2);
-            *reinterpret_cast<float4 *>(m_col + base) = mc;
-        } else {
-            for (int64_t i = base; i < n && i < base + 4; ++i) {
-                float sq = 0.f;
-                for (int r = 8; r < 56; ++r) {
-                    const float x = ld_attr(attr + r * stride + i);
-                    sq = fmaf(x, x, sq);
-                }
-                m_col[i] = feat_one(acc, __ldg(pos + i), __ldg(pos + stride + i), __ldg(pos + 2 * stride + i),
-                                    ld_attr(attr + i), ld_attr(attr + stride + i), ld_attr(attr + 2 * stride + i),
-                                    ld_attr(attr + 7 * stride + i), ld_attr(attr + 8 * stride + i),
-                                    ld_attr(attr + 9 * stride + i), ld_attr(attr + 10 * stride + i), sq, eta,
-                                    l0, l1, l2);
-            }
+        for (int r = 8; r < 56; ++r) {
+            const float x = ld_attr(attr + r * S + i);
+            sq = fmaf(x, x, sq);
         }
+        float4 ra, rb, rc, rd;
+        primitive_record(acc, __ldg(pos + i), __ldg(pos + S + i), __ldg(pos + 2 * S + i), ld_attr(attr + i),
+                         ld_attr(attr + S + i), ld_attr(attr + 2 * S + i), ld_attr(attr + 3 * S + i),
+                         ld_attr(attr + 4 * S + i), ld_attr(attr + 5 * S + i), ld_attr(attr + 6 * S + i),
+                         ld_attr(attr + 7 * S + i), ld_attr(attr + 8 * S + i), ld_attr(attr + 9 * S + i),
+                         ld_attr(attr + 10 * S + i), sq, eta, l0, l1, l2, ra, rb, rc, rd, zero_q);
+        PrimRec *r = recs + i;
+        r->a = ra; r->b = rb; r->c = rc; r->d = rd;
     }
     if (!isfinite(acc.bad)) set_status(status, kEnonfinite);
+    if (zero_q) set_status(status, kEinval);
 
     __shared__ double red[kFeatSums][kFeatThreads];
 #pragma unroll
     for (int k = 0; k < kFeatSums; ++k) red[k][threadIdx.x] = (double)acc.s[k];
     __syncthreads();
-    for (int s = kFeatThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) {
+    for (int h = kFeatThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
 #pragma unroll
-            for (int k = 0; k < kFeatSums; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+            for (int k = 0; k < kFeatSums; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
         }
         __syncthreads();
     }
     if (threadIdx.x < kFeatSums) partials[(int64_t)blockIdx.x * kFeatSums + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// A single wave on a 152-SM part (4 CTAs of 256 threads per SM); the grid
+// depends only on n, so the per-block sums, and the scene constants, do too.
 int feature_blocks(int64_t n)
 {
-    const int64_t per_block = (int64_t)kFeatThreads * 4 * 2;
-    int64_t b = (n + per_block - 1) / per_block;
+    int64_t b = (n + (int64_t)kFeatThreads * 8 - 1) / ((int64_t)kFeatThreads * 8);
     if (b < 1) b = 1;
-    if (b > 1024) b = 1024;
+    if (b > 608) b = 608;
     return (int)b;
 }
 
 cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
-                            float eta, const float luma[3], float *m_col, double *partials, bool vec,
-                            int *status, cudaStream_t s)
+                            float eta, const float luma[3], PrimRec *recs, double *partials, int *status,
+                            cudaStream_t s)
 {
     const int nb = feature_blocks(n);
-    if (dtype == REFINE_BF16) {
-        const __nv_bfloat16 *a = static_cast<const __nv_bfloat16 *>(attr);
-        if (vec)
-            k_features<__nv_bfloat16, true><<<nb, kFeatThreads, 0, s>>>(pos, a, stride, n, eta, luma[0], luma[1],
-                                                                       luma[2], m_col, partials, status);
-        else
-            k_features<__nv_bfloat16, false><<<nb, kFeatThreads, 0, s>>>(pos, a, stride, n, eta, luma[0], luma[1],
-                                                                        luma[2], m_col, partials, status);
-    } else {
-        const float *a = static_cast<const float *>(attr);
-        if (vec)
-            k_features<float, true><<<nb, kFeatThreads, 0, s>>>(pos, a, stride, n, eta, luma[0], luma[1], luma[2],
-                                                               m_col, partials, status);
-        else
-            k_features<float, false><<<nb, kFeatThreads, 0, s>>>(pos, a, stride, n, eta, luma[0], luma[1],
-                                                                luma[2], m_col, partials, status);
-    }
+    if (dtype == REFINE_BF16)
+        k_features<__nv_bfloat16><<<nb, kFeatThreads, 0, s>>>(pos, static_cast<const __nv_bfloat16 *>(attr), stride,
+                                                              n, eta, luma[0], luma[1], luma[2], recs, partials,
+                                                              status);
+    else
+        k_features<float><<<nb, kFeatThreads, 0, s>>>(pos, static_cast<const float *>(attr), stride, n, eta, luma[0],
+                                                      luma[1], luma[2], recs, partials, status);
     return cudaGetLastError();
 }
 
@@ -299,12 +199,18 @@ cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_
 }
 
 // ---------------------------------------------------------------------
-// Processing order.  Primitives are bucketed by a 64^3 Morton-numbered grid
-// (counting sort) so that the 32 lanes of a warp hold nearby primitives and
-// tend to take the same side of each view's frustum edges.  The order only
-// affects speed: every primitive's score is computed by one thread with the
-// views in a fixed order, whatever its position.
+// Processing order.  Primitives are sorted by their cell in a 2^b x 2^b x
+// 2^b grid over the mean +- 3 sigma box of the centres, cells numbered in
+// Morton order (a counting sort: count, scan, scatter), so that the 32
+// lanes of a warp hold nearby primitives and tend to take the same side of
+// each view's frustum edges.  The order only affects speed: every
+// primitive's score is computed by one thread with the views in a fixed
+// order, whatever its position, so the sort need not be stable (the
+// scatter's atomics order the primitives of a cell arbitrarily).  Each
+// thread keeps kSortU primitives in flight.
 // ---------------------------------------------------------------------
+constexpr int kSortU = 4;
+
 __device__ __forceinline__ uint32_t spread3(uint32_t x)
 {
     uint32_t r = 0;
@@ -324,27 +230,48 @@ __global__ void k_cells(const float *__restrict__ pos, int64_t stride, int64_t n
 {
     const SceneConsts c = *consts;
     const float top = (float)((1 << cell_bits) - 1);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t id = spread3(quantise(__ldg(pos + i), c.lo[0], c.qscale[0], top)) |
-                            (spread3(quantise(__ldg(pos + stride + i), c.lo[1], c.qscale[1], top)) << 1) |
-                            (spread3(quantise(__ldg(pos + 2 * stride + i), c.lo[2], c.qscale[2], top)) << 2);
-        cell[i] = id;
-        atomicAdd(&counts[id], 1u);
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += kSortU * step) {
+        float x[kSortU], y[kSortU], z[kSortU];
+#pragma unroll
+        for (int u = 0; u < kSortU; ++u) {
+            const int64_t j = i + u * step;
+            const bool ok = j < n;
+            x[u] = ok ? __ldg(pos + j) : 0.f;
+            y[u] = ok ? __ldg(pos + stride + j) : 0.f;
+            z[u] = ok ? __ldg(pos + 2 * stride + j) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortU; ++u) {
+            const int64_t j = i + u * step;
+            if (j >= n) break;
+            const uint32_t id = spread3(quantise(x[u], c.lo[0], c.qscale[0], top)) |
+                                (spread3(quantise(y[u], c.lo[1], c.qscale[1], top)) << 1) |
+                                (spread3(quantise(z[u], c.lo[2], c.qscale[2], top)) << 2);
+            cell[j] = id;
+            atomicAdd(&counts[id], 1u);
+        }
     }
+}
+
+static int sort_grid(int num_sms, int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
+    if (g < 1) g = 1;
+    return (int)g;
 }
 
 cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, int cell_bits, const SceneConsts *consts,
                          uint32_t *cell, unsigned *counts, int num_sms, cudaStream_t s)
 {
-    int64_t g = (n + 255) / 256;
-    if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
-    if (g < 1) g = 1;
-    k_cells<<<(int)g, 256, 0, s>>>(pos, stride, n, cell_bits, consts, cell, counts);
+    k_cells<<<sort_grid(num_sms, n), 256, 0, s>>>(pos, stride, n, cell_bits, consts, cell, counts);
     return cudaGetLastError();
 }
 
-// Exclusive scan of the cell counts: local offsets within blocks of 1024
-// cells, then the last block turns the block totals into block offsets.
+// Exclusive scan of the cell counts: local offsets within blocks of
+// kScanThreads cells, then the last block turns the block totals into block
+// offsets, so cell c starts at bsum[c / kScanThreads] + off_local[c].
 __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *wsum)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -405,7 +332,7 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(const unsigned *__re
 cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done, int cell_bits,
                              cudaStream_t s)
 {
-    const int cells = 1 << (3 * cell_bits);
+    const int cells = cell_count(cell_bits);
     k_cell_scan<<<cells / kScanThreads, kScanThreads, 0, s>>>(counts, off_local, bsum, done);
     return cudaGetLastError();
 }
@@ -414,10 +341,24 @@ __global__ void k_cell_scatter(const uint32_t *__restrict__ cell, int64_t n, uns
                                const unsigned *__restrict__ off_local, const unsigned *__restrict__ boff,
                                uint32_t *__restrict__ perm)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = cell[i];
-        const unsigned slot = boff[c / kScanThreads] + off_local[c] + atomicSub(&counts[c], 1u) - 1u;
-        perm[slot] = (uint32_t)i;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += kSortU * step) {
+        uint32_t c[kSortU], slot[kSortU];
+#pragma unroll
+        for (int u = 0; u < kSortU; ++u) {
+            const int64_t j = i + u * step;
+            c[u] = j < n ? __ldg(cell + j) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortU; ++u) {
+            const int64_t j = i + u * step;
+            if (j < n) slot[u] = atomicSub(&counts[c[u]], 1u) - 1u;
+        }
+#pragma unroll
+        for (int u = 0; u < kSortU; ++u) {
+            const int64_t j = i + u * step;
+            if (j < n) perm[boff[c[u] / kScanThreads] + off_local[c[u]] + slot[u]] = (uint32_t)j;
+        }
     }
 }
 
@@ -425,10 +366,7 @@ cudaError_t launch_cell_scatter(const uint32_t *cell, int64_t n, unsigned *count
                                 const unsigned *off_local, const unsigned *bsum, uint32_t *perm,
                                 int num_sms, cudaStream_t s)
 {
-    int64_t g = (n + 255) / 256;
-    if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
-    if (g < 1) g = 1;
-    k_cell_scatter<<<(int)g, 256, 0, s>>>(cell, n, counts, off_local, bsum, perm);
+    k_cell_scatter<<<sort_grid(num_sms, n), 256, 0, s>>>(cell, n, counts, off_local, bsum, perm);
     return cudaGetLastError();
 }
 
@@ -693,30 +631,20 @@ __device__ __forceinline__ void fence_proxy_async_shared()
 // Scores one tile of kScoreThreads * kScoreGPT primitives of the processing
 // order starting at `base`; `next_base` (or -1) is the tile this CTA takes
 // next, whose primitives are pulled towards L2 meanwhile.
-template <typename AT, bool NOPROJ, bool COUNT>
+template <bool NOPROJ, bool COUNT>
 __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *cs, const SceneConsts &sc,
                                            int64_t base, int64_t next_base, unsigned long long (&cnt)[kCountSlots])
 {
-    const AT *attr = static_cast<const AT *>(a.attr);
-    const int64_t S = a.stride;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (next_base >= 0) {
 #pragma unroll
         for (int g = 0; g < kScoreGPT; ++g) {
             const int64_t j = next_base + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
-            if (j < a.n) {
-                const int64_t i = __ldg(a.perm + j);
-                prefetch_l2(a.pos + i);
-                prefetch_l2(a.pos + S + i);
-                prefetch_l2(a.pos + 2 * S + i);
-#pragma unroll
-                for (int r = 0; r < 8; ++r) prefetch_l2(attr + r * S + i);
-                prefetch_l2(a.m_col + i);
-            }
+            if (j < a.n) prefetch_l2(a.recs + __ldg(a.perm + j));
         }
     }
     PairIn p[kScoreGPT];
-    float acc[kScoreGPT], alpha[kScoreGPT], mg[kScoreGPT];
+    float acc[kScoreGPT];
     int64_t idx[kScoreGPT];
     bool valid[kScoreGPT];
     bool degen = false;
@@ -724,53 +652,22 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
 #pragma unroll
     for (int g = 0; g < kScoreGPT; ++g) {
         const int64_t j = base + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
-        float ls0 = 0.f, ls1 = 0.f, ls2 = 0.f, qw = 1.f, qx = 0.f, qy = 0.f, qz = 0.f, lg = 0.f;
-        p[g].mx = p[g].my = p[g].mz = 0.f;
+        float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
         idx[g] = -1;
         acc[g] = 0.f;
         valid[g] = j < a.n;
         if (valid[g]) {
             const int64_t i = __ldg(a.perm + j);
             idx[g] = i;
-            p[g].mx = __ldg(a.pos + i);
-            p[g].my = __ldg(a.pos + S + i);
-            p[g].mz = __ldg(a.pos + 2 * S + i);
-            ls0 = ld_attr(attr + i);
-            ls1 = ld_attr(attr + S + i);
-            ls2 = ld_attr(attr + 2 * S + i);
-            qw = ld_attr(attr + 3 * S + i);
-            qx = ld_attr(attr + 4 * S + i);
-            qy = ld_attr(attr + 5 * S + i);
-            qz = ld_attr(attr + 6 * S + i);
-            lg = ld_attr(attr + 7 * S + i);
+            const PrimRec *r = a.recs + i;
+            ra = __ldg(&r->a); rb = __ldg(&r->b); rc = __ldg(&r->c); rd = __ldg(&r->d);
             if (!a.first) acc[g] = a.running[i];
-            if (!isfinite(fmaf(qw + qx + qy + qz, 0.f, 0.f))) set_status(a.status, kEnonfinite);
         }
-        const float qn2 = fmaf(qw, qw, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
-        if (!(qn2 > 0.f)) {
-            if (valid[g]) set_status(a.status, kEinval);
-            qw = 1.f; qx = qy = qz = 0.f;
-        } else {
-            const float r = rsqrtf(qn2);
-            qw *= r; qx *= r; qy *= r; qz *= r;
-        }
-        const float e0 = expf(ls0), e1 = expf(ls1), e2 = expf(ls2);
-        alpha[g] = 1.f / (1.f + expf(-lg));
-        mg[g] = fmaxf(fmaxf(e0 * e1, e0 * e2), e1 * e2);
-        const float s0 = 3.f * e0, s1 = 3.f * e1, s2 = 3.f * e2;
-        const float smax = fmaxf(s0, fmaxf(s1, s2));
-        p[g].b2 = smax * smax * 1.0009765625f;
-        degen |= (s0 == 0.f) | (s1 == 0.f) | (s2 == 0.f);
-        // the rows of L are the columns of R(q) scaled by 3 s_k
-        p[g].L[0] = s0 * (1.f - 2.f * (qy * qy + qz * qz));
-        p[g].L[1] = s0 * (2.f * (qx * qy + qw * qz));
-        p[g].L[2] = s0 * (2.f * (qx * qz - qw * qy));
-        p[g].L[3] = s1 * (2.f * (qx * qy - qw * qz));
-        p[g].L[4] = s1 * (1.f - 2.f * (qx * qx + qz * qz));
-        p[g].L[5] = s1 * (2.f * (qy * qz + qw * qx));
-        p[g].L[6] = s2 * (2.f * (qx * qz + qw * qy));
-        p[g].L[7] = s2 * (2.f * (qy * qz - qw * qx));
-        p[g].L[8] = s2 * (1.f - 2.f * (qx * qx + qy * qy));
+        p[g].mx = ra.x; p[g].my = ra.y; p[g].mz = ra.z; p[g].b2 = ra.w;
+        p[g].L[0] = rb.x; p[g].L[1] = rb.y; p[g].L[2] = rb.z; p[g].L[3] = rb.w;
+        p[g].L[4] = rc.x; p[g].L[5] = rc.y; p[g].L[6] = rc.z; p[g].L[7] = rc.w;
+        p[g].L[8] = rd.x;
+        degen |= ra.w < 0.f;
         if (valid[g]) {
             lo[0] = fminf(lo[0], p[g].mx); hi[0] = fmaxf(hi[0], p[g].mx);
             lo[1] = fminf(lo[1], p[g].my); hi[1] = fmaxf(hi[1], p[g].my);
@@ -808,14 +705,14 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
         }
         const float Ssum = acc[g];
         if (a.view_sum) a.view_sum[i] = Ssum;
-        const float coupled =
-            fmaf(sc.kappa[0], mg[g], fmaf(sc.kappa[1], __ldg(a.m_col + i), sc.kappa[2] * alpha[g]));
-        const float A = ((a.flags & REFINE_FLAG_NO_VIS) ? 1.f : alpha[g]) * (Ssum * a.inv_views);
+        const float4 rd = __ldg(&a.recs[i].d);  // (L8, alpha, m_gem, m_col)
+        const float coupled = fmaf(sc.kappa[0], rd.z, fmaf(sc.kappa[1], rd.w, sc.kappa[2] * rd.y));
+        const float A = ((a.flags & REFINE_FLAG_NO_VIS) ? 1.f : rd.y) * (Ssum * a.inv_views);
         a.scores[i] = A * coupled;
     }
 }
 
-template <typename AT, bool NOPROJ, bool COUNT>
+template <bool NOPROJ, bool COUNT>
 __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -845,7 +742,7 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
     const SceneConsts sc = *a.consts;
     const int64_t tile = (int64_t)blockDim.x * kScoreGPT;
     for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile)
-        score_tile<AT, NOPROJ, COUNT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
+        score_tile<NOPROJ, COUNT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
     if (COUNT) {
         const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -863,7 +760,7 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 // by scene); when a CTA moves to another scene it restages that scene's
 // cameras by TMA.  Every tile is scored by score_tile exactly as in
 // k_score, so a scene's scores are the same alone and in a batch.
-template <typename AT, bool NOPROJ>
+template <bool NOPROJ>
 __global__ void __launch_bounds__(kScoreThreads, 3) k_score_batch(BatchLaunch b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -918,25 +815,21 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_batch(BatchLaunch b)
             cur = sidx;
         }
         const SceneConsts sc = *a.consts;
-        score_tile<AT, NOPROJ, false>(a, cs, sc, base, -1, cnt);
+        score_tile<NOPROJ, false>(a, cs, sc, base, -1, cnt);
         __syncthreads();  // the cameras and s_scene are free again
     }
 }
 
-template <typename AT, bool NOPROJ, bool COUNT>
+template <bool NOPROJ, bool COUNT>
 static const void *score_fn()
 {
-    return reinterpret_cast<const void *>(&k_score<AT, NOPROJ, COUNT>);
+    return reinterpret_cast<const void *>(&k_score<NOPROJ, COUNT>);
 }
 
-static const void *pick_score(int dtype, bool noproj, bool count)
+static const void *pick_score(bool noproj, bool count)
 {
-    if (dtype == REFINE_BF16) {
-        if (count) return noproj ? score_fn<__nv_bfloat16, true, true>() : score_fn<__nv_bfloat16, false, true>();
-        return noproj ? score_fn<__nv_bfloat16, true, false>() : score_fn<__nv_bfloat16, false, false>();
-    }
-    if (count) return noproj ? score_fn<float, true, true>() : score_fn<float, false, true>();
-    return noproj ? score_fn<float, true, false>() : score_fn<float, false, false>();
+    if (count) return noproj ? score_fn<true, true>() : score_fn<false, true>();
+    return noproj ? score_fn<true, false>() : score_fn<false, false>();
 }
 
 int score_grid(int num_sms, int64_t n, int vcount)
@@ -944,7 +837,7 @@ int score_grid(int num_sms, int64_t n, int vcount)
     // Persistent grid: as many CTAs as fit per SM, capped by the tile count.
     int per_sm = 0;
     const size_t smem = (size_t)vcount * sizeof(CamRec);
-    const void *fn = pick_score(REFINE_F32, false, false);
+    const void *fn = pick_score(false, false);
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kScoreThreads, smem) != cudaSuccess ||
         per_sm < 1) {
@@ -960,7 +853,7 @@ int score_grid(int num_sms, int64_t n, int vcount)
 
 cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s)
 {
-    const void *fn = pick_score(a.dtype, (a.flags & REFINE_FLAG_NO_PROJ) != 0, a.need != nullptr);
+    const void *fn = pick_score((a.flags & REFINE_FLAG_NO_PROJ) != 0, a.need != nullptr);
     const size_t smem = (size_t)a.vcount * sizeof(CamRec);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -971,16 +864,16 @@ cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s)
     return cudaLaunchKernel(fn, dim3(a.grid), dim3(kScoreThreads), args, smem, s);
 }
 
-template <typename AT, bool NOPROJ>
+template <bool NOPROJ>
 static const void *batch_fn()
 {
-    return reinterpret_cast<const void *>(&k_score_batch<AT, NOPROJ>);
+    return reinterpret_cast<const void *>(&k_score_batch<NOPROJ>);
 }
 
 int score_batch_grid(int num_sms, int dtype, bool noproj, int max_vcount)
 {
-    const void *fn = dtype == REFINE_BF16 ? (noproj ? batch_fn<__nv_bfloat16, true>() : batch_fn<__nv_bfloat16, false>())
-                                          : (noproj ? batch_fn<float, true>() : batch_fn<float, false>());
+    (void)dtype;
+    const void *fn = noproj ? batch_fn<true>() : batch_fn<false>();
     const size_t smem = (size_t)max_vcount * sizeof(CamRec);
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -993,8 +886,8 @@ int score_batch_grid(int num_sms, int dtype, bool noproj, int max_vcount)
 
 cudaError_t launch_score_batch(const BatchLaunch &b, int dtype, bool noproj, int max_vcount, int grid, cudaStream_t s)
 {
-    const void *fn = dtype == REFINE_BF16 ? (noproj ? batch_fn<__nv_bfloat16, true>() : batch_fn<__nv_bfloat16, false>())
-                                          : (noproj ? batch_fn<float, true>() : batch_fn<float, false>());
+    (void)dtype;
+    const void *fn = noproj ? batch_fn<true>() : batch_fn<false>();
     const size_t smem = (size_t)max_vcount * sizeof(CamRec);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -84,7 +84,6 @@ struct refine_ctx {
     double ms[K_NCLASS] = {0};
     int64_t launches[K_NCLASS] = {0};
     int64_t launch_count = 0;
-    int score_gpt = 2;
 };
 
 namespace {
@@ -197,13 +196,6 @@ refine_status check_scene(refine_ctx *c, const refine_scene *s)
 }
 
 // Rows may be read with 16-byte vector loads.
-bool scene_vec_ok(const refine_scene *s)
-{
-    const size_t es = s->dtype == REFINE_BF16 ? 2 : 4;
-    return aligned16(s->pos) && aligned16(s->attr) && ((size_t)s->row_stride * 4) % 16 == 0 &&
-           ((size_t)s->row_stride * es) % 16 == 0;
-}
-
 // Reads back and clears the device status word (synchronises `s`).
 refine_status read_status(refine_ctx *c, cudaStream_t s)
 {
@@ -229,14 +221,13 @@ struct ScenePlan {
     int64_t n = 0;
     int V = 0;
     bool multipass = false;
-    bool vec = false;
     int nb = 1;    // feature-pass blocks
     int bits = 4;  // processing-order grid resolution
 };
 
 struct SceneScratch {
     CamRec *cams;
-    float *m_col;
+    PrimRec *recs;
     double *partials;
     SceneConsts *consts;
     SceneStats *stats;
@@ -255,13 +246,7 @@ ScenePlan plan_scene(const refine_ctx *c, const refine_scene *sc, int V)
     pl.n = sc->n;
     pl.V = V;
     pl.multipass = V > kViewsPerPass;
-    pl.vec = scene_vec_ok(sc);
     pl.nb = feature_blocks(pl.n);
-    if (pl.vec) {
-        const int64_t chunks = pl.n / 256 + 1;
-        pl.nb = feature_tma_blocks(c->num_sms, sc->dtype);
-        if (pl.nb > chunks) pl.nb = (int)chunks;
-    }
     pl.bits = cell_bits_for(pl.n);
     return pl;
 }
@@ -269,7 +254,7 @@ ScenePlan plan_scene(const refine_ctx *c, const refine_scene *sc, int V)
 size_t scene_bytes(const ScenePlan &pl)
 {
     const size_t n = (size_t)pl.n, cells = (size_t)cell_count(pl.bits);
-    return carve_size({sizeof(CamRec) * (size_t)pl.V, sizeof(float) * n, sizeof(double) * kFeatSums * 1024,
+    return carve_size({sizeof(CamRec) * (size_t)pl.V, sizeof(PrimRec) * n, sizeof(double) * kFeatSums * 1024,
                        sizeof(SceneConsts), sizeof(SceneStats), sizeof(uint32_t) * n,
                        sizeof(unsigned) * (cells + 64), sizeof(unsigned) * cells,
                        sizeof(unsigned) * (cells / kScanThreads), sizeof(uint32_t) * n,
@@ -282,7 +267,7 @@ SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
     const int cells = cell_count(pl.bits);
     SceneScratch x;
     x.cams = cv.take<CamRec>(pl.V);
-    x.m_col = cv.take<float>(n);
+    x.recs = cv.take<PrimRec>(n);
     x.partials = cv.take<double>(kFeatSums * 1024);
     x.consts = cv.take<SceneConsts>(1);
     x.stats = cv.take<SceneStats>(1);
@@ -310,11 +295,8 @@ refine_status enqueue_prep(refine_ctx *c, L &&run, const refine_scene *sc, const
     refine_status st;
     if ((st = run(K_CAM_PREP, [&] { return launch_cam_prep(cams, pl.V, x.cams, status, s); }))) return st;
     if ((st = run(K_FEATURES, [&] {
-             if (pl.vec)
-                 return launch_features_tma(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, x.m_col,
-                                            x.partials, pl.nb, status, s);
-             return launch_features(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, x.m_col,
-                                    x.partials, false, status, s);
+             return launch_features(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, x.recs,
+                                    x.partials, status, s);
          })))
         return st;
     if ((st = run(K_FEAT_FINAL,
@@ -335,12 +317,8 @@ ScoreLaunch make_score_launch(const refine_scene *sc, const ScenePlan &pl, const
                               const refine_params &p, int v0, float *scores, float *view_sum, bool count, int *status)
 {
     ScoreLaunch a;
-    a.pos = sc->pos;
-    a.attr = sc->attr;
-    a.dtype = sc->dtype;
-    a.stride = sc->row_stride;
+    a.recs = x.recs;
     a.perm = x.perm;
-    a.m_col = x.m_col;
     a.n = pl.n;
     a.cams = x.cams + v0;
     a.vcount = pl.V - v0 < kViewsPerPass ? pl.V - v0 : kViewsPerPass;
@@ -486,12 +464,9 @@ refine_status enqueue_compact(refine_ctx *c, L &&run, const refine_scene *in, co
              return launch_compact_count(mask, n, seg_cnt, seg_off, cs, out_stride, (int)cgrid, status, s);
          })))
         return st;
-    const bool tma = scene_vec_ok(in);
-    int64_t sgrid = tma ? compact_stream_blocks(c->num_sms, in->dtype) : (int64_t)c->num_sms * 4;
-    if (sgrid > nseg) sgrid = nseg;
+    const int sgrid = compact_grid(c->num_sms, n);
     if ((st = run(K_CMP_SCATTER, [&] {
-             return launch_compact_stream(*in, mask, seg_off, cs, out_pos, out_attr, out_stride, idx, tma, (int)sgrid,
-                                          status, s);
+             return launch_compact_scatter(*in, mask, seg_off, cs, out_pos, out_attr, out_stride, idx, sgrid, s);
          })))
         return st;
     *total_dev = &cs->total;
@@ -557,10 +532,6 @@ refine_status refine_ctx_create(refine_ctx **out, int device)
         if (c->d_status) cudaFree(c->d_status);
         delete c;
         return REFINE_ECUDA;
-    }
-    if (const char *g = getenv("REFINE_SCORE_GPT")) {
-        int v = atoi(g);
-        if (v == 1 || v == 2) c->score_gpt = v;
     }
     *out = c;
     return REFINE_OK;
