@@ -255,8 +255,8 @@ typedef struct refine_job {
 
 typedef struct refine_batch refine_batch;
 
-/* Builds a batch of n_jobs scenes (1 <= n_jobs <= 4096, one storage dtype,
- * n >= 1 each, n_views <= 512 each; the jobs array is copied).  Allocates
+/* Builds a batch of n_jobs scenes (1 <= n_jobs <= 4096, n >= 1 and
+ * n_views <= 512 each, storage types may differ; the jobs array is copied).  Allocates
  * all scratch up front (released by refine_batch_destroy).  EINVAL on a bad
  * job (refine_last_error(ctx) names it), ENOMEM if the scratch does not fit. */
 refine_status refine_batch_create(refine_ctx *ctx, const refine_job *jobs, int32_t n_jobs,
@@ -278,6 +278,104 @@ int64_t refine_batch_launches(const refine_batch *batch);
 
 /* Releases the batch (synchronising its device first).  NULL is a no-op. */
 void refine_batch_destroy(refine_batch *batch);
+
+/* ------------------------------------------------------ request queue
+ * A serving loop for pruning requests (Sec. 3.3 applied to a stream of
+ * scenes).  Two native threads own the GPU work:
+ *   - the dispatcher admits pending requests in arrival order while the
+ *     device bytes of the admitted ones fit the queue's HBM budget and a
+ *     slot is free; each admitted request gets a slot (its own CUDA stream)
+ *     and one device block from the queue's memory pool, into which its
+ *     scene and cameras are copied.  All requests admitted together form a
+ *     round: their preparation runs on their slot streams, ONE persistent
+ *     launch scores all of them (the batched kernel), then selection,
+ *     compaction and the copies back run on the slot streams again.  A
+ *     round is issued as soon as it is formed, while earlier rounds are
+ *     still on the GPU, so requests that arrive meanwhile overlap with them
+ *     (continuous batching);
+ *   - the completion thread retires requests whose GPU work has finished:
+ *     it finishes copies into pageable host buffers, records the result,
+ *     frees the device block and returns its bytes to the budget.
+ * A request's results are bit-identical to refine_score + refine_select +
+ * refine_compact on the same scene, whatever else is in flight. */
+typedef struct refine_queue refine_queue;
+
+/* One pruning request.  Every pointer is host memory owned by the caller;
+ * inputs are read, and outputs written, between submission and the moment
+ * the request's result is reported by refine_queue_poll, so all of them
+ * must stay valid until then.  Page-locked buffers (cudaHostAlloc or
+ * cudaHostRegister) are copied asynchronously; pageable ones are copied by
+ * the queue's threads synchronously, which is slower. */
+typedef struct refine_request {
+    int64_t n;                       /* primitives, 1 .. 2^31 - 1                           */
+    int32_t dtype;                   /* REFINE_F32 or REFINE_BF16 (attribute rows)          */
+    int32_t n_views;                 /* 1 .. 512                                           */
+    const float *pos_host;           /* [3][n] float32 means                               */
+    const void *attr_host;           /* [56][n] in dtype, rows as in refine_scene          */
+    const refine_camera *cams_host;  /* [n_views]                                          */
+    double ratio;                    /* pruning ratio in [0, 1)                            */
+    const refine_params *params;     /* NULL = the queue's parameters; copied at submit    */
+    uint32_t *keep_mask_host;        /* [ceil(n/32)] or NULL                               */
+    float *scores_host;              /* [n] or NULL                                        */
+    float *out_pos_host;             /* [3][n_keep] compacted means, or NULL (no compaction) */
+    void *out_attr_host;             /* [56][n_keep] in dtype; needed with out_pos_host    */
+    int32_t *kept_idx_host;          /* [n_keep] original indices, or NULL                 */
+} refine_request;
+
+/* Result of one request.  Times are host steady-clock instants in ms since
+ * the queue was created: submission, admission (device block granted) and
+ * completion (every output in host memory). */
+typedef struct refine_result {
+    refine_status status;  /* of this request: OK, ENONFINITE, EINVAL (bad camera), ECUDA, ECANCELLED */
+    int32_t round_size;    /* requests scored by the same launch                                   */
+    int64_t n_keep;        /* n - floor(ratio n)                                                    */
+    float threshold;       /* as refine_select                                                      */
+    float reserved;
+    double submit_ms, admit_ms, done_ms;
+} refine_result;
+
+typedef struct refine_queue_stats {
+    int64_t submitted, admitted, completed, rounds;
+    int64_t pending, in_flight;
+    uint64_t bytes_in_use, peak_bytes, budget_bytes;
+    int32_t max_round, slots;
+    int64_t kernel_launches;
+} refine_queue_stats;
+
+/* Device bytes one request holds while admitted (scene, cameras, scratch,
+ * scores, mask and, with compact != 0, the compacted rows). */
+uint64_t refine_queue_footprint(int64_t n, int32_t dtype, int32_t n_views, double ratio, int32_t compact);
+
+/* Creates a queue on ctx's device (ctx itself is not used by the queue's
+ * threads and may keep serving other calls).  hbm_budget_bytes bounds the
+ * sum of the footprints of admitted requests; max_slots (1 .. 64) bounds
+ * their number.  params NULL = refine_params_default().  EINVAL on bad
+ * arguments, ENOMEM/ECUDA if streams, pools or threads cannot be made. */
+refine_status refine_queue_create(refine_ctx *ctx, uint64_t hbm_budget_bytes, int32_t max_slots,
+                                  const refine_params *params, refine_queue **out);
+
+/* Enqueues a request (the struct and *params are copied) and returns its
+ * ticket.  EINVAL for a malformed request, ENOMEM if its footprint alone
+ * exceeds the budget, ECANCELLED after refine_queue_destroy began.  Never
+ * blocks on the GPU. */
+refine_status refine_queue_submit(refine_queue *q, const refine_request *req, uint64_t *ticket);
+
+/* Waits up to timeout_ms (0 = do not wait, < 0 = no limit) for the request
+ * with this ticket and, when it is done, fills *out and retires the ticket.
+ * Returns OK (see out->status for the request's own outcome), ETIMEOUT if it
+ * is not done yet, ENOTFOUND for an unknown or already retired ticket. */
+refine_status refine_queue_poll(refine_queue *q, uint64_t ticket, refine_result *out, int32_t timeout_ms);
+
+refine_status refine_queue_stats_get(refine_queue *q, refine_queue_stats *out);
+
+/* Text of the last failure the queue's threads met while issuing GPU work
+ * ("" if none).  The string is owned by the queue and valid until the next
+ * call on it. */
+const char *refine_queue_last_error(refine_queue *q);
+
+/* Stops admitting, cancels pending requests, waits for the admitted ones,
+ * joins the threads and frees everything.  NULL is a no-op. */
+void refine_queue_destroy(refine_queue *q);
 
 /* Ratio pruning without any allocation.  The paper has no counterpart; this
  * entry point exists for callers that cannot allocate device memory -- code

@@ -86,8 +86,29 @@ class refine_job(C.Structure):
                 ("out_row_stride", C.c_int64), ("kept_idx_dev", C.c_void_p)]
 
 
+class refine_request(C.Structure):
+    _fields_ = [("n", C.c_int64), ("dtype", C.c_int32), ("n_views", C.c_int32), ("pos_host", C.c_void_p),
+                ("attr_host", C.c_void_p), ("cams_host", C.c_void_p), ("ratio", C.c_double),
+                ("params", C.c_void_p), ("keep_mask_host", C.c_void_p), ("scores_host", C.c_void_p),
+                ("out_pos_host", C.c_void_p), ("out_attr_host", C.c_void_p), ("kept_idx_host", C.c_void_p)]
+
+
+class refine_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("round_size", C.c_int32), ("n_keep", C.c_int64),
+                ("threshold", C.c_float), ("reserved", C.c_float), ("submit_ms", C.c_double),
+                ("admit_ms", C.c_double), ("done_ms", C.c_double)]
+
+
+class refine_queue_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("rounds", C.c_int64), ("pending", C.c_int64), ("in_flight", C.c_int64),
+                ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64), ("budget_bytes", C.c_uint64),
+                ("max_round", C.c_int32), ("slots", C.c_int32), ("kernel_launches", C.c_int64)]
+
+
 assert C.sizeof(refine_camera) == 80 and C.sizeof(refine_scene) == 40 and C.sizeof(refine_job) == 112
 assert C.sizeof(refine_params) == 48
+assert C.sizeof(refine_request) == 96 and C.sizeof(refine_result) == 48 and C.sizeof(refine_queue_stats) == 88
 
 _P = C.c_void_p
 _SIGNATURES = {
@@ -115,6 +136,14 @@ _SIGNATURES = {
     "refine_batch_results": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_float), _P]),
     "refine_batch_launches": (C.c_int64, [_P]),
     "refine_batch_destroy": (None, [_P]),
+    "refine_queue_footprint": (C.c_uint64, [C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_int32]),
+    "refine_queue_create": (C.c_int, [_P, C.c_uint64, C.c_int32, C.POINTER(refine_params),
+                                      C.POINTER(C.c_void_p)]),
+    "refine_queue_submit": (C.c_int, [_P, C.POINTER(refine_request), C.POINTER(C.c_uint64)]),
+    "refine_queue_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(refine_result), C.c_int32]),
+    "refine_queue_stats_get": (C.c_int, [_P, C.POINTER(refine_queue_stats)]),
+    "refine_queue_destroy": (None, [_P]),
+    "refine_queue_last_error": (C.c_char_p, [_P]),
     "refine_ctx_check": (C.c_int, [_P, _P]),
     "refine_ctx_set_timing": (C.c_int, [_P, C.c_int]),
     "refine_ctx_kernel_times": (C.c_int, [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -397,6 +426,132 @@ class Batch:
         if self.handle:
             refine_batch_destroy(self.handle)  # noqa: F821
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptr(a) -> int:
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return a.ctypes.data
+    if a.is_cuda or not a.is_contiguous():
+        raise ValueError("host tensors must be contiguous CPU tensors")
+    return a.data_ptr()
+
+
+def _host_dtype_code(a) -> int:
+    if isinstance(a, np.ndarray):
+        if a.dtype == np.float32:
+            return REFINE_F32
+        if a.dtype in (np.uint16, np.int16):
+            return REFINE_BF16
+    else:
+        import torch
+        if a.dtype == torch.float32:
+            return REFINE_F32
+        if a.dtype in (torch.bfloat16, torch.int16, torch.uint16):
+            return REFINE_BF16
+    raise TypeError(f"unsupported attribute dtype {a.dtype}")
+
+
+class Queue:
+    """Request queue (refine_queue_*): pruning requests for host-resident
+    scenes, admitted by HBM footprint and scored in rounds by the batched
+    kernel while earlier rounds run.  ``submit`` takes host arrays (numpy or
+    CPU tensors; page-locked tensors are copied asynchronously) and returns a
+    ticket; the queue keeps the arrays alive until ``poll`` returns them."""
+
+    def __init__(self, ctx: Context, budget_bytes: int, max_slots: int = 8, params=None):
+        self.ctx = ctx
+        h = C.c_void_p()
+        rc = refine_queue_create(ctx.handle, int(budget_bytes), int(max_slots),  # noqa: F821
+                                 C.byref(params) if params is not None else None, C.byref(h))
+        _check(ctx.handle, rc)
+        self.handle = h
+        self._live = {}
+
+    @staticmethod
+    def footprint(n, dtype, n_views, ratio, compact=True) -> int:
+        return int(refine_queue_footprint(int(n), int(dtype), int(n_views), float(ratio), int(bool(compact))))  # noqa: F821
+
+    def submit(self, pos, attr, cams, ratio, params=None, outputs=None, mask=True, scores=False,
+               compact=True, pin=False) -> int:
+        """Submits one request.  ``outputs`` may hold preallocated host
+        buffers (keys mask, scores, out_pos, out_attr, idx); missing ones are
+        allocated (page-locked when ``pin``)."""
+        import torch
+        n = int(pos.shape[1])
+        dt = _host_dtype_code(attr)
+        cams = np.ascontiguousarray(cams, dtype=CAMERA_DTYPE)
+        n_keep = n - int(np.floor(float(ratio) * n))
+        out = dict(outputs or {})
+
+        def alloc(key, shape, np_dtype, t_dtype):
+            if key not in out:
+                out[key] = (torch.empty(shape, dtype=t_dtype, pin_memory=True) if pin
+                            else np.empty(shape, dtype=np_dtype))
+        if mask:
+            alloc("mask", ((n + 31) // 32,), np.uint32, torch.int32)
+        if scores:
+            alloc("scores", (n,), np.float32, torch.float32)
+        if compact:
+            alloc("out_pos", (3, n_keep), np.float32, torch.float32)
+            alloc("out_attr", (56, n_keep), np.float32 if dt == REFINE_F32 else np.uint16,
+                  torch.float32 if dt == REFINE_F32 else torch.bfloat16)
+            alloc("idx", (n_keep,), np.int32, torch.int32)
+        r = refine_request()
+        r.n = n
+        r.dtype = dt
+        r.n_views = len(cams)
+        r.pos_host = _host_ptr(pos)
+        r.attr_host = _host_ptr(attr)
+        r.cams_host = cams.ctypes.data
+        r.ratio = float(ratio)
+        r.params = C.cast(C.pointer(params), C.c_void_p) if params is not None else None
+        r.keep_mask_host = _host_ptr(out.get("mask"))
+        r.scores_host = _host_ptr(out.get("scores"))
+        r.out_pos_host = _host_ptr(out.get("out_pos"))
+        r.out_attr_host = _host_ptr(out.get("out_attr"))
+        r.kept_idx_host = _host_ptr(out.get("idx"))
+        t = C.c_uint64()
+        rc = refine_queue_submit(self.handle, C.byref(r), C.byref(t))  # noqa: F821
+        if rc != REFINE_OK:
+            raise RefineError(rc, f"refine_queue_submit: {STATUS_NAMES.get(rc, rc)}")
+        self._live[t.value] = (pos, attr, cams, out)
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """Returns (result dict, outputs dict) or None if not done in time."""
+        res = refine_result()
+        rc = refine_queue_poll(self.handle, int(ticket), C.byref(res), int(timeout_ms))  # noqa: F821
+        if rc == REFINE_ETIMEOUT:
+            return None
+        if rc != REFINE_OK:
+            raise RefineError(rc, f"refine_queue_poll: {STATUS_NAMES.get(rc, rc)}")
+        _, _, _, out = self._live.pop(int(ticket))
+        d = {k: getattr(res, k) for k, _ in refine_result._fields_ if k != "reserved"}
+        return d, out
+
+    def last_error(self) -> str:
+        return refine_queue_last_error(self.handle).decode(errors="replace")  # noqa: F821
+
+    def stats(self) -> dict:
+        st = refine_queue_stats()
+        refine_queue_stats_get(self.handle, C.byref(st))  # noqa: F821
+        return {k: getattr(st, k) for k, _ in refine_queue_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            refine_queue_destroy(self.handle)  # noqa: F821
+            self.handle = None
+            self._live.clear()
 
     def __del__(self):
         try:

@@ -97,7 +97,7 @@ cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s);
 int score_grid(int num_sms, int64_t n, int vcount);
 
 // Batched score launch over the tiles of many scenes (each scene a single
-// pass of at most kViewsPerPass views, one storage type per batch).
+// pass of at most kViewsPerPass views).
 struct BatchLaunch {
     const ScoreLaunch *scenes;       // device [n_scenes]
     const long long *tile_begin;     // device [n_scenes + 1], first tile of each scene
@@ -106,9 +106,8 @@ struct BatchLaunch {
     unsigned long long *counter;     // device, zero before the launch
     int *status;
 };
-int score_batch_grid(int num_sms, int dtype, bool noproj, int max_vcount);
-cudaError_t launch_score_batch(const BatchLaunch &b, int dtype, bool noproj, int max_vcount, int grid,
-                               cudaStream_t s);
+int score_batch_grid(int num_sms, int max_vcount);
+cudaError_t launch_score_batch(const BatchLaunch &b, int max_vcount, int grid, cudaStream_t s);
 
 // ------------------------------------------------------------- select
 struct SelState {

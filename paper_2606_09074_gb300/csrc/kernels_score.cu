@@ -712,6 +712,16 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
     }
 }
 
+// A camera block may be staged by one bulk copy chain only if its source is
+// 16-byte aligned and it fits the launch's dynamic shared memory.
+__device__ __forceinline__ int cams_stageable(const CamRec *cams, int vcount)
+{
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    return vcount >= 1 && (reinterpret_cast<uintptr_t>(cams) & 15u) == 0 &&
+           (uint64_t)vcount * sizeof(CamRec) <= (uint64_t)dyn;
+}
+
 template <bool NOPROJ, bool COUNT>
 __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 {
@@ -720,16 +730,23 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
     CamRec *cs = reinterpret_cast<CamRec *>(smem_raw);
 
     // Stage this pass's cameras once per CTA (TMA bulk copy, mbarrier).
+    __shared__ int s_ok;
     const uint32_t bytes = (uint32_t)a.vcount * (uint32_t)sizeof(CamRec);
     if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        mbar_expect_tx(&bar, bytes);
-        for (uint32_t off = 0; off < bytes; off += 16384u) {
-            const uint32_t len = bytes - off < 16384u ? bytes - off : 16384u;
-            bulk_g2s(smem_raw + off, reinterpret_cast<const unsigned char *>(a.cams) + off, len, &bar);
+        s_ok = cams_stageable(a.cams, a.vcount);
+        if (s_ok) {
+            mbar_init(&bar, 1);
+            mbar_expect_tx(&bar, bytes);
+            for (uint32_t off = 0; off < bytes; off += 16384u) {
+                const uint32_t len = bytes - off < 16384u ? bytes - off : 16384u;
+                bulk_g2s(smem_raw + off, reinterpret_cast<const unsigned char *>(a.cams) + off, len, &bar);
+            }
+        } else {
+            set_status(a.status, kEinval);
         }
     }
     __syncthreads();
+    if (!s_ok) return;
     if (!mbar_wait_bounded(&bar, 0)) {
         set_status(a.status, kEtimeout);
         mbar_wait_bounded(&bar, 0);  // give the copy a second bound before leaving
@@ -759,13 +776,13 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 // CTAs take (scene, tile) items from an atomic counter (items are ordered
 // by scene); when a CTA moves to another scene it restages that scene's
 // cameras by TMA.  Every tile is scored by score_tile exactly as in
-// k_score, so a scene's scores are the same alone and in a batch.
-template <bool NOPROJ>
+// k_score, so a scene's scores are the same alone and in a batch; scenes
+// may differ in storage type (the records are float32) and in flags.
 __global__ void __launch_bounds__(kScoreThreads, 3) k_score_batch(BatchLaunch b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_scene;
+    __shared__ int s_scene, s_ok;
     __shared__ long long s_base;
     CamRec *cs = reinterpret_cast<CamRec *>(smem_raw);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -798,13 +815,23 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_batch(BatchLaunch b)
         const ScoreLaunch &a = b.scenes[sidx];
         if (sidx != cur) {
             if (threadIdx.x == 0) {
-                fence_proxy_async_shared();
-                const uint32_t bytes = (uint32_t)a.vcount * (uint32_t)sizeof(CamRec);
-                mbar_expect_tx(&bar, bytes);
-                for (uint32_t off = 0; off < bytes; off += 16384u) {
-                    const uint32_t len = bytes - off < 16384u ? bytes - off : 16384u;
-                    bulk_g2s(smem_raw + off, reinterpret_cast<const unsigned char *>(a.cams) + off, len, &bar);
+                s_ok = cams_stageable(a.cams, a.vcount);
+                if (s_ok) {
+                    fence_proxy_async_shared();
+                    const uint32_t bytes = (uint32_t)a.vcount * (uint32_t)sizeof(CamRec);
+                    mbar_expect_tx(&bar, bytes);
+                    for (uint32_t off = 0; off < bytes; off += 16384u) {
+                        const uint32_t len = bytes - off < 16384u ? bytes - off : 16384u;
+                        bulk_g2s(smem_raw + off, reinterpret_cast<const unsigned char *>(a.cams) + off, len, &bar);
+                    }
+                } else {
+                    set_status(a.status, kEinval);
                 }
+            }
+            __syncthreads();
+            if (!s_ok) {
+                cur = -1;
+                continue;  // the tile is left unscored; the loop's first barrier orders s_scene
             }
             if (!mbar_wait_bounded(&bar, phase)) {
                 set_status(b.status, kEtimeout);
@@ -815,7 +842,10 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_batch(BatchLaunch b)
             cur = sidx;
         }
         const SceneConsts sc = *a.consts;
-        score_tile<NOPROJ, false>(a, cs, sc, base, -1, cnt);
+        if (a.flags & REFINE_FLAG_NO_PROJ)
+            score_tile<true, false>(a, cs, sc, base, -1, cnt);
+        else
+            score_tile<false, false>(a, cs, sc, base, -1, cnt);
         __syncthreads();  // the cameras and s_scene are free again
     }
 }
@@ -864,16 +894,9 @@ cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s)
     return cudaLaunchKernel(fn, dim3(a.grid), dim3(kScoreThreads), args, smem, s);
 }
 
-template <bool NOPROJ>
-static const void *batch_fn()
+int score_batch_grid(int num_sms, int max_vcount)
 {
-    return reinterpret_cast<const void *>(&k_score_batch<NOPROJ>);
-}
-
-int score_batch_grid(int num_sms, int dtype, bool noproj, int max_vcount)
-{
-    (void)dtype;
-    const void *fn = noproj ? batch_fn<true>() : batch_fn<false>();
+    const void *fn = reinterpret_cast<const void *>(&k_score_batch);
     const size_t smem = (size_t)max_vcount * sizeof(CamRec);
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -884,18 +907,16 @@ int score_batch_grid(int num_sms, int dtype, bool noproj, int max_vcount)
     return num_sms * per_sm;
 }
 
-cudaError_t launch_score_batch(const BatchLaunch &b, int dtype, bool noproj, int max_vcount, int grid, cudaStream_t s)
+cudaError_t launch_score_batch(const BatchLaunch &b, int max_vcount, int grid, cudaStream_t s)
 {
-    (void)dtype;
-    const void *fn = noproj ? batch_fn<true>() : batch_fn<false>();
     const size_t smem = (size_t)max_vcount * sizeof(CamRec);
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_score_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    BatchLaunch arg = b;
-    void *args[] = {&arg};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kScoreThreads), args, smem, s);
+    k_score_batch<<<grid, kScoreThreads, smem, s>>>(b);
+    return cudaGetLastError();
 }
 
 }  // namespace refine

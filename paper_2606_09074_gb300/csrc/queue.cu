@@ -1,0 +1,680 @@
+// Request queue (refine_queue_*): a serving loop that admits pruning
+// requests by HBM footprint and scores the requests admitted together with
+// one batched launch, while earlier rounds are still on the GPU.
+//
+// Threads and streams:
+//   dispatcher   admits (FIFO, budget, slots) and issues a round: per request
+//                on its slot stream a pool allocation, the host->device copies
+//                and the preparation; on the score stream the round's work
+//                list and ONE k_score_batch launch; per request on its slot
+//                stream again the selection, the compaction, the copies back
+//                (asynchronous when the host buffers are page-locked) and a
+//                completion event.
+//   completion   polls the completion events of the requests in flight,
+//                finishes copies into pageable buffers, reads the request's
+//                status and threshold, frees its block and its slot.
+// Device status words are per request (and per round for the batched
+// launch), so an error is reported on the request that caused it.
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+
+#include "api_internal.h"
+
+using namespace refine;
+using namespace refine_api;
+
+namespace {
+
+constexpr int kQueueMaxSlots = 64;
+
+// Rows of the device copy start on 16-byte boundaries.
+inline int64_t dev_stride(int64_t n) { return (n + 7) & ~int64_t(7); }
+
+inline int64_t keep_count(int64_t n, double ratio) { return n - (int64_t)floor(ratio * (double)n); }
+
+struct SlotHost {  // page-locked read-back of one slot
+    unsigned int kstar;
+    int status;
+    int round_status;
+    int pad;
+};
+
+struct QJob {
+    uint64_t ticket = 0;
+    refine_request req{};
+    refine_params params{};
+    int64_t n_keep = 0;
+    uint64_t footprint = 0;
+    bool compact = false, pinned_out = false;
+    double t_submit = 0, t_admit = 0;
+    int slot = -1;
+    int round_size = 0;
+    void *block = nullptr;
+    refine_scene scene{};
+    refine_camera *cams = nullptr;
+    float *scores = nullptr;
+    uint32_t *mask = nullptr;
+    float *out_pos = nullptr;
+    void *out_attr = nullptr;
+    int32_t *idx = nullptr;
+    int *status = nullptr;
+    ScenePlan plan;
+    SceneScratch sx{};
+    void *sel_scr = nullptr, *cmp_scr = nullptr;
+    unsigned int *kstar = nullptr;
+    long long *total = nullptr;
+    refine_status host_status = REFINE_OK;
+    bool issued = false;  // GPU work enqueued (its completion event is recorded)
+};
+
+struct RoundRes {  // one entry of the round ring
+    ScoreLaunch *h_launch = nullptr;  // page-locked [slots]
+    long long *h_tb = nullptr;        // page-locked [slots + 1]
+    ScoreLaunch *d_launch = nullptr;
+    long long *d_tb = nullptr;
+    unsigned long long *d_counter = nullptr;
+    int *d_status = nullptr;
+    cudaEvent_t scored = nullptr;
+};
+
+double now_ms(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+bool is_pinned(const void *p)
+{
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+size_t elem_size(int dtype) { return dtype == REFINE_BF16 ? 2 : 4; }
+
+}  // namespace
+
+struct refine_queue {
+    refine_ctx pc;  // private context of the dispatcher (error text, device, SM count)
+    refine_params params{};
+    uint64_t budget = 0;
+    int slots = 0;
+    std::chrono::steady_clock::time_point t0;
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t score_stream = nullptr;
+    std::vector<cudaStream_t> slot_stream;
+    std::vector<cudaEvent_t> prepped, done;
+    SlotHost *slot_host = nullptr;  // page-locked [slots]
+    std::vector<RoundRes> ring;
+    void *ring_dev = nullptr;
+    void *ring_host = nullptr;
+    int64_t round_seq = 0;
+
+    std::mutex mu;
+    std::condition_variable cv_dispatch, cv_complete, cv_poll;
+    std::deque<QJob *> pending;
+    std::list<QJob *> inflight;
+    std::unordered_map<uint64_t, refine_result> results;
+    std::unordered_set<uint64_t> live;  // submitted, not yet returned by refine_queue_poll
+    std::vector<int> free_slots;
+    uint64_t used = 0, peak = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false, dispatcher_done = false;
+    int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_rounds = 0;
+    int max_round = 0;
+    std::atomic<int64_t> launches{0};
+    char err_copy[1024] = {0};
+    char cerr[256] = {0};  // last failure seen by the completion thread
+    std::thread dispatcher, completer;
+};
+
+namespace {
+
+uint64_t footprint_of(int64_t n, int dtype, int V, double ratio, bool compact)
+{
+    const size_t S = (size_t)dev_stride(n), es = elem_size(dtype);
+    const int64_t nk = keep_count(n, ratio);
+    const ScenePlan pl = plan_scene(n, V);
+    const size_t parts = carve_size({3 * S * 4, 56 * S * es, sizeof(refine_camera) * (size_t)V, 4 * (size_t)n,
+                                     4 * (size_t)((n + 31) / 32), compact ? 3 * (size_t)nk * 4 : 0,
+                                     compact ? 56 * (size_t)nk * es : 0, compact ? 4 * (size_t)nk : 0, 256});
+    return parts + scene_bytes(pl) + select_bytes(n) + compact_bytes(n) + 3 * 256;
+}
+
+// Carves the request's block (the order of footprint_of).
+void carve_job(QJob *j)
+{
+    const int64_t n = j->req.n, S = dev_stride(n), nk = j->n_keep;
+    const size_t es = elem_size(j->req.dtype);
+    Carver cv(j->block);
+    float *pos = cv.take<float>(3 * (size_t)S);
+    char *attr = cv.take<char>(56 * (size_t)S * es);
+    j->cams = cv.take<refine_camera>(j->req.n_views);
+    j->scores = cv.take<float>(n);
+    j->mask = cv.take<uint32_t>((n + 31) / 32);
+    if (j->compact) {
+        j->out_pos = cv.take<float>(3 * (size_t)nk);
+        j->out_attr = cv.take<char>(56 * (size_t)nk * es);
+        j->idx = cv.take<int32_t>(nk);
+    } else {
+        cv.take<char>(0);
+        cv.take<char>(0);
+        cv.take<char>(0);
+    }
+    j->status = cv.take<int>(64);
+    j->scene.n = n;
+    j->scene.dtype = j->req.dtype;
+    j->scene.reserved = 0;
+    j->scene.pos = pos;
+    j->scene.attr = attr;
+    j->scene.row_stride = S;
+    j->sx = carve_scene(cv, j->plan);
+    j->sel_scr = cv.take<char>(select_bytes(n));
+    j->cmp_scr = cv.take<char>(compact_bytes(n));
+}
+
+template <typename F>
+refine_status counted_run(refine_queue *q, int cls, F &&f)
+{
+    const cudaError_t e = f();
+    if (e != cudaSuccess) return cuda_fail(&q->pc, e, kClassName[cls]);
+    q->launches.fetch_add(1, std::memory_order_relaxed);
+    return REFINE_OK;
+}
+
+// Issues the preparation of one admitted request on its slot stream.
+refine_status issue_prep(refine_queue *q, QJob *j)
+{
+    cudaStream_t s = q->slot_stream[j->slot];
+    refine_ctx *c = &q->pc;
+    cudaError_t e = cudaMallocFromPoolAsync(&j->block, j->footprint, q->pool, s);
+    if (e != cudaSuccess) {
+        j->block = nullptr;
+        return cuda_fail(c, e, "queue: device block");
+    }
+    carve_job(j);
+    const int64_t n = j->req.n, S = dev_stride(n);
+    const size_t es = elem_size(j->req.dtype);
+    e = cudaMemsetAsync(j->status, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(const_cast<float *>(j->scene.pos), (size_t)S * 4, j->req.pos_host, (size_t)n * 4,
+                              (size_t)n * 4, 3, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(const_cast<void *>(j->scene.attr), (size_t)S * es, j->req.attr_host, (size_t)n * es,
+                              (size_t)n * es, 56, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(j->cams, j->req.cams_host, sizeof(refine_camera) * j->req.n_views,
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "queue: input copy");
+    auto run = [q](int cls, auto &&f) { return counted_run(q, cls, f); };
+    refine_status st = enqueue_prep(c, run, &j->scene, j->cams, j->plan, j->sx, j->params, false, j->status, s);
+    if (st) return st;
+    e = cudaEventRecord(q->prepped[j->slot], s);
+    return e == cudaSuccess ? REFINE_OK : cuda_fail(c, e, "queue: event");
+}
+
+// Selection, compaction and read-back of one scored request.
+refine_status issue_finish(refine_queue *q, QJob *j, const RoundRes &R)
+{
+    cudaStream_t s = q->slot_stream[j->slot];
+    refine_ctx *c = &q->pc;
+    cudaError_t e = cudaStreamWaitEvent(s, R.scored, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "queue: wait");
+    auto run = [q](int cls, auto &&f) { return counted_run(q, cls, f); };
+    const int64_t n = j->req.n, nk = j->n_keep;
+    refine_status st = enqueue_select(c, run, j->scores, n, nk, j->mask, j->sel_scr, &j->kstar, j->status, s);
+    if (!st && j->compact)
+        st = enqueue_compact(c, run, &j->scene, j->mask, j->out_pos, j->out_attr, nk, j->idx, j->cmp_scr, &j->total,
+                             j->status, s);
+    if (st) return st;
+    SlotHost *h = &q->slot_host[j->slot];
+    h->kstar = 0u;
+    if (j->kstar) e = cudaMemcpyAsync(&h->kstar, j->kstar, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h->status, j->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h->round_status, R.d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && j->pinned_out) {
+        const size_t es = elem_size(j->req.dtype);
+        if (j->req.keep_mask_host)
+            e = cudaMemcpyAsync(j->req.keep_mask_host, j->mask, 4 * (size_t)((n + 31) / 32), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && j->req.scores_host)
+            e = cudaMemcpyAsync(j->req.scores_host, j->scores, 4 * (size_t)n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && j->compact) {
+            e = cudaMemcpyAsync(j->req.out_pos_host, j->out_pos, 12 * (size_t)nk, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(j->req.out_attr_host, j->out_attr, 56 * es * (size_t)nk, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && j->req.kept_idx_host)
+                e = cudaMemcpyAsync(j->req.kept_idx_host, j->idx, 4 * (size_t)nk, cudaMemcpyDeviceToHost, s);
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "queue: read-back");
+    return REFINE_OK;
+}
+
+void issue_round(refine_queue *q, std::vector<QJob *> &round)
+{
+    RoundRes &R = q->ring[(size_t)(q->round_seq++ % q->slots)];
+    std::vector<QJob *> live;
+    for (QJob *j : round) {
+        j->round_size = (int)round.size();
+        j->host_status = issue_prep(q, j);
+        if (!j->host_status) live.push_back(j);
+    }
+    const long long tile = (long long)kScoreThreads * kScoreGPT;
+    refine_status st = REFINE_OK;
+    if (!live.empty()) {
+        int max_v = 0;
+        R.h_tb[0] = 0;
+        for (size_t i = 0; i < live.size(); ++i) {
+            QJob *j = live[i];
+            R.h_launch[i] = make_score_launch(&j->scene, j->plan, j->sx, j->params, 0, j->scores, nullptr, false,
+                                              j->status);
+            R.h_tb[i + 1] = R.h_tb[i] + (j->req.n + tile - 1) / tile;
+            max_v = std::max(max_v, j->req.n_views);
+        }
+        const int k = (int)live.size();
+        cudaStream_t m = q->score_stream;
+        cudaError_t e = cudaMemcpyAsync(R.d_launch, R.h_launch, sizeof(ScoreLaunch) * k, cudaMemcpyHostToDevice, m);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(R.d_tb, R.h_tb, sizeof(long long) * (k + 1), cudaMemcpyHostToDevice, m);
+        if (e == cudaSuccess) e = cudaMemsetAsync(R.d_counter, 0, sizeof(unsigned long long), m);
+        if (e == cudaSuccess) e = cudaMemsetAsync(R.d_status, 0, sizeof(int), m);
+        for (QJob *j : live)
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(m, q->prepped[j->slot], 0);
+        if (e == cudaSuccess) {
+            BatchLaunch bl;
+            bl.scenes = R.d_launch;
+            bl.tile_begin = R.d_tb;
+            bl.n_scenes = k;
+            bl.total_tiles = R.h_tb[k];
+            bl.counter = R.d_counter;
+            bl.status = R.d_status;
+            int grid = score_batch_grid(q->pc.num_sms, max_v);
+            if (grid > bl.total_tiles) grid = (int)bl.total_tiles;
+            e = launch_score_batch(bl, max_v, grid, m);
+            if (e == cudaSuccess) q->launches.fetch_add(1, std::memory_order_relaxed);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(R.scored, m);
+        if (e != cudaSuccess) st = cuda_fail(&q->pc, e, "queue: batched score");
+    }
+    for (QJob *j : round) {
+        if (!j->host_status) j->host_status = st ? st : issue_finish(q, j, R);
+        // the completion event closes the slot stream's work in every case
+        if (cudaEventRecord(q->done[j->slot], q->slot_stream[j->slot]) == cudaSuccess) j->issued = true;
+        else cudaGetLastError();
+    }
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        for (QJob *j : round) q->inflight.push_back(j);
+        q->n_rounds++;
+        q->max_round = std::max(q->max_round, (int)round.size());
+    }
+    q->cv_complete.notify_one();
+}
+
+bool admissible(const refine_queue *q, const QJob *j)
+{
+    return !q->free_slots.empty() && q->used + j->footprint <= q->budget;
+}
+
+void dispatcher_main(refine_queue *q)
+{
+    cudaSetDevice(q->pc.device);
+    for (;;) {
+        std::vector<QJob *> round;
+        {
+            std::unique_lock<std::mutex> lk(q->mu);
+            q->cv_dispatch.wait(lk, [q] { return q->stop || (!q->pending.empty() && admissible(q, q->pending.front())); });
+            if (q->stop) break;
+            const double t = now_ms(q->t0);
+            while (!q->pending.empty() && admissible(q, q->pending.front())) {
+                QJob *j = q->pending.front();
+                q->pending.pop_front();
+                j->slot = q->free_slots.back();
+                q->free_slots.pop_back();
+                j->t_admit = t;
+                q->used += j->footprint;
+                q->n_admitted++;
+                round.push_back(j);
+            }
+            q->peak = std::max(q->peak, q->used);
+        }
+        issue_round(q, round);
+    }
+    std::lock_guard<std::mutex> lk(q->mu);
+    q->dispatcher_done = true;
+    q->cv_complete.notify_one();
+}
+
+// Copies into pageable host buffers (synchronous), then frees the block.
+refine_status finish_pageable(refine_queue *q, QJob *j)
+{
+    cudaStream_t s = q->slot_stream[j->slot];
+    const int64_t n = j->req.n, nk = j->n_keep;
+    const size_t es = elem_size(j->req.dtype);
+    cudaError_t e = cudaSuccess;
+    if (j->req.keep_mask_host)
+        e = cudaMemcpyAsync(j->req.keep_mask_host, j->mask, 4 * (size_t)((n + 31) / 32), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && j->req.scores_host)
+        e = cudaMemcpyAsync(j->req.scores_host, j->scores, 4 * (size_t)n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && j->compact) {
+        e = cudaMemcpyAsync(j->req.out_pos_host, j->out_pos, 12 * (size_t)nk, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(j->req.out_attr_host, j->out_attr, 56 * es * (size_t)nk, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && j->req.kept_idx_host)
+            e = cudaMemcpyAsync(j->req.kept_idx_host, j->idx, 4 * (size_t)nk, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(q->mu);
+        snprintf(q->cerr, sizeof q->cerr, "queue: request %llu: copy back: %s", (unsigned long long)j->ticket,
+                 cudaGetErrorString(e));
+        return REFINE_ECUDA;
+    }
+    return REFINE_OK;
+}
+
+void retire(refine_queue *q, QJob *j)
+{
+    refine_status st = j->host_status;
+    const SlotHost &h = q->slot_host[j->slot];
+    if (!st && j->issued) {
+        if (h.status) st = (refine_status)h.status;
+        else if (h.round_status) st = (refine_status)h.round_status;
+        if (!st && !j->pinned_out) st = finish_pageable(q, j);
+    }
+    refine_result r{};
+    r.status = st;
+    r.round_size = j->round_size;
+    r.n_keep = j->n_keep;
+    r.threshold = (!st && j->kstar) ? key_to_score(h.kstar) : -INFINITY;
+    r.submit_ms = j->t_submit;
+    r.admit_ms = j->t_admit;
+    if (j->block) {
+        cudaFreeAsync(j->block, q->slot_stream[j->slot]);
+        cudaGetLastError();
+    }
+    r.done_ms = now_ms(q->t0);
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        q->used -= j->footprint;
+        q->free_slots.push_back(j->slot);
+        q->n_completed++;
+        q->results[j->ticket] = r;
+    }
+    delete j;
+    q->cv_dispatch.notify_one();
+    q->cv_poll.notify_all();
+}
+
+void completer_main(refine_queue *q)
+{
+    cudaSetDevice(q->pc.device);
+    for (;;) {
+        std::vector<QJob *> ready;
+        {
+            std::unique_lock<std::mutex> lk(q->mu);
+            q->cv_complete.wait(lk, [q] { return !q->inflight.empty() || q->dispatcher_done; });
+            if (q->inflight.empty() && q->dispatcher_done) break;
+            for (auto it = q->inflight.begin(); it != q->inflight.end();) {
+                QJob *j = *it;
+                bool fin = !j->issued;
+                if (!fin) {
+                    const cudaError_t e = cudaEventQuery(q->done[j->slot]);
+                    fin = e != cudaErrorNotReady;
+                    if (e != cudaSuccess && e != cudaErrorNotReady) {
+                        cudaGetLastError();
+                        snprintf(q->cerr, sizeof q->cerr, "queue: request %llu: %s", (unsigned long long)j->ticket,
+                                 cudaGetErrorString(e));
+                        if (!j->host_status) j->host_status = REFINE_ECUDA;
+                    }
+                }
+                if (fin) {
+                    ready.push_back(j);
+                    it = q->inflight.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        for (QJob *j : ready) retire(q, j);
+        if (ready.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+void queue_free(refine_queue *q)
+{
+    for (cudaStream_t s : q->slot_stream)
+        if (s) cudaStreamDestroy(s);
+    if (q->score_stream) cudaStreamDestroy(q->score_stream);
+    for (cudaEvent_t e : q->prepped)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : q->done)
+        if (e) cudaEventDestroy(e);
+    for (RoundRes &r : q->ring)
+        if (r.scored) cudaEventDestroy(r.scored);
+    if (q->ring_dev) cudaFree(q->ring_dev);
+    if (q->ring_host) cudaFreeHost(q->ring_host);
+    if (q->slot_host) cudaFreeHost(q->slot_host);
+    if (q->pool) cudaMemPoolDestroy(q->pool);
+    if (q->pc.d_status) cudaFree(q->pc.d_status);
+    delete q;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t refine_queue_footprint(int64_t n, int32_t dtype, int32_t n_views, double ratio, int32_t compact)
+{
+    if (n < 1 || n > INT32_MAX || (dtype != REFINE_F32 && dtype != REFINE_BF16) || n_views < 1 ||
+        n_views > kViewsPerPass || !(ratio >= 0.0 && ratio < 1.0))
+        return 0;
+    return footprint_of(n, dtype, n_views, ratio, compact != 0);
+}
+
+refine_status refine_queue_create(refine_ctx *c, uint64_t hbm_budget_bytes, int32_t max_slots,
+                                  const refine_params *params, refine_queue **out)
+{
+    if (!c || !out) return REFINE_EINVAL;
+    *out = nullptr;
+    refine_status st = use_device(c);
+    if (st) return st;
+    if (max_slots < 1 || max_slots > kQueueMaxSlots)
+        return fail(c, REFINE_EINVAL, "queue: max_slots must lie in [1, %d]", kQueueMaxSlots);
+    if (hbm_budget_bytes == 0) return fail(c, REFINE_EINVAL, "queue: zero HBM budget");
+    refine_params p;
+    if (params) p = *params; else refine_params_default(&p);
+    if ((st = check_params(c, &p))) return st;
+    refine_queue *q = new refine_queue();
+    q->pc.device = c->device;
+    q->pc.num_sms = c->num_sms;
+    q->params = p;
+    q->budget = hbm_budget_bytes;
+    q->slots = max_slots;
+    q->t0 = std::chrono::steady_clock::now();
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    cudaError_t e = cudaMemPoolCreate(&q->pool, &props);
+    if (e == cudaSuccess) {
+        uint64_t keep = hbm_budget_bytes;  // keep freed blocks cached up to the budget
+        e = cudaMemPoolSetAttribute(q->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->score_stream, cudaStreamNonBlocking);
+    q->slot_stream.assign(max_slots, nullptr);
+    q->prepped.assign(max_slots, nullptr);
+    q->done.assign(max_slots, nullptr);
+    for (int s = 0; s < max_slots && e == cudaSuccess; ++s) {
+        e = cudaStreamCreateWithFlags(&q->slot_stream[s], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->prepped[s], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->done[s], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMallocHost(&q->slot_host, sizeof(SlotHost) * max_slots);
+    const size_t per_dev = carve_size({sizeof(ScoreLaunch) * (size_t)max_slots, sizeof(long long) * (max_slots + 1),
+                                       sizeof(unsigned long long), sizeof(int)});
+    const size_t per_host = carve_size({sizeof(ScoreLaunch) * (size_t)max_slots, sizeof(long long) * (max_slots + 1)});
+    if (e == cudaSuccess) e = cudaMalloc(&q->ring_dev, per_dev * max_slots);
+    if (e == cudaSuccess) e = cudaMallocHost(&q->ring_host, per_host * max_slots);
+    q->ring.resize(max_slots);
+    for (int r = 0; r < max_slots && e == cudaSuccess; ++r) {
+        RoundRes &R = q->ring[r];
+        Carver dv(static_cast<char *>(q->ring_dev) + per_dev * r);
+        R.d_launch = dv.take<ScoreLaunch>(max_slots);
+        R.d_tb = dv.take<long long>(max_slots + 1);
+        R.d_counter = dv.take<unsigned long long>(1);
+        R.d_status = dv.take<int>(1);
+        Carver hv(static_cast<char *>(q->ring_host) + per_host * r);
+        R.h_launch = hv.take<ScoreLaunch>(max_slots);
+        R.h_tb = hv.take<long long>(max_slots + 1);
+        e = cudaEventCreateWithFlags(&R.scored, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        st = cuda_fail(c, e, "queue: set-up");
+        queue_free(q);
+        return st;
+    }
+    for (int s = max_slots - 1; s >= 0; --s) q->free_slots.push_back(s);
+    try {
+        q->dispatcher = std::thread(dispatcher_main, q);
+        q->completer = std::thread(completer_main, q);
+    } catch (...) {
+        if (q->dispatcher.joinable()) {
+            {
+                std::lock_guard<std::mutex> lk(q->mu);
+                q->stop = true;
+            }
+            q->cv_dispatch.notify_all();
+            q->dispatcher.join();
+        }
+        queue_free(q);
+        return fail(c, REFINE_ENOMEM, "queue: cannot start threads");
+    }
+    *out = q;
+    return REFINE_OK;
+}
+
+refine_status refine_queue_submit(refine_queue *q, const refine_request *req, uint64_t *ticket)
+{
+    if (!q || !req || !ticket) return REFINE_EINVAL;
+    const refine_request &r = *req;
+    if (r.n < 1 || r.n > INT32_MAX || (r.dtype != REFINE_F32 && r.dtype != REFINE_BF16) || r.n_views < 1 ||
+        r.n_views > kViewsPerPass || !(r.ratio >= 0.0 && r.ratio < 1.0) || !r.pos_host || !r.attr_host ||
+        !r.cams_host || (r.out_pos_host && !r.out_attr_host) || (!r.out_pos_host && (r.out_attr_host || r.kept_idx_host)))
+        return REFINE_EINVAL;
+    QJob *j = new QJob();
+    j->req = r;
+    j->params = r.params ? *r.params : q->params;
+    if (!(j->params.eta > 0.f) || !isfinite(j->params.eta) || j->params.e_ln_gem == 0.0 || j->params.e_col == 0.0 ||
+        j->params.e_opa == 0.0) {
+        delete j;
+        return REFINE_EINVAL;
+    }
+    j->req.params = nullptr;
+    j->n_keep = keep_count(r.n, r.ratio);
+    j->compact = r.out_pos_host != nullptr;
+    j->footprint = footprint_of(r.n, r.dtype, r.n_views, r.ratio, j->compact);
+    j->plan = plan_scene(r.n, r.n_views);
+    j->pinned_out = is_pinned(r.keep_mask_host) && is_pinned(r.scores_host) && is_pinned(r.out_pos_host) &&
+                    is_pinned(r.out_attr_host) && is_pinned(r.kept_idx_host);
+    if (j->footprint > q->budget) {
+        delete j;
+        return REFINE_ENOMEM;
+    }
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        if (q->stop) {
+            delete j;
+            return REFINE_ECANCELLED;
+        }
+        j->ticket = q->next_ticket++;
+        j->t_submit = now_ms(q->t0);
+        *ticket = j->ticket;
+        q->live.insert(j->ticket);
+        q->pending.push_back(j);
+        q->n_submitted++;
+    }
+    q->cv_dispatch.notify_one();
+    return REFINE_OK;
+}
+
+refine_status refine_queue_poll(refine_queue *q, uint64_t ticket, refine_result *out, int32_t timeout_ms)
+{
+    if (!q || !out) return REFINE_EINVAL;
+    std::unique_lock<std::mutex> lk(q->mu);
+    if (!q->live.count(ticket)) return REFINE_ENOTFOUND;
+    auto ready = [&] { return q->results.count(ticket) != 0; };
+    if (!ready()) {
+        if (timeout_ms == 0) return REFINE_ETIMEOUT;
+        if (timeout_ms < 0)
+            q->cv_poll.wait(lk, ready);
+        else if (!q->cv_poll.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+            return REFINE_ETIMEOUT;
+    }
+    auto it = q->results.find(ticket);
+    *out = it->second;
+    q->results.erase(it);
+    q->live.erase(ticket);
+    return REFINE_OK;
+}
+
+const char *refine_queue_last_error(refine_queue *q)
+{
+    if (!q) return "NULL queue";
+    std::lock_guard<std::mutex> lk(q->mu);
+    snprintf(q->err_copy, sizeof q->err_copy, "%s%s%s", q->pc.err, q->pc.err[0] && q->cerr[0] ? "; " : "", q->cerr);
+    return q->err_copy;
+}
+
+refine_status refine_queue_stats_get(refine_queue *q, refine_queue_stats *out)
+{
+    if (!q || !out) return REFINE_EINVAL;
+    std::lock_guard<std::mutex> lk(q->mu);
+    out->submitted = q->n_submitted;
+    out->admitted = q->n_admitted;
+    out->completed = q->n_completed;
+    out->rounds = q->n_rounds;
+    out->pending = (int64_t)q->pending.size();
+    out->in_flight = q->n_admitted - q->n_completed;
+    out->bytes_in_use = q->used;
+    out->peak_bytes = q->peak;
+    out->budget_bytes = q->budget;
+    out->max_round = q->max_round;
+    out->slots = q->slots;
+    out->kernel_launches = q->launches.load();
+    return REFINE_OK;
+}
+
+void refine_queue_destroy(refine_queue *q)
+{
+    if (!q) return;
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        q->stop = true;
+        for (QJob *j : q->pending) {
+            q->live.erase(j->ticket);
+            delete j;
+        }
+        q->pending.clear();
+    }
+    q->cv_dispatch.notify_all();
+    if (q->dispatcher.joinable()) q->dispatcher.join();
+    if (q->completer.joinable()) q->completer.join();
+    cudaSetDevice(q->pc.device);
+    for (cudaStream_t s : q->slot_stream)
+        if (s) cudaStreamSynchronize(s);
+    queue_free(q);
+}
+
+}  // extern "C"

@@ -47,6 +47,9 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(refine_camera), sizeof(refine_scene), sizeof(refine_params), sizeof(refine_scene_stats));
   printf("%zu %zu %zu %zu\\n", offsetof(refine_camera, width), offsetof(refine_camera, zfar), offsetof(refine_scene, pos), offsetof(refine_scene, row_stride));
   printf("%zu %zu %zu\\n", offsetof(refine_params, e_ln_gem), offsetof(refine_params, flags), offsetof(refine_scene_stats, mean_m));
+  printf("%zu %zu %zu\\n", sizeof(refine_request), sizeof(refine_result), sizeof(refine_queue_stats));
+  printf("%zu %zu %zu %zu\\n", offsetof(refine_request, ratio), offsetof(refine_request, kept_idx_host), offsetof(refine_result, threshold), offsetof(refine_result, done_ms));
+  printf("%zu %zu\\n", offsetof(refine_queue_stats, max_round), offsetof(refine_queue_stats, kernel_launches));
   return 0; }
 ''')
     exe = tmp_path / "layout"
@@ -59,6 +62,10 @@ int main(void) {
                       b.refine_scene.row_stride.offset]
     assert got[2] == [b.refine_params.e_ln_gem.offset, b.refine_params.flags.offset,
                       b.refine_scene_stats.mean_m.offset]
+    assert got[3] == [C.sizeof(b.refine_request), C.sizeof(b.refine_result), C.sizeof(b.refine_queue_stats)]
+    assert got[4] == [b.refine_request.ratio.offset, b.refine_request.kept_idx_host.offset,
+                      b.refine_result.threshold.offset, b.refine_result.done_ms.offset]
+    assert got[5] == [b.refine_queue_stats.max_round.offset, b.refine_queue_stats.kernel_launches.offset]
 
 
 def test_camera_dtype_matches_struct():
@@ -78,3 +85,23 @@ def test_params_default_and_errors_without_gpu(lib):
     assert b.refine_score(None, None, None, 1, None, None, None) == b.REFINE_EINVAL
     assert b.refine_select(None, None, 0, 0.5, None, None, None, None) == b.REFINE_EINVAL
     assert b.refine_ctx_launch_count(None) == -1
+    assert b.refine_queue_submit(None, None, None) == b.REFINE_EINVAL
+    assert b.refine_queue_poll(None, 1, None, 0) == b.REFINE_EINVAL
+    assert b.refine_queue_stats_get(None, None) == b.REFINE_EINVAL
+    b.refine_queue_destroy(None)
+
+
+def test_queue_footprint_host_only(lib):
+    """The admission size is host arithmetic: it covers the scene copy, the
+    outputs and the scratch, grows with n and rejects malformed requests."""
+    from paper_2606_09074_gb300 import binding as b
+    fp = b.Queue.footprint
+    n = 1_000_000
+    f32 = fp(n, b.REFINE_F32, 200, 0.5)
+    bf16 = fp(n, b.REFINE_BF16, 200, 0.5)
+    assert f32 > 236 * n + 120 * n          # scene copy + compacted half
+    assert bf16 < f32 and bf16 > 124 * n
+    assert fp(n, b.REFINE_F32, 200, 0.5, compact=False) < f32
+    assert fp(2 * n, b.REFINE_F32, 200, 0.5) > f32
+    assert fp(0, b.REFINE_F32, 200, 0.5) == 0 and fp(n, 7, 200, 0.5) == 0
+    assert fp(n, b.REFINE_F32, 513, 0.5) == 0 and fp(n, b.REFINE_F32, 200, 1.0) == 0

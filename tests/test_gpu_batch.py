@@ -73,11 +73,27 @@ def test_batch_rejects_bad_jobs(env):
     with pytest.raises(rb.RefineError):
         rb.Batch(ctx, [{"pos": p1, "attr": a1, "cams": c1, "ratio": 0.5},
                        {"pos": p2, "attr": a2, "cams": c2, "ratio": 0.5}])
-    w3 = synth.random_scene(seed=3, n=100, v=4)
-    w3.scene = w3.scene.to_bf16()
-    p3, a3, c3 = upload(torch, rb, w3)
-    with pytest.raises(rb.RefineError):  # mixed storage types
-        rb.Batch(ctx, [{"pos": p1, "attr": a1, "cams": c1, "ratio": 0.5},
-                       {"pos": p3, "attr": a3, "cams": c3, "ratio": 0.5}])
     with pytest.raises(rb.RefineError):
         rb.Batch(ctx, [{"pos": p1, "attr": a1, "cams": c1, "ratio": 1.0}])
+
+
+def test_batch_mixed_storage_and_flags(env):
+    """Scenes of both storage types share one batched launch; each equals
+    its own per-scene run."""
+    torch, rb, ctx = env
+    ws = []
+    for k, (seed, n, v) in enumerate([(41, 5000, 9), (42, 33_333, 40), (43, 700, 3)]):
+        w = synth.random_scene(seed=seed, n=n, v=v, means="core_shell")
+        if k % 2:
+            w.scene = w.scene.to_bf16()
+        ws.append(w)
+    up = [upload(torch, rb, w) for w in ws]
+    jobs = [{"pos": p, "attr": a, "cams": c, "ratio": 0.5} for (p, a, c) in up]
+    batch = rb.Batch(ctx, jobs)
+    batch.run()
+    nk_b, thr_b = batch.results()
+    for k, (p, a, c) in enumerate(up):
+        s = ctx.score(p, a, c)
+        m, thr, nk = ctx.select(s, 0.5)
+        assert torch.equal(batch.outputs[k]["scores"], s)
+        assert nk_b[k] == nk and thr_b[k] == thr
