@@ -415,6 +415,10 @@ def run_batch_mode(args):
     pairs = sum(x["n"] * x["V"] for x in scenes)
     ctx = rb.Context(0)
     stream = torch.cuda.current_stream(dev)
+    # tile and CTA shape of the score kernels from the autotuner (results do
+    # not depend on it); every path below runs with the tuned shape
+    best, table = ctx.autotune([{"pos": x["pos"], "attr": x["a16"], "cams": x["cams"], "ratio": x["ratio"]}
+                                for x in scenes], reps=3)
 
     def plain(key):
         outs = []
@@ -471,9 +475,195 @@ def run_batch_mode(args):
             "speedup_vs_plain_f32": res["plain_f32"]["wall_ms_per_batch"] / res["batched_bf16"]["wall_ms_per_batch"],
             "speedup_vs_plain_bf16": res["plain_bf16"]["wall_ms_per_batch"] / res["batched_bf16"]["wall_ms_per_batch"],
             "batched_scores_equal_plain": same, "results": res, "data": "synthetic",
+            "autotune": {"best": best, "candidates": table},
             "config": {"workload": "64 scenes, seeds 100-163, N log-uniform 50k-2M, V 50-300, ratio 0.66"}}
     print(json.dumps(line), flush=True)
     batch.close()
+    ctx.close()
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    lo, hi = int(math.floor(k)), int(math.ceil(k))
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+class _OutputSets:
+    """Page-locked output buffers for the serving run: `copies` sets per
+    pool scene, each sized for the largest kept count (ratio 0.5)."""
+
+    def __init__(self, torch, pool, copies):
+        self.free = []
+        self.cv = threading.Condition()
+        for p, sc in enumerate(pool):
+            nk = sc["n"] - sc["n"] // 2
+            sets = []
+            for _ in range(copies):
+                sets.append({"mask": torch.empty((sc["n"] + 31) // 32, dtype=torch.int32, pin_memory=True),
+                             "out_pos": torch.empty(3 * nk, dtype=torch.float32, pin_memory=True),
+                             "out_attr": torch.empty(56 * nk, dtype=torch.bfloat16, pin_memory=True),
+                             "idx": torch.empty(nk, dtype=torch.int32, pin_memory=True)})
+            self.free.append(sets)
+
+    def take(self, p):
+        with self.cv:
+            while not self.free[p]:
+                self.cv.wait()
+            return self.free[p].pop()
+
+    def give(self, p, s):
+        with self.cv:
+            self.free[p].append(s)
+            self.cv.notify_all()
+
+
+def _serve_pass(torch, rb, ctx, pool, jobs, arrivals, budget, slots, outsets, keep_ref, agreement, agree_first=0):
+    """Submits `jobs` [(pool index, ratio)] at `arrivals` (seconds from the
+    start; None = as fast as output buffers allow) and collects them.
+    Returns per-job latencies (ms) and the wall time (s)."""
+    q = rb.Queue(ctx, budget_bytes=budget, max_slots=slots)
+    sub = []  # (ticket, pool index, ratio, outputs, arrival perf time, submit perf time)
+    lock = threading.Lock()
+    ready = threading.Semaphore(0)
+    t_start = time.perf_counter()
+
+    def feeder():
+        for k, (p, r) in enumerate(jobs):
+            if arrivals is not None:
+                delay = t_start + arrivals[k] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            t_arr = t_start + arrivals[k] if arrivals is not None else time.perf_counter()
+            outs = outsets.take(p)
+            sc = pool[p]
+            t_sub = time.perf_counter()
+            t = q.submit(sc["pos"], sc["a16"], sc["cams"], r, outputs=outs, mask=True, compact=True)
+            with lock:
+                sub.append((t, p, r, outs, t_arr, t_sub))
+            ready.release()
+
+    th = threading.Thread(target=feeder, daemon=True)
+    th.start()
+    lat, rounds = [], []
+    for k in range(len(jobs)):
+        ready.acquire()
+        with lock:
+            t, p, r, outs, t_arr, t_sub = sub[k]
+        res, _ = q.poll(t, timeout_ms=-1)
+        if res["status"] != 0:
+            raise RuntimeError(f"serving job {k} failed: status {res['status']} {q.last_error()}")
+        # queue clock: submit -> done; host clock: arrival -> submit
+        lat.append(res["done_ms"] - res["submit_ms"] + (t_sub - t_arr) * 1000.0)
+        rounds.append(res["round_size"])
+        if agreement is not None and (p, r) in keep_ref and k < agree_first:
+            nk = res["n_keep"]
+            keep = np.zeros(pool[p]["n"], dtype=bool)
+            keep[outs["idx"][:nk].numpy()] = True
+            agreement.append(float(np.mean(keep == keep_ref[(p, r)])))
+        outsets.give(p, outs)
+    wall = time.perf_counter() - t_start
+    th.join()
+    st = q.stats()
+    q.close()
+    return lat, wall, rounds, st
+
+
+def run_serve_mode(args):
+    """Serving workload: pruning jobs drawn as the 2,000-job stream (seeds
+    1000.., N log-uniform in [50k, 3.5M], V in 50..300, ratio from {0.5,
+    0.66, 0.9}, Poisson arrivals at 20/s from seed 999), served by the
+    request queue with BF16 storage from page-locked host memory, against the
+    plain FP32 per-scene path (refine_prune_host) as a single FIFO server."""
+    import torch
+    from paper_2606_09074_gb300 import binding as rb
+    from paper_2606_09074_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    P = args.pool
+    pool = []
+    for k in range(P):
+        w = synth.job_scene(1000 + k, dtype="f32")
+        a16 = torch.from_numpy(synth.f32_to_bf16_bits(w.scene.attr).view(np.int16)).view(torch.bfloat16)
+        pool.append({"pos": torch.from_numpy(w.scene.pos).pin_memory(),
+                     "a32": torch.from_numpy(w.scene.attr).pin_memory(), "a16": a16.pin_memory(),
+                     "cams": w.cams, "n": w.scene.n, "V": len(w.cams)})
+    ratio_of = lambda k: synth.job_spec(1000 + k)[3]  # noqa: E731
+    jobs = [(k % P, ratio_of(k)) for k in range(args.jobs)]
+    arrivals = synth.job_arrivals(args.jobs, rate=args.rate, seed=999)
+    sat_jobs = [(k % P, ratio_of(k)) for k in range(args.sat_jobs)]
+    ctx = rb.Context(0)
+
+    # keep masks of the plain FP32 per-scene path, for the mask agreement
+    keep_ref = {}
+    for p, r in sorted(set(jobs)):
+        sc = pool[p]
+        res = ctx.prune_host(sc["pos"], sc["a32"], sc["cams"], r)
+        keep = np.zeros(sc["n"], dtype=bool)
+        keep[res["idx"].numpy()] = True
+        keep_ref[(p, r)] = keep
+
+    def plain_server(job_list, arr):
+        """The plain FP32 path as one FIFO server thread fed the same
+        arrivals (None = back to back): returns latencies (ms) and wall (s)."""
+        lat = []
+        t_start = time.perf_counter()
+        for k, (p, r) in enumerate(job_list):
+            if arr is not None:
+                delay = t_start + arr[k] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            t_arr = t_start + arr[k] if arr is not None else time.perf_counter()
+            sc = pool[p]
+            ctx.prune_host(sc["pos"], sc["a32"], sc["cams"], r, out=plain_out[p])
+            lat.append((time.perf_counter() - t_arr) * 1000.0)
+        return lat, time.perf_counter() - t_start
+
+    plain_out = []
+    for sc in pool:
+        nk = sc["n"] - sc["n"] // 2
+        plain_out.append({"out_pos": torch.empty((3, nk), dtype=torch.float32, pin_memory=True),
+                          "out_attr": torch.empty((56, nk), dtype=torch.float32, pin_memory=True),
+                          "idx": torch.empty(nk, dtype=torch.int32, pin_memory=True)})
+    plain_lat, _ = plain_server(jobs, arrivals)
+    _, plain_wall = plain_server(sat_jobs, None)
+    plain_sat = len(sat_jobs) / plain_wall
+
+    budget = int(args.budget_gb * (1 << 30))
+    outsets = _OutputSets(torch, pool, copies=args.copies)
+    # warm the queue path (pool growth, module loads) on a few jobs
+    _serve_pass(torch, rb, ctx, pool, sat_jobs[: min(8, len(sat_jobs))], None, budget, args.slots, outsets, {}, None)
+    agree = []
+    lat, wall, rounds, st = _serve_pass(torch, rb, ctx, pool, jobs, arrivals, budget, args.slots, outsets,
+                                        keep_ref, agree, agree_first=len(jobs))
+    lat_s, wall_s, rounds_s, st_s = _serve_pass(torch, rb, ctx, pool, sat_jobs, None, budget, args.slots, outsets,
+                                                keep_ref, None)
+    served_sat = len(sat_jobs) / wall_s
+    pairs = sum(pool[p]["n"] * pool[p]["V"] for p, _ in sat_jobs)
+    line = {"mode": "serve", "metric": "scenes/s", "value": served_sat, "unit": "scenes/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32 (bf16 storage)", "data": "synthetic",
+            "poisson": {"jobs": len(jobs), "rate_per_s": args.rate, "wall_s": wall,
+                        "p50_ms": _percentile(lat, 0.5), "p99_ms": _percentile(lat, 0.99),
+                        "plain_f32_p50_ms": _percentile(plain_lat, 0.5),
+                        "plain_f32_p99_ms": _percentile(plain_lat, 0.99),
+                        "mean_round": statistics.mean(rounds), "max_round": max(rounds)},
+            "saturation": {"jobs": len(sat_jobs), "served_scenes_per_s": served_sat,
+                           "served_pairs_per_s": pairs / wall_s, "plain_f32_scenes_per_s": plain_sat,
+                           "speedup_vs_plain_f32": served_sat / plain_sat,
+                           "p50_ms": _percentile(lat_s, 0.5), "p99_ms": _percentile(lat_s, 0.99),
+                           "mean_round": statistics.mean(rounds_s), "max_round": max(rounds_s)},
+            "mask_agreement_vs_plain_f32": {"min": min(agree), "mean": statistics.mean(agree),
+                                            "jobs": len(agree), "below_99.9": sum(a < 0.999 for a in agree)},
+            "queue": {"budget_bytes": budget, "slots": args.slots, "peak_bytes": max(st["peak_bytes"],
+                                                                                      st_s["peak_bytes"])},
+            "config": {"workload": f"serving: {args.jobs} Poisson jobs at {args.rate}/s + {args.sat_jobs} "
+                                   f"back-to-back; scenes from a pool of {P} (seeds 1000-{999 + P}), ratio per "
+                                   f"job seed, BF16 storage, budget {args.budget_gb} GB",
+                       "plain_path": "refine_prune_host, FP32, one FIFO server thread fed the same arrivals "
+                                     "from page-locked host memory"}}
+    print(json.dumps(line), flush=True)
     ctx.close()
 
 
@@ -487,10 +677,18 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
-    ap.add_argument("--mode", default="single", choices=["single", "batch"],
-                    help="single: the default workload; batch: 64 scenes, batched vs per-scene")
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
+                    help="single: the default workload; batch: 64 scenes, batched vs per-scene; "
+                         "serve: the request queue under Poisson and back-to-back arrivals")
     ap.add_argument("--scenes", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--jobs", type=int, default=300, help="serve: Poisson jobs")
+    ap.add_argument("--sat-jobs", type=int, default=200, help="serve: back-to-back jobs")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
+    ap.add_argument("--pool", type=int, default=16, help="serve: distinct scenes")
+    ap.add_argument("--copies", type=int, default=2, help="serve: output buffer sets per scene")
+    ap.add_argument("--slots", type=int, default=8, help="serve: requests in flight")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
     ap.add_argument("--accuracy", action="store_true",
                     help="also report error and mask agreement against the FP64 oracle")
     args = ap.parse_args(argv)
@@ -502,6 +700,8 @@ def main(argv=None):
         run_reference(args, rank, world)
     elif args.mode == "batch":
         run_batch_mode(args)
+    elif args.mode == "serve":
+        run_serve_mode(args)
     else:
         run_ours(args, rank, world)
 

@@ -279,6 +279,37 @@ int64_t refine_batch_launches(const refine_batch *batch);
 /* Releases the batch (synchronising its device first).  NULL is a no-op. */
 void refine_batch_destroy(refine_batch *batch);
 
+/* ------------------------------------------------------------ autotuner
+ * Work-item shape of the score kernels.  A warp scores a tile of 32 or 64
+ * consecutive primitives of the processing order against every view; the
+ * batched kernel hands out CTA-sized items of such tiles.  Every primitive's
+ * score is computed by one thread with the views in a fixed order, whatever
+ * tile it is in, so the shape changes speed only: results are bit-identical
+ * for every shape. */
+typedef struct refine_shape {
+    int32_t tile;         /* primitives per warp tile: 32 or 64 (default 64)            */
+    int32_t cta_threads;  /* threads per CTA of the batched kernel: 128 or 256          */
+    int32_t ctas_per_sm;  /* cap on resident CTAs per SM (batched kernel), 0 = all fit */
+    int32_t reserved;
+    double ms;            /* refine_autotune: measured time of one batched score launch */
+} refine_shape;
+
+/* Times the batched score launch of `jobs` (as refine_batch_create takes
+ * them; their scores are written) under every candidate shape, `reps`
+ * launches each after one warm-up, and makes the fastest the context's shape
+ * (used by refine_score and by batches and queues created afterwards).
+ * *best_out (may be NULL) receives it; table_out (may be NULL) receives up to
+ * table_cap candidates in the order tried, *table_count their number.
+ * EINVAL for bad jobs or reps < 1. */
+refine_status refine_autotune(refine_ctx *ctx, const refine_job *jobs, int32_t n_jobs,
+                              const refine_params *params, int32_t reps, refine_shape *best_out,
+                              refine_shape *table_out, int32_t table_cap, int32_t *table_count);
+
+/* Reads or sets the context's shape (EINVAL for a shape outside the
+ * candidates: tile 32 or 64, cta_threads 128 or 256, ctas_per_sm >= 0). */
+refine_status refine_ctx_get_shape(const refine_ctx *ctx, refine_shape *out);
+refine_status refine_ctx_set_shape(refine_ctx *ctx, const refine_shape *shape);
+
 /* ------------------------------------------------------ request queue
  * A serving loop for pruning requests (Sec. 3.3 applied to a stream of
  * scenes).  Two native threads own the GPU work:

@@ -86,6 +86,11 @@ class refine_job(C.Structure):
                 ("out_row_stride", C.c_int64), ("kept_idx_dev", C.c_void_p)]
 
 
+class refine_shape(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("reserved", C.c_int32), ("ms", C.c_double)]
+
+
 class refine_request(C.Structure):
     _fields_ = [("n", C.c_int64), ("dtype", C.c_int32), ("n_views", C.c_int32), ("pos_host", C.c_void_p),
                 ("attr_host", C.c_void_p), ("cams_host", C.c_void_p), ("ratio", C.c_double),
@@ -108,6 +113,7 @@ class refine_queue_stats(C.Structure):
 
 assert C.sizeof(refine_camera) == 80 and C.sizeof(refine_scene) == 40 and C.sizeof(refine_job) == 112
 assert C.sizeof(refine_params) == 48
+assert C.sizeof(refine_shape) == 24
 assert C.sizeof(refine_request) == 96 and C.sizeof(refine_result) == 48 and C.sizeof(refine_queue_stats) == 88
 
 _P = C.c_void_p
@@ -136,6 +142,11 @@ _SIGNATURES = {
     "refine_batch_results": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_float), _P]),
     "refine_batch_launches": (C.c_int64, [_P]),
     "refine_batch_destroy": (None, [_P]),
+    "refine_autotune": (C.c_int, [_P, C.POINTER(refine_job), C.c_int32, C.POINTER(refine_params), C.c_int32,
+                                  C.POINTER(refine_shape), C.POINTER(refine_shape), C.c_int32,
+                                  C.POINTER(C.c_int32)]),
+    "refine_ctx_get_shape": (C.c_int, [_P, C.POINTER(refine_shape)]),
+    "refine_ctx_set_shape": (C.c_int, [_P, C.POINTER(refine_shape)]),
     "refine_queue_footprint": (C.c_uint64, [C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_int32]),
     "refine_queue_create": (C.c_int, [_P, C.c_uint64, C.c_int32, C.POINTER(refine_params),
                                       C.POINTER(C.c_void_p)]),
@@ -363,6 +374,67 @@ class Context:
     def launch_count(self) -> int:
         return int(refine_ctx_launch_count(self.handle))  # noqa: F821
 
+    def autotune(self, jobs, params=None, reps=3):
+        """Times the batched score launch of ``jobs`` (device-tensor dicts as
+        for Batch) under every candidate shape and keeps the fastest for this
+        context.  Returns (best, table) as dicts."""
+        arr, outs, keep = _make_jobs(self, jobs, compact=False)  # outs must outlive the call
+        best = refine_shape()
+        table = (refine_shape * 16)()
+        cnt = C.c_int32()
+        _check(self.handle, refine_autotune(self.handle, arr, len(jobs),  # noqa: F821
+                                            C.byref(params) if params is not None else None, int(reps),
+                                            C.byref(best), table, 16, C.byref(cnt)))
+        del outs, keep
+        return _shape_dict(best), [_shape_dict(table[k]) for k in range(min(cnt.value, 16))]
+
+    def get_shape(self) -> dict:
+        sh = refine_shape()
+        _check(self.handle, refine_ctx_get_shape(self.handle, C.byref(sh)))  # noqa: F821
+        return _shape_dict(sh)
+
+    def set_shape(self, tile=64, cta_threads=256, ctas_per_sm=0):
+        sh = refine_shape(tile, cta_threads, ctas_per_sm, 0, 0.0)
+        _check(self.handle, refine_ctx_set_shape(self.handle, C.byref(sh)))  # noqa: F821
+
+
+def _make_jobs(ctx, jobs, compact=True):
+    """refine_job array for device-tensor job dicts (pos, attr, cams, ratio,
+    optional compact=False), with the score, mask and compaction outputs."""
+    import torch
+    keep, outputs = [], []
+    arr = (refine_job * len(jobs))()
+    for k, jd in enumerate(jobs):
+        pos, attr, cams = jd["pos"], jd["attr"], jd["cams"]
+        n = pos.shape[1]
+        ratio = float(jd["ratio"])
+        n_keep = n - int(np.floor(ratio * n))
+        out = {"scores": torch.empty(n, dtype=torch.float32, device=ctx.device),
+               "mask": torch.empty((n + 31) // 32, dtype=torch.int32, device=ctx.device)}
+        j = arr[k]
+        j.scene = make_scene(pos, attr)
+        j.cams_dev = cams.data_ptr()
+        j.n_views = cams.numel() // 80
+        j.ratio = ratio
+        j.scores_dev = out["scores"].data_ptr()
+        j.keep_mask_dev = out["mask"].data_ptr()
+        if compact and jd.get("compact", True):
+            out["out_pos"] = torch.empty((3, max(n_keep, 1)), dtype=torch.float32, device=ctx.device)
+            out["out_attr"] = torch.empty((56, max(n_keep, 1)), dtype=attr.dtype, device=ctx.device)
+            out["idx"] = torch.empty(max(n_keep, 1), dtype=torch.int32, device=ctx.device)
+            j.out_pos_dev = out["out_pos"].data_ptr()
+            j.out_attr_dev = out["out_attr"].data_ptr()
+            j.out_row_stride = max(n_keep, 1)
+            j.kept_idx_dev = out["idx"].data_ptr()
+        out["n_keep"] = n_keep
+        outputs.append(out)
+        keep.append((pos, attr, cams))
+    return arr, outputs, keep
+
+
+def _shape_dict(sh) -> dict:
+    return {"tile": sh.tile, "cta_threads": sh.cta_threads, "ctas_per_sm": sh.ctas_per_sm, "ms": sh.ms}
+
 
 class Batch:
     """A batch of scenes scored by one persistent launch and replayed as a
@@ -372,36 +444,8 @@ class Batch:
     tensor alive for its lifetime."""
 
     def __init__(self, ctx: Context, jobs, params=None, compact=True):
-        import torch
         self.ctx = ctx
-        self.keep = []
-        self.outputs = []
-        arr = (refine_job * len(jobs))()
-        for k, jd in enumerate(jobs):
-            pos, attr, cams = jd["pos"], jd["attr"], jd["cams"]
-            n = pos.shape[1]
-            ratio = float(jd["ratio"])
-            n_keep = n - int(np.floor(ratio * n))
-            out = {"scores": torch.empty(n, dtype=torch.float32, device=ctx.device),
-                   "mask": torch.empty((n + 31) // 32, dtype=torch.int32, device=ctx.device)}
-            j = arr[k]
-            j.scene = make_scene(pos, attr)
-            j.cams_dev = cams.data_ptr()
-            j.n_views = cams.numel() // 80
-            j.ratio = ratio
-            j.scores_dev = out["scores"].data_ptr()
-            j.keep_mask_dev = out["mask"].data_ptr()
-            if compact and jd.get("compact", True):
-                out["out_pos"] = torch.empty((3, max(n_keep, 1)), dtype=torch.float32, device=ctx.device)
-                out["out_attr"] = torch.empty((56, max(n_keep, 1)), dtype=attr.dtype, device=ctx.device)
-                out["idx"] = torch.empty(max(n_keep, 1), dtype=torch.int32, device=ctx.device)
-                j.out_pos_dev = out["out_pos"].data_ptr()
-                j.out_attr_dev = out["out_attr"].data_ptr()
-                j.out_row_stride = max(n_keep, 1)
-                j.kept_idx_dev = out["idx"].data_ptr()
-            out["n_keep"] = n_keep
-            self.outputs.append(out)
-            self.keep.append((pos, attr, cams))
+        arr, self.outputs, self.keep = _make_jobs(ctx, jobs, compact)
         self.n = len(jobs)
         h = C.c_void_p()
         rc = refine_batch_create(ctx.handle, arr, len(jobs), C.byref(params) if params is not None else None,  # noqa: F821

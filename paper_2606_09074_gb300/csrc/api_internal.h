@@ -92,6 +92,7 @@ struct refine_ctx {
     double ms[refine_api::K_NCLASS] = {0};
     int64_t launches[refine_api::K_NCLASS] = {0};
     int64_t launch_count = 0;
+    refine::ScoreShape shape;  // work-item shape of the score kernels (refine_autotune)
 };
 
 namespace refine_api {
@@ -374,8 +375,8 @@ inline refine_status score_impl(refine_ctx *c, const refine_scene *sc, const ref
     if ((st = enqueue_prep(c, run, sc, cams, pl, x, p, need_dev != nullptr, c->d_status, s))) return st;
     for (int v0 = 0; v0 < V; v0 += kViewsPerPass) {
         ScoreLaunch a = make_score_launch(sc, pl, x, p, v0, scores, view_sum, need_dev != nullptr, c->d_status);
-        a.grid = score_grid(c->num_sms, pl.n, a.vcount);
-        if ((st = launch(c, K_SCORE, s, [&] { return launch_score(a, s); }))) return st;
+        a.grid = score_grid(c->num_sms, pl.n, a.vcount, c->shape);
+        if ((st = launch(c, K_SCORE, s, [&] { return launch_score(a, c->shape, s); }))) return st;
     }
     return REFINE_OK;
 }

@@ -14,8 +14,19 @@ namespace refine {
 // larger view set is split into passes of this size; pass boundaries fall
 // on multiples of 32 views so the summation order is independent of it.
 constexpr int kViewsPerPass = 512;
-constexpr int kScoreThreads = 256;
-constexpr int kScoreGPT = 2;          // primitives per thread in k_score
+constexpr int kScoreThreads = 256;     // threads per CTA of k_score
+
+// Work-item shape of the score kernels, chosen per device by the autotuner
+// (refine_autotune).  Every primitive's score is computed by one thread with
+// the views in a fixed order, whatever tile it is in, so the shape changes
+// speed only, never a result.
+struct ScoreShape {
+    int gpt = 2;          // primitives per thread: a warp's tile is 32 * gpt primitives (1 or 2)
+    int threads = 256;    // threads per CTA of the batched kernel (128 or 256); k_score uses kScoreThreads
+    int ctas_per_sm = 0;  // cap on resident CTAs per SM of the batched kernel (0 = as many as fit)
+};
+bool shape_valid(const ScoreShape &sh);
+inline int64_t batch_tile(const ScoreShape &sh) { return (int64_t)sh.threads * sh.gpt; }
 constexpr int kFeatThreads = 256;
 
 // Spatial cells for the processing order of k_score: a 2^b x 2^b x 2^b grid
@@ -93,8 +104,8 @@ cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bs
 cudaError_t launch_cell_scatter(const uint32_t *cell, int64_t n, unsigned *counts,
                                 const unsigned *off_local, const unsigned *bsum, uint32_t *perm,
                                 int num_sms, cudaStream_t s);
-cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s);
-int score_grid(int num_sms, int64_t n, int vcount);
+cudaError_t launch_score(const ScoreLaunch &a, const ScoreShape &sh, cudaStream_t s);
+int score_grid(int num_sms, int64_t n, int vcount, const ScoreShape &sh);
 
 // Batched score launch over the tiles of many scenes (each scene a single
 // pass of at most kViewsPerPass views).
@@ -106,8 +117,8 @@ struct BatchLaunch {
     unsigned long long *counter;     // device, zero before the launch
     int *status;
 };
-int score_batch_grid(int num_sms, int max_vcount);
-cudaError_t launch_score_batch(const BatchLaunch &b, int max_vcount, int grid, cudaStream_t s);
+int score_batch_grid(int num_sms, int max_vcount, const ScoreShape &sh);
+cudaError_t launch_score_batch(const BatchLaunch &b, int max_vcount, int grid, const ScoreShape &sh, cudaStream_t s);
 
 // ------------------------------------------------------------- select
 struct SelState {

@@ -407,9 +407,10 @@ cudaError_t launch_cell_scatter(const uint32_t *cell, int64_t n, unsigned *count
 //    centre outside is first tested against Qx <= 9 s_max^2 ((U - cx z)^2 +
 //    fx^2 z^2) (as |g0|^2 = fx^2 (x^2 + z^2); inflated by 2^-10), and only
 //    lanes passing that bound need Qx and Qy.
-// Views are summed in blocks of 16 into a running total, in view order (an
-// invisible or skipped view adds +0, which changes nothing), so a
-// primitive's sum does not depend on the tile it is in.
+// Views are summed in blocks of 16, in view order (an invisible or skipped
+// view adds +0, which changes nothing), and the block sums are added to the
+// primitive's total with Kahan compensation, so a primitive's sum does not
+// depend on the tile it is in and its rounding error does not grow with V.
 // The epilogue forms D_i = alpha_i S_i / |V| * sum_k lambda^k G~_i^k (Eq. 7).
 // ---------------------------------------------------------------------
 struct PairIn {
@@ -512,16 +513,16 @@ __device__ __forceinline__ float weight(float z, float eta)
     return NOPROJ ? 1.f : rcp_approx(fmaf(z, z, eta));
 }
 
-template <bool NOPROJ, bool DET, bool COUNT>
-__device__ __forceinline__ void mixed_view(const CamRec &c, float eta, const PairIn (&p)[kScoreGPT],
-                                           const bool (&valid)[kScoreGPT], float (&part)[kScoreGPT],
+template <bool NOPROJ, bool DET, bool COUNT, int GPT>
+__device__ __forceinline__ void mixed_view(const CamRec &c, float eta, const PairIn (&p)[GPT],
+                                           const bool (&valid)[GPT], float (&part)[GPT],
                                            unsigned long long (&cnt)[kCountSlots])
 {
     const float4 c0 = c.r0, c1 = c.r1, c2 = c.r2, lim = c.lim;
-    PairGeom q[kScoreGPT];
-    bool vis[kScoreGPT], out = false;
+    PairGeom q[GPT];
+    bool vis[GPT], out = false;
 #pragma unroll
-    for (int g = 0; g < kScoreGPT; ++g) {
+    for (int g = 0; g < GPT; ++g) {
         q[g] = pair_geom(c0, c1, c2, lim, p[g]);
         vis[g] = q[g].inside;
         out |= q[g].inz & !q[g].inside;
@@ -529,9 +530,9 @@ __device__ __forceinline__ void mixed_view(const CamRec &c, float eta, const Pai
     }
     if (DET || __any_sync(0xffffffffu, out)) {
         const float4 k = c.k;
-        bool nearq = false, nq[kScoreGPT];
+        bool nearq = false, nq[GPT];
 #pragma unroll
-        for (int g = 0; g < kScoreGPT; ++g) {
+        for (int g = 0; g < GPT; ++g) {
             const float tx = fmaf(-k.z, q[g].z, q[g].U), ty = fmaf(-k.w, q[g].z, q[g].V);
             const float zz = q[g].z * q[g].z;
             const bool o = q[g].inz & !q[g].inside;
@@ -544,23 +545,24 @@ __device__ __forceinline__ void mixed_view(const CamRec &c, float eta, const Pai
         }
         if (DET || __any_sync(0xffffffffu, nearq)) {
 #pragma unroll
-            for (int g = 0; g < kScoreGPT; ++g)
+            for (int g = 0; g < GPT; ++g)
                 vis[g] = q[g].inz & exact_box<DET>(c0, c1, c2, q[g].U, q[g].V, q[g].z, q[g].ex2, q[g].ey2, p[g]);
         }
     }
 #pragma unroll
-    for (int g = 0; g < kScoreGPT; ++g) part[g] += vis[g] ? weight<NOPROJ>(q[g].z, eta) : 0.f;
+    for (int g = 0; g < GPT; ++g) part[g] += vis[g] ? weight<NOPROJ>(q[g].z, eta) : 0.f;
 }
 
-template <bool NOPROJ, bool DET, bool COUNT>
-__device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float eta, const PairIn (&p)[kScoreGPT],
-                                          const bool (&valid)[kScoreGPT], const TileBox &tb,
-                                          float (&acc)[kScoreGPT], unsigned long long (&cnt)[kCountSlots])
+template <bool NOPROJ, bool DET, bool COUNT, int GPT>
+__device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float eta, const PairIn (&p)[GPT],
+                                          const bool (&valid)[GPT], const TileBox &tb,
+                                          float (&acc)[GPT], float (&comp)[GPT],
+                                          unsigned long long (&cnt)[kCountSlots])
 {
     const int lane = threadIdx.x & 31;
     int nvalid = 0;
 #pragma unroll
-    for (int g = 0; g < kScoreGPT; ++g) nvalid += __popc(__ballot_sync(0xffffffffu, valid[g]));
+    for (int g = 0; g < GPT; ++g) nvalid += __popc(__ballot_sync(0xffffffffu, valid[g]));
     for (int vb = 0; vb < vcount; vb += 32) {
         const int nv = min(32, vcount - vb);
         const unsigned vmask = nv == 32 ? 0xffffffffu : ((1u << nv) - 1u);
@@ -579,9 +581,9 @@ __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float et
         for (int half = 0; half < 2; ++half) {
             const unsigned hm = (half ? 0xffff0000u : 0x0000ffffu) & vmask;
             if (!hm) break;
-            float part[kScoreGPT];
+            float part[GPT];
 #pragma unroll
-            for (int g = 0; g < kScoreGPT; ++g) part[g] = 0.f;
+            for (int g = 0; g < GPT; ++g) part[g] = 0.f;
             unsigned todo = hm & ~out_m;
             while (todo) {
                 const int b = __ffs(todo) - 1;
@@ -590,16 +592,22 @@ __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float et
                 if ((in_m >> b) & 1u) {
                     const float4 c2 = c.r2;
 #pragma unroll
-                    for (int g = 0; g < kScoreGPT; ++g) {
+                    for (int g = 0; g < GPT; ++g) {
                         const float z = fmaf(c2.x, p[g].mx, fmaf(c2.y, p[g].my, fmaf(c2.z, p[g].mz, c2.w)));
                         part[g] += weight<NOPROJ>(z, eta);
                     }
                 } else {
-                    mixed_view<NOPROJ, DET, COUNT>(c, eta, p, valid, part, cnt);
+                    mixed_view<NOPROJ, DET, COUNT, GPT>(c, eta, p, valid, part, cnt);
                 }
             }
+            // Kahan-compensated sum of the 16-view partial sums
 #pragma unroll
-            for (int g = 0; g < kScoreGPT; ++g) acc[g] += part[g];
+            for (int g = 0; g < GPT; ++g) {
+                const float y = part[g] - comp[g];
+                const float t = acc[g] + y;
+                comp[g] = (t - acc[g]) - y;
+                acc[g] = t;
+            }
         }
     }
 }
@@ -628,33 +636,34 @@ __device__ __forceinline__ void fence_proxy_async_shared()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Scores one tile of kScoreThreads * kScoreGPT primitives of the processing
+// Scores one tile of blockDim.x * GPT primitives of the processing
 // order starting at `base`; `next_base` (or -1) is the tile this CTA takes
 // next, whose primitives are pulled towards L2 meanwhile.
-template <bool NOPROJ, bool COUNT>
+template <bool NOPROJ, bool COUNT, int GPT>
 __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *cs, const SceneConsts &sc,
                                            int64_t base, int64_t next_base, unsigned long long (&cnt)[kCountSlots])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (next_base >= 0) {
 #pragma unroll
-        for (int g = 0; g < kScoreGPT; ++g) {
-            const int64_t j = next_base + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
+        for (int g = 0; g < GPT; ++g) {
+            const int64_t j = next_base + (int64_t)warp * 32 * GPT + g * 32 + lane;
             if (j < a.n) prefetch_l2(a.recs + __ldg(a.perm + j));
         }
     }
-    PairIn p[kScoreGPT];
-    float acc[kScoreGPT];
-    int64_t idx[kScoreGPT];
-    bool valid[kScoreGPT];
+    PairIn p[GPT];
+    float acc[GPT], comp[GPT];
+    int64_t idx[GPT];
+    bool valid[GPT];
     bool degen = false;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, b2 = 0.f;
 #pragma unroll
-    for (int g = 0; g < kScoreGPT; ++g) {
-        const int64_t j = base + (int64_t)warp * 32 * kScoreGPT + g * 32 + lane;
+    for (int g = 0; g < GPT; ++g) {
+        const int64_t j = base + (int64_t)warp * 32 * GPT + g * 32 + lane;
         float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
         idx[g] = -1;
         acc[g] = 0.f;
+        comp[g] = 0.f;
         valid[g] = j < a.n;
         if (valid[g]) {
             const int64_t i = __ldg(a.perm + j);
@@ -691,19 +700,19 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
     }
 
     if (__any_sync(0xffffffffu, degen))
-        view_loop<NOPROJ, true, COUNT>(cs, a.vcount, a.eta, p, valid, tb, acc, cnt);
+        view_loop<NOPROJ, true, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tb, acc, comp, cnt);
     else
-        view_loop<NOPROJ, false, COUNT>(cs, a.vcount, a.eta, p, valid, tb, acc, cnt);
+        view_loop<NOPROJ, false, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tb, acc, comp, cnt);
 
 #pragma unroll
-    for (int g = 0; g < kScoreGPT; ++g) {
+    for (int g = 0; g < GPT; ++g) {
         const int64_t i = idx[g];
         if (i < 0) continue;
+        const float Ssum = acc[g] - comp[g];
         if (!a.last) {
-            a.running[i] = acc[g];
+            a.running[i] = Ssum;
             continue;
         }
-        const float Ssum = acc[g];
         if (a.view_sum) a.view_sum[i] = Ssum;
         const float4 rd = __ldg(&a.recs[i].d);  // (L8, alpha, m_gem, m_col)
         const float coupled = fmaf(sc.kappa[0], rd.z, fmaf(sc.kappa[1], rd.w, sc.kappa[2] * rd.y));
@@ -722,7 +731,7 @@ __device__ __forceinline__ int cams_stageable(const CamRec *cams, int vcount)
            (uint64_t)vcount * sizeof(CamRec) <= (uint64_t)dyn;
 }
 
-template <bool NOPROJ, bool COUNT>
+template <bool NOPROJ, bool COUNT, int GPT>
 __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -757,9 +766,9 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 #pragma unroll
     for (int k = 0; k < kCountSlots; ++k) cnt[k] = 0;
     const SceneConsts sc = *a.consts;
-    const int64_t tile = (int64_t)blockDim.x * kScoreGPT;
+    const int64_t tile = (int64_t)blockDim.x * GPT;
     for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile)
-        score_tile<NOPROJ, COUNT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
+        score_tile<NOPROJ, COUNT, GPT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
     if (COUNT) {
         const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -778,7 +787,8 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 // cameras by TMA.  Every tile is scored by score_tile exactly as in
 // k_score, so a scene's scores are the same alone and in a batch; scenes
 // may differ in storage type (the records are float32) and in flags.
-__global__ void __launch_bounds__(kScoreThreads, 3) k_score_batch(BatchLaunch b)
+template <int GPT, int THREADS>
+__global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLaunch b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
@@ -790,7 +800,7 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_batch(BatchLaunch b)
     unsigned long long cnt[kCountSlots];
     int cur = -1;
     uint32_t phase = 0;
-    const int64_t tile = (int64_t)blockDim.x * kScoreGPT;
+    const int64_t tile = (int64_t)blockDim.x * GPT;
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long item = atomicAdd(b.counter, 1ull);
@@ -843,47 +853,59 @@ __global__ void __launch_bounds__(kScoreThreads, 3) k_score_batch(BatchLaunch b)
         }
         const SceneConsts sc = *a.consts;
         if (a.flags & REFINE_FLAG_NO_PROJ)
-            score_tile<true, false>(a, cs, sc, base, -1, cnt);
+            score_tile<true, false, GPT>(a, cs, sc, base, -1, cnt);
         else
-            score_tile<false, false>(a, cs, sc, base, -1, cnt);
+            score_tile<false, false, GPT>(a, cs, sc, base, -1, cnt);
         __syncthreads();  // the cameras and s_scene are free again
     }
 }
 
-template <bool NOPROJ, bool COUNT>
+template <bool NOPROJ, bool COUNT, int GPT>
 static const void *score_fn()
 {
-    return reinterpret_cast<const void *>(&k_score<NOPROJ, COUNT>);
+    return reinterpret_cast<const void *>(&k_score<NOPROJ, COUNT, GPT>);
 }
 
-static const void *pick_score(bool noproj, bool count)
+template <int GPT>
+static const void *pick_score_g(bool noproj, bool count)
 {
-    if (count) return noproj ? score_fn<true, true>() : score_fn<false, true>();
-    return noproj ? score_fn<true, false>() : score_fn<false, false>();
+    if (count) return noproj ? score_fn<true, true, GPT>() : score_fn<false, true, GPT>();
+    return noproj ? score_fn<true, false, GPT>() : score_fn<false, false, GPT>();
 }
 
-int score_grid(int num_sms, int64_t n, int vcount)
+static const void *pick_score(bool noproj, bool count, int gpt)
+{
+    return gpt == 1 ? pick_score_g<1>(noproj, count) : pick_score_g<2>(noproj, count);
+}
+
+bool shape_valid(const ScoreShape &sh)
+{
+    return (sh.gpt == 1 || sh.gpt == 2) && (sh.threads == 128 || sh.threads == 256);
+}
+
+int score_grid(int num_sms, int64_t n, int vcount, const ScoreShape &sh)
 {
     // Persistent grid: as many CTAs as fit per SM, capped by the tile count.
     int per_sm = 0;
     const size_t smem = (size_t)vcount * sizeof(CamRec);
-    const void *fn = pick_score(false, false);
+    const void *fn = pick_score(false, false, sh.gpt);
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kScoreThreads, smem) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
-    const int64_t tiles = (n + (int64_t)kScoreThreads * kScoreGPT - 1) / ((int64_t)kScoreThreads * kScoreGPT);
+    const int64_t tile = (int64_t)kScoreThreads * sh.gpt;
+    const int64_t tiles = (n + tile - 1) / tile;
     int64_t g = (int64_t)num_sms * per_sm;
     if (g > tiles) g = tiles;
     if (g < 1) g = 1;
     return (int)g;
 }
 
-cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s)
+cudaError_t launch_score(const ScoreLaunch &a, const ScoreShape &sh, cudaStream_t s)
 {
-    const void *fn = pick_score((a.flags & REFINE_FLAG_NO_PROJ) != 0, a.need != nullptr);
+    const void *fn = pick_score((a.flags & REFINE_FLAG_NO_PROJ) != 0, a.need != nullptr, sh.gpt);
     const size_t smem = (size_t)a.vcount * sizeof(CamRec);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -894,29 +916,40 @@ cudaError_t launch_score(const ScoreLaunch &a, cudaStream_t s)
     return cudaLaunchKernel(fn, dim3(a.grid), dim3(kScoreThreads), args, smem, s);
 }
 
-int score_batch_grid(int num_sms, int max_vcount)
+static const void *batch_fn(const ScoreShape &sh)
 {
-    const void *fn = reinterpret_cast<const void *>(&k_score_batch);
+    if (sh.threads == 128)
+        return sh.gpt == 1 ? reinterpret_cast<const void *>(&k_score_batch<1, 128>)
+                           : reinterpret_cast<const void *>(&k_score_batch<2, 128>);
+    return sh.gpt == 1 ? reinterpret_cast<const void *>(&k_score_batch<1, 256>)
+                       : reinterpret_cast<const void *>(&k_score_batch<2, 256>);
+}
+
+int score_batch_grid(int num_sms, int max_vcount, const ScoreShape &sh)
+{
+    const void *fn = batch_fn(sh);
     const size_t smem = (size_t)max_vcount * sizeof(CamRec);
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kScoreThreads, smem) != cudaSuccess || per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, sh.threads, smem) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
+    if (sh.ctas_per_sm > 0 && sh.ctas_per_sm < per_sm) per_sm = sh.ctas_per_sm;
     return num_sms * per_sm;
 }
 
-cudaError_t launch_score_batch(const BatchLaunch &b, int max_vcount, int grid, cudaStream_t s)
+cudaError_t launch_score_batch(const BatchLaunch &b, int max_vcount, int grid, const ScoreShape &sh, cudaStream_t s)
 {
+    const void *fn = batch_fn(sh);
     const size_t smem = (size_t)max_vcount * sizeof(CamRec);
     if (smem > 48 * 1024) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_score_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_score_batch<<<grid, kScoreThreads, smem, s>>>(b);
-    return cudaGetLastError();
+    BatchLaunch arg = b;
+    void *args[] = {&arg};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(sh.threads), args, smem, s);
 }
 
 }  // namespace refine

@@ -107,6 +107,7 @@ size_t elem_size(int dtype) { return dtype == REFINE_BF16 ? 2 : 4; }
 struct refine_queue {
     refine_ctx pc;  // private context of the dispatcher (error text, device, SM count)
     refine_params params{};
+    ScoreShape shape;  // the creating context's tuned shape
     uint64_t budget = 0;
     int slots = 0;
     std::chrono::steady_clock::time_point t0;
@@ -269,7 +270,7 @@ void issue_round(refine_queue *q, std::vector<QJob *> &round)
         j->host_status = issue_prep(q, j);
         if (!j->host_status) live.push_back(j);
     }
-    const long long tile = (long long)kScoreThreads * kScoreGPT;
+    const long long tile = batch_tile(q->shape);
     refine_status st = REFINE_OK;
     if (!live.empty()) {
         int max_v = 0;
@@ -298,9 +299,9 @@ void issue_round(refine_queue *q, std::vector<QJob *> &round)
             bl.total_tiles = R.h_tb[k];
             bl.counter = R.d_counter;
             bl.status = R.d_status;
-            int grid = score_batch_grid(q->pc.num_sms, max_v);
+            int grid = score_batch_grid(q->pc.num_sms, max_v, q->shape);
             if (grid > bl.total_tiles) grid = (int)bl.total_tiles;
-            e = launch_score_batch(bl, max_v, grid, m);
+            e = launch_score_batch(bl, max_v, grid, q->shape, m);
             if (e == cudaSuccess) q->launches.fetch_add(1, std::memory_order_relaxed);
         }
         if (e == cudaSuccess) e = cudaEventRecord(R.scored, m);
@@ -499,6 +500,7 @@ refine_status refine_queue_create(refine_ctx *c, uint64_t hbm_budget_bytes, int3
     refine_queue *q = new refine_queue();
     q->pc.device = c->device;
     q->pc.num_sms = c->num_sms;
+    q->shape = c->shape;
     q->params = p;
     q->budget = hbm_budget_bytes;
     q->slots = max_slots;

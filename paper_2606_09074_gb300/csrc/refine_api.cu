@@ -300,6 +300,7 @@ struct refine_batch {
     long long total_tiles = 0;
     int max_v = 0;
     int grid = 1;
+    ScoreShape shape;
     cudaStream_t main = nullptr;
     std::vector<cudaStream_t> lanes;
     std::vector<cudaEvent_t> events;  // fork, join[lanes], fork2, join2[lanes]
@@ -347,7 +348,7 @@ refine_status batch_record(refine_batch *b)
         bl.total_tiles = b->total_tiles;
         bl.counter = b->d_counter;
         bl.status = c->d_status;
-        e = launch_score_batch(bl, b->max_v, b->grid, m);
+        e = launch_score_batch(bl, b->max_v, b->grid, b->shape, m);
         if (e == cudaSuccess) ++launches;
     }
     if (e == cudaSuccess && !st) e = cudaEventRecord(fork2, m);
@@ -459,7 +460,8 @@ refine_status refine_batch_create(refine_ctx *c, const refine_job *jobs, int32_t
     b->d_counter = cv.take<unsigned long long>(1);
     std::vector<ScoreLaunch> hl(S);
     std::vector<long long> tb(S + 1, 0);
-    const long long tile = (long long)kScoreThreads * kScoreGPT;
+    b->shape = c->shape;
+    const long long tile = batch_tile(b->shape);
     for (int j = 0; j < S; ++j) {
         b->sx.push_back(carve_scene(cv, b->plans[j]));
         b->sel_scr.push_back(cv.take<char>(select_bytes(jobs[j].scene.n)));
@@ -473,7 +475,7 @@ refine_status refine_batch_create(refine_ctx *c, const refine_job *jobs, int32_t
     b->total_tiles = tb[S];
     e = cudaMemcpy(b->d_launch, hl.data(), sizeof(ScoreLaunch) * S, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_tile_begin, tb.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice);
-    b->grid = score_batch_grid(c->num_sms, b->max_v);
+    b->grid = score_batch_grid(c->num_sms, b->max_v, b->shape);
     if (b->grid > b->total_tiles) b->grid = (int)b->total_tiles;
     const int L = std::min(8, S);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking);
@@ -539,6 +541,127 @@ void refine_batch_destroy(refine_batch *b)
     cudaSetDevice(b->ctx->device);
     cudaDeviceSynchronize();
     batch_free(b);
+}
+
+}  // extern "C"
+
+// ============================================================ autotuner
+namespace refine_api {
+
+refine_shape shape_to_abi(const ScoreShape &sh, double ms)
+{
+    refine_shape r{};
+    r.tile = 32 * sh.gpt;
+    r.cta_threads = sh.threads;
+    r.ctas_per_sm = sh.ctas_per_sm;
+    r.ms = ms;
+    return r;
+}
+
+bool shape_from_abi(const refine_shape &r, ScoreShape *sh)
+{
+    if ((r.tile != 32 && r.tile != 64) || (r.cta_threads != 128 && r.cta_threads != 256) || r.ctas_per_sm < 0)
+        return false;
+    sh->gpt = r.tile / 32;
+    sh->threads = r.cta_threads;
+    sh->ctas_per_sm = r.ctas_per_sm;
+    return true;
+}
+
+}  // namespace refine_api
+
+extern "C" {
+
+refine_status refine_ctx_get_shape(const refine_ctx *c, refine_shape *out)
+{
+    if (!c || !out) return REFINE_EINVAL;
+    *out = shape_to_abi(c->shape, 0.0);
+    return REFINE_OK;
+}
+
+refine_status refine_ctx_set_shape(refine_ctx *c, const refine_shape *shape)
+{
+    if (!c || !shape) return REFINE_EINVAL;
+    ScoreShape sh;
+    if (!shape_from_abi(*shape, &sh)) return fail(c, REFINE_EINVAL, "shape: tile 32|64, cta_threads 128|256");
+    c->shape = sh;
+    return REFINE_OK;
+}
+
+refine_status refine_autotune(refine_ctx *c, const refine_job *jobs, int32_t n_jobs, const refine_params *params,
+                              int32_t reps, refine_shape *best_out, refine_shape *table_out, int32_t table_cap,
+                              int32_t *table_count)
+{
+    if (!c) return REFINE_EINVAL;
+    if (reps < 1) return fail(c, REFINE_EINVAL, "autotune: reps must be >= 1");
+    refine_batch *b = nullptr;
+    refine_status st = refine_batch_create(c, jobs, n_jobs, params, &b);
+    if (st) return st;
+    cudaStream_t m = b->main;
+    auto run = [c](int cls, auto &&f) -> refine_status {
+        const cudaError_t e = f();
+        return e == cudaSuccess ? REFINE_OK : cuda_fail(c, e, kClassName[cls]);
+    };
+    const int S = (int)b->jobs.size();
+    for (int j = 0; j < S && !st; ++j)
+        st = enqueue_prep(c, run, &b->jobs[j].scene, b->jobs[j].cams_dev, b->plans[j], b->sx[j], b->params, false,
+                          c->d_status, m);
+    std::vector<ScoreShape> cand;
+    for (int gpt : {2, 1})
+        for (int threads : {256, 128})
+            for (int cap : {0, threads == 256 ? 2 : 4}) {
+                ScoreShape sh;
+                sh.gpt = gpt;
+                sh.threads = threads;
+                sh.ctas_per_sm = cap;
+                cand.push_back(sh);
+            }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    std::vector<double> ms(cand.size(), 0.0);
+    std::vector<long long> tb(S + 1, 0);
+    for (size_t k = 0; k < cand.size() && e == cudaSuccess && !st; ++k) {
+        const ScoreShape &sh = cand[k];
+        const long long tile = batch_tile(sh);
+        for (int j = 0; j < S; ++j) tb[j + 1] = tb[j] + (b->jobs[j].scene.n + tile - 1) / tile;
+        e = cudaMemcpyAsync(b->d_tile_begin, tb.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice, m);
+        BatchLaunch bl;
+        bl.scenes = b->d_launch;
+        bl.tile_begin = b->d_tile_begin;
+        bl.n_scenes = S;
+        bl.total_tiles = tb[S];
+        bl.counter = b->d_counter;
+        bl.status = c->d_status;
+        int grid = score_batch_grid(c->num_sms, b->max_v, sh);
+        if (grid > bl.total_tiles) grid = (int)bl.total_tiles;
+        for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+            if (r == 0) e = cudaEventRecord(e0, m);
+            if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), m);
+            if (e == cudaSuccess) e = launch_score_batch(bl, b->max_v, grid, sh, m);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, m);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        ms[k] = (double)t / reps;
+    }
+    if (e != cudaSuccess && !st) st = cuda_fail(c, e, "autotune");
+    if (!st) st = read_status(c, m);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (!st) {
+        size_t best = 0;
+        for (size_t k = 1; k < cand.size(); ++k)
+            if (ms[k] < ms[best]) best = k;
+        c->shape = cand[best];
+        if (best_out) *best_out = shape_to_abi(cand[best], ms[best]);
+        if (table_out)
+            for (size_t k = 0; k < cand.size() && (int)k < table_cap; ++k) table_out[k] = shape_to_abi(cand[k], ms[k]);
+        if (table_count) *table_count = (int32_t)cand.size();
+    }
+    refine_batch_destroy(b);
+    return st;
 }
 
 }  // extern "C"

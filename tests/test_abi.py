@@ -50,6 +50,7 @@ int main(void) {
   printf("%zu %zu %zu\\n", sizeof(refine_request), sizeof(refine_result), sizeof(refine_queue_stats));
   printf("%zu %zu %zu %zu\\n", offsetof(refine_request, ratio), offsetof(refine_request, kept_idx_host), offsetof(refine_result, threshold), offsetof(refine_result, done_ms));
   printf("%zu %zu\\n", offsetof(refine_queue_stats, max_round), offsetof(refine_queue_stats, kernel_launches));
+  printf("%zu %zu\\n", sizeof(refine_shape), offsetof(refine_shape, ms));
   return 0; }
 ''')
     exe = tmp_path / "layout"
@@ -66,6 +67,7 @@ int main(void) {
     assert got[4] == [b.refine_request.ratio.offset, b.refine_request.kept_idx_host.offset,
                       b.refine_result.threshold.offset, b.refine_result.done_ms.offset]
     assert got[5] == [b.refine_queue_stats.max_round.offset, b.refine_queue_stats.kernel_launches.offset]
+    assert got[6] == [C.sizeof(b.refine_shape), b.refine_shape.ms.offset]
 
 
 def test_camera_dtype_matches_struct():
@@ -88,6 +90,8 @@ def test_params_default_and_errors_without_gpu(lib):
     assert b.refine_queue_submit(None, None, None) == b.REFINE_EINVAL
     assert b.refine_queue_poll(None, 1, None, 0) == b.REFINE_EINVAL
     assert b.refine_queue_stats_get(None, None) == b.REFINE_EINVAL
+    assert b.refine_autotune(None, None, 0, None, 1, None, None, 0, None) == b.REFINE_EINVAL
+    assert b.refine_ctx_get_shape(None, None) == b.REFINE_EINVAL
     b.refine_queue_destroy(None)
 
 

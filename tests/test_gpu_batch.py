@@ -97,3 +97,40 @@ def test_batch_mixed_storage_and_flags(env):
         m, thr, nk = ctx.select(s, 0.5)
         assert torch.equal(batch.outputs[k]["scores"], s)
         assert nk_b[k] == nk and thr_b[k] == thr
+
+
+def test_every_shape_gives_the_same_scores(env):
+    """The work-item shape (tile 32/64, CTA 128/256 threads, CTAs per SM)
+    changes speed only: plain and batched scores are bit-identical for every
+    shape, and the autotuner reports every candidate and keeps the fastest."""
+    torch, rb, ctx = env
+    ws = [synth.random_scene(seed=51, n=20_000, v=30, means="core_shell"),
+          synth.random_scene(seed=52, n=4_097, v=5, means="core_shell")]
+    ws[1].scene = ws[1].scene.to_bf16()
+    up = [upload(torch, rb, w) for w in ws]
+    jobs = [{"pos": p, "attr": a, "cams": c, "ratio": 0.5} for (p, a, c) in up]
+    default = ctx.get_shape()
+    ref = [ctx.score(p, a, c) for (p, a, c) in up]
+    try:
+        for tile in (32, 64):
+            for cta in (128, 256):
+                for cap in (0, 2):
+                    ctx.set_shape(tile, cta, cap)
+                    for k, (p, a, c) in enumerate(up):
+                        assert torch.equal(ctx.score(p, a, c), ref[k]), (tile, cta, cap, k)
+                    batch = rb.Batch(ctx, jobs, compact=False)
+                    batch.run()
+                    batch.results()
+                    for k in range(len(up)):
+                        assert torch.equal(batch.outputs[k]["scores"], ref[k]), (tile, cta, cap, k)
+                    batch.close()
+        best, table = ctx.autotune(jobs, reps=1)
+        assert len(table) == 8 and all(t["ms"] > 0 for t in table)
+        assert best["ms"] == min(t["ms"] for t in table)
+        got = ctx.get_shape()
+        assert (got["tile"], got["cta_threads"], got["ctas_per_sm"]) == (best["tile"], best["cta_threads"],
+                                                                           best["ctas_per_sm"])
+        with pytest.raises(rb.RefineError):
+            ctx.set_shape(48, 256, 0)
+    finally:
+        ctx.set_shape(default["tile"], default["cta_threads"], default["ctas_per_sm"])
