@@ -245,6 +245,7 @@ struct SceneScratch {
     unsigned *bsum;
     uint32_t *perm;
     unsigned long long *need;
+    unsigned long long *tiles;  // k_score's tile counter
     float *running;
 };
 
@@ -266,7 +267,8 @@ inline size_t scene_bytes(const ScenePlan &pl)
                        sizeof(SceneConsts), sizeof(SceneStats), sizeof(uint32_t) * n,
                        sizeof(unsigned) * (cells + 64), sizeof(unsigned) * cells,
                        sizeof(unsigned) * (cells / kScanThreads), sizeof(uint32_t) * n,
-                       kCountSlots * sizeof(unsigned long long), pl.multipass ? sizeof(float) * n : 0});
+                       kCountSlots * sizeof(unsigned long long), sizeof(unsigned long long),
+                       pl.multipass ? sizeof(float) * n : 0});
 }
 
 inline SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
@@ -285,6 +287,7 @@ inline SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
     x.bsum = cv.take<unsigned>(cells / kScanThreads);
     x.perm = cv.take<uint32_t>(n);
     x.need = cv.take<unsigned long long>(kCountSlots);
+    x.tiles = cv.take<unsigned long long>(1);
     x.running = pl.multipass ? cv.take<float>(n) : nullptr;
     return x;
 }
@@ -340,6 +343,7 @@ inline ScoreLaunch make_score_launch(const refine_scene *sc, const ScenePlan &pl
     a.scores = scores;
     a.view_sum = view_sum;
     a.need = count ? x.need : nullptr;
+    a.tiles_taken = nullptr;
     a.status = status;
     a.grid = 0;
     return a;
@@ -376,6 +380,9 @@ inline refine_status score_impl(refine_ctx *c, const refine_scene *sc, const ref
     for (int v0 = 0; v0 < V; v0 += kViewsPerPass) {
         ScoreLaunch a = make_score_launch(sc, pl, x, p, v0, scores, view_sum, need_dev != nullptr, c->d_status);
         a.grid = score_grid(c->num_sms, pl.n, a.vcount, c->shape);
+        a.tiles_taken = x.tiles;
+        const cudaError_t e = cudaMemsetAsync(x.tiles, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
         if ((st = launch(c, K_SCORE, s, [&] { return launch_score(a, c->shape, s); }))) return st;
     }
     return REFINE_OK;

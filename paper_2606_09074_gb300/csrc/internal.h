@@ -84,6 +84,8 @@ struct ScoreLaunch {
     float *scores;
     float *view_sum;            // optional
     unsigned long long *need;   // optional diagnostic counters (kCountSlots), see k_score
+    unsigned long long *tiles_taken;  // k_score: tile counter (zero before the launch) for dynamic
+                                      // scheduling; NULL = static grid-stride order
     int *status;
     int grid;                   // CTAs (persistent)
 };

@@ -767,8 +767,27 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
     for (int k = 0; k < kCountSlots; ++k) cnt[k] = 0;
     const SceneConsts sc = *a.consts;
     const int64_t tile = (int64_t)blockDim.x * GPT;
-    for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile)
-        score_tile<NOPROJ, COUNT, GPT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
+    if (a.tiles_taken) {
+        // Tiles are taken from a counter, one ahead (its records are pulled
+        // towards L2 while the current tile is scored), so CTAs that draw
+        // cheap tiles take more of them.
+        __shared__ long long s_next;
+        const long long ntiles = (long long)((a.n + tile - 1) / tile);
+        if (threadIdx.x == 0) s_next = (long long)atomicAdd(a.tiles_taken, 1ull);
+        __syncthreads();
+        long long cur = s_next;
+        while (cur < ntiles) {
+            __syncthreads();  // every thread has read s_next
+            if (threadIdx.x == 0) s_next = (long long)atomicAdd(a.tiles_taken, 1ull);
+            __syncthreads();
+            const long long nxt = s_next;
+            score_tile<NOPROJ, COUNT, GPT>(a, cs, sc, cur * tile, nxt < ntiles ? nxt * tile : -1, cnt);
+            cur = nxt;
+        }
+    } else {
+        for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile)
+            score_tile<NOPROJ, COUNT, GPT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
+    }
     if (COUNT) {
         const int lane = threadIdx.x & 31;
 #pragma unroll
