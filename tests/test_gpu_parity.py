@@ -314,3 +314,31 @@ def test_core_shell_3p5m_sampled(torch, rb, ctx):
     np.testing.assert_allclose(st["lambda"], ref["stats"]["lambda"], rtol=1e-6)
     mask, _, nk = check_select_exact(torch, ctx, s, 0.5)
     check_compact_exact(torch, ctx, w.scene, pos, attr, mask, nk)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_padded_row_stride(torch, rb, ctx, dtype):
+    """Rows of a scene may be longer than n (row_stride > n): scores,
+    selection and compaction equal those of the tightly packed scene."""
+    w = synth.random_scene(seed=77, n=12_345, v=20, means="core_shell")
+    sc = w.scene.to_bf16() if dtype == "bf16" else w.scene
+    dev = torch.device("cuda", 0)
+    n, pad = sc.n, 45
+    cams = rb.cameras_to_device(w.cams, dev)
+    pos = torch.from_numpy(sc.pos).to(dev)
+    if dtype == "bf16":
+        attr = torch.from_numpy(sc.attr.view(np.int16)).to(dev).view(torch.bfloat16)
+    else:
+        attr = torch.from_numpy(sc.attr).to(dev)
+    pos_p = torch.zeros((3, n + pad), dtype=pos.dtype, device=dev)
+    attr_p = torch.zeros((56, n + pad), dtype=attr.dtype, device=dev)
+    pos_p[:, :n] = pos
+    attr_p[:, :n] = attr
+    pos_v, attr_v = pos_p[:, :n], attr_p[:, :n]
+    s0 = ctx.score(pos, attr, cams)
+    s1 = ctx.score(pos_v, attr_v, cams)
+    assert torch.equal(s0, s1)
+    m0, thr0, nk = ctx.select(s0, 0.5)
+    op0, oa0, i0 = ctx.compact(pos, attr, m0, nk)
+    op1, oa1, i1 = ctx.compact(pos_v, attr_v, m0, nk)
+    assert torch.equal(i0, i1) and torch.equal(op0, op1) and torch.equal(oa0, oa1)
