@@ -137,25 +137,21 @@ cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64
 
 // Eq. (features) -> Eq. 18 -> Eq. 19 in double, one block; also the grid box
 // (mean +- 3 sigma of the means) of the processing order.
-__global__ void k_features_finalize(const double *__restrict__ partials, int nblocks, int64_t n,
-                                    refine_params p, int cell_bits, SceneConsts *consts, SceneStats *stats)
+__global__ void __launch_bounds__(32 * kFeatSums) k_features_finalize(const double *__restrict__ partials,
+                                                                      int nblocks, int64_t n, refine_params p,
+                                                                      int cell_bits, SceneConsts *consts,
+                                                                      SceneStats *stats)
 {
-    __shared__ double red[kFeatSums][256];
-    double loc[kFeatSums];
+    // warp k reduces sum k over the block partials in a fixed order
+    __shared__ double red[kFeatSums][1];
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double v = 0.0;
+#pragma unroll 4
+    for (int b = lane; b < nblocks; b += 32) v += partials[(int64_t)b * kFeatSums + k];
 #pragma unroll
-    for (int k = 0; k < kFeatSums; ++k) loc[k] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < kFeatSums; ++k) loc[k] += partials[(int64_t)b * kFeatSums + k];
-#pragma unroll
-    for (int k = 0; k < kFeatSums; ++k) red[k][threadIdx.x] = loc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[k][0] = v;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-#pragma unroll
-            for (int k = 0; k < kFeatSums; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
-        __syncthreads();
-    }
     if (threadIdx.x != 0) return;
     const double N = (double)n;
     SceneStats st;
@@ -194,7 +190,7 @@ cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_
                                      const refine_params *p, int cell_bits, SceneConsts *consts,
                                      SceneStats *stats, cudaStream_t s)
 {
-    k_features_finalize<<<1, 256, 0, s>>>(partials, nblocks, n, *p, cell_bits, consts, stats);
+    k_features_finalize<<<1, 32 * kFeatSums, 0, s>>>(partials, nblocks, n, *p, cell_bits, consts, stats);
     return cudaGetLastError();
 }
 
