@@ -250,9 +250,13 @@ def run_ours(args, rank: int, world: int):
     kept = torch.empty(n_keep, dtype=torch.int32, device=dev)
     ctx = rb.Context(local)
     stream = torch.cuda.current_stream(dev)
+    params = rb.default_params(max_views=args.max_views) if args.max_views else None
+    V_all = V
+    if args.max_views and V > args.max_views:
+        V = -(-V // -(-V // args.max_views))  # views scored: every ceil(V / max_views)-th
 
     def step():
-        ctx.score(pos, attr, cams, scores=scores, stream=stream)
+        ctx.score(pos, attr, cams, scores=scores, params=params, stream=stream)
         ctx.select(scores, ratio, mask=mask, threshold=False, stream=stream)
         ctx.compact(pos, attr, mask, n_keep, out_pos=out_pos, out_attr=out_attr, kept_idx=True,
                     out_row_stride=n_keep, stream=stream)
@@ -319,14 +323,14 @@ def run_ours(args, rank: int, world: int):
                     "out_attr": torch.empty((56, n_keep), dtype=attr.dtype, pin_memory=True),
                     "idx": torch.empty(n_keep, dtype=torch.int32, pin_memory=True)}
             for _ in range(2):
-                ctx.prune_host(pos_h, attr_h, w.cams, ratio, out=outs, stream=stream)
+                ctx.prune_host(pos_h, attr_h, w.cams, ratio, params=params, out=outs, stream=stream)
             k_e2e = max(3, min(args.steps, 60))
             t0 = time.perf_counter()
             for _ in range(k_e2e):
-                ctx.prune_host(pos_h, attr_h, w.cams, ratio, out=outs, stream=stream)
+                ctx.prune_host(pos_h, attr_h, w.cams, ratio, params=params, out=outs, stream=stream)
             dt = (time.perf_counter() - t0) / k_e2e
             asz = attr.element_size() * 56
-            e2e = {"value": pairs / dt, "unit": "pairs/s", "h2d_bytes_per_step": 12 * n + asz * n + 80 * V,
+            e2e = {"value": pairs / dt, "unit": "pairs/s", "h2d_bytes_per_step": 12 * n + asz * n + 80 * V_all,
                    "d2h_bytes_per_step": (12 + asz + 4) * n_keep + 4 + 4, "ms_per_step": dt * 1000,
                    "steps": k_e2e, "api": "refine_prune_host (pinned host buffers)"}
         cpu = None
@@ -351,6 +355,14 @@ def run_ours(args, rank: int, world: int):
                 "clocks": clock_summary, "gpu": props.name}
         if acc is not None:
             line["accuracy"] = acc
+        if params is not None:
+            # keep masks of the subsampled and of the all-view scoring
+            s_all = ctx.score(pos, attr, cams, stream=stream)
+            m_all, _, _ = ctx.select(s_all, ratio, stream=stream)
+            a = np.unpackbits(mask.cpu().numpy().view(np.uint8), bitorder="little")[:n]
+            b = np.unpackbits(m_all.cpu().numpy().view(np.uint8), bitorder="little")[:n]
+            line["view_subsampling"] = {"max_views": args.max_views, "views_scored": V, "views_total": V_all,
+                                        "mask_agreement_vs_all_views": float((a == b).mean())}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -682,6 +694,8 @@ def main(argv=None):
                          "serve: the request queue under Poisson and back-to-back arrivals")
     ap.add_argument("--scenes", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--max-views", type=int, default=0,
+                    help="score every ceil(V/max_views)-th view (Table B.1 subsampling); 0 = all")
     ap.add_argument("--jobs", type=int, default=300, help="serve: Poisson jobs")
     ap.add_argument("--sat-jobs", type=int, default=200, help="serve: back-to-back jobs")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")

@@ -57,6 +57,10 @@ enum { REFINE_F32 = 0, REFINE_BF16 = 1 };
 #define REFINE_FLAG_NO_PROJ      (1 << 1) /* Table 3 "w/o P": 1/(z^2+eta) -> 1 in Eq. 20    */
 #define REFINE_FLAG_EQUAL_LAMBDA (1 << 2) /* Table 3 "Equal lambda^k": lambda^k = 1/3       */
 #define REFINE_FLAG_NORM_ATTR    (1 << 3) /* G~^k = m^k / mean_j(m^k_j) (default on)        */
+#define REFINE_FLAG_FULL_JACOBIAN (1 << 4) /* projection term of Eq. 14 before the Eq. 16 *
+                                            * simplification: Tr(J^T J) = (fx^2+fy^2)/z^2 *
+                                            * + ((fx x)^2+(fy y)^2)/z^4 instead of        *
+                                            * 1/(z^2+eta); NO_PROJ takes precedence       */
 
 /* Defaults.  eta is the paper's stability constant (Eq. 17, Sec. 3.2).  The
  * paper calibrates lambda~ by expectations E[.] (Eq. 18) without printing
@@ -109,7 +113,10 @@ typedef struct refine_params {
     double e_col;     /* Eq. 18 calibration E[F_col]    (nonzero)                      */
     double e_opa;     /* Eq. 18 calibration E[F_opa]    (nonzero)                      */
     int32_t flags;    /* REFINE_FLAG_*                                                 */
-    int32_t reserved;
+    int32_t max_views; /* view subsampling (Table B.1 scores 64 views): with          *
+                        * 0 < max_views < n_views, views 0, s, 2s, ... are scored,    *
+                        * s = ceil(n_views / max_views), and |V| in Eq. 20 is their   *
+                        * count; 0 = every view (default)                             */
 } refine_params;
 
 /* Scene statistics computed on the device (Eq. (features), Eq. 18-19). */
@@ -242,7 +249,7 @@ refine_status refine_prune_host(refine_ctx *ctx, int64_t n, int32_t dtype,
 typedef struct refine_job {
     refine_scene scene;            /* primitives (see refine_scene)                      */
     const refine_camera *cams_dev; /* n_views camera records                             */
-    int32_t n_views;               /* 1 .. 512 in a batch                                */
+    int32_t n_views;               /* >= 1; at most 512 scored (see max_views)           */
     int32_t reserved;
     double ratio;                  /* pruning ratio in [0, 1)                             */
     float *scores_dev;             /* [n] written                                         */
@@ -340,7 +347,7 @@ typedef struct refine_queue refine_queue;
 typedef struct refine_request {
     int64_t n;                       /* primitives, 1 .. 2^31 - 1                           */
     int32_t dtype;                   /* REFINE_F32 or REFINE_BF16 (attribute rows)          */
-    int32_t n_views;                 /* 1 .. 512                                           */
+    int32_t n_views;                 /* 1 .. 65535, at most 512 scored (see max_views)     */
     const float *pos_host;           /* [3][n] float32 means                               */
     const void *attr_host;           /* [56][n] in dtype, rows as in refine_scene          */
     const refine_camera *cams_host;  /* [n_views]                                          */
@@ -433,6 +440,29 @@ refine_status refine_select_noalloc(const float *scores_dev, int64_t n, double r
                                     uint32_t *keep_mask_dev, float *threshold_out,
                                     int64_t *n_keep_out, char *errbuf, size_t errlen,
                                     refine_stream_t stream);
+
+/* ------------------------------------------------------------ scene files
+ * Host-side I/O of scenes in the PLY layout of 3D Gaussian Splatting
+ * checkpoints, the format in which a pruned scene is saved ("saving
+ * primitives", Sec. 4.2): binary little-endian, one float32 vertex per
+ * primitive with properties x y z nx ny nz f_dc_0-2 f_rest_0-44 opacity
+ * scale_0-2 rot_0-3 (log-scales, quaternion w x y z, opacity logit, f_rest
+ * channel-major).  Rows map to refine_scene rows one to one (normals are
+ * written as 0 and ignored on reading). */
+
+/* Writes n primitives from host rows pos_host [3][row_stride] (float32) and
+ * attr_host [56][row_stride] (dtype; bfloat16 is widened exactly).  EINVAL
+ * for bad arguments or a file that cannot be written. */
+refine_status refine_write_ply(const char *path, int64_t n, int32_t dtype, const float *pos_host,
+                               const void *attr_host, int64_t row_stride);
+
+/* Reads a scene PLY.  With pos_host and attr_host NULL only *n_out is set;
+ * otherwise the rows are written to pos_host [3][row_stride] and attr_host
+ * [56][row_stride], both float32, row_stride >= n.  Properties are matched by
+ * name, in any order, extra ones ignored.  EINVAL for a file that is not
+ * binary little-endian with one float32 vertex element holding them all. */
+refine_status refine_read_ply(const char *path, int64_t *n_out, float *pos_host, float *attr_host,
+                              int64_t row_stride);
 
 /* Synchronises `stream` and returns (then clears) the device status word:
  * REFINE_OK, or the first error a kernel recorded since the last check. */

@@ -26,6 +26,7 @@ NO_VIS = 1 << 0
 NO_PROJ = 1 << 1
 EQUAL_LAMBDA = 1 << 2
 NORM_ATTR = 1 << 3
+FULL_JACOBIAN = 1 << 4
 
 # Calibration constants of Eq. 18 (E[ln F_gem], E[F_col], E[F_opa]); see
 # ``calibrate.py`` for how they were produced.

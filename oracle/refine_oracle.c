@@ -45,6 +45,7 @@
 #define ORC_NO_PROJ       (1 << 1)  /* Table 3 "w/o P": P -> 1 in Eq. 20     */
 #define ORC_EQUAL_LAMBDA  (1 << 2)  /* Table 3 "Equal lambda^k"             */
 #define ORC_NORM_ATTR     (1 << 3)  /* R1: G~^k = m^k / mean(m^k)           */
+#define ORC_FULL_JAC      (1 << 4)  /* Eq. 14 before Eq. 16: P = Tr(J^T J)  */
 
 /* Relative width of the band inside which a float32 evaluation of a
  * visibility decision may differ from this FP64 one (64 float32 ulps). */
@@ -304,7 +305,17 @@ void orc_score_subset(const double *g, int64_t stride, int64_t n, const int64_t 
             int vis = orc_visible(&cams[v], mu, Sigma, &border);
             double tc[3];
             orc_to_camera(&cams[v], mu, tc);
-            double P = (p->flags & ORC_NO_PROJ) ? 1.0 : 1.0 / (tc[2] * tc[2] + p->eta); /* Eq. 17 */
+            double P;
+            if (p->flags & ORC_NO_PROJ) {
+                P = 1.0;
+            } else if (p->flags & ORC_FULL_JAC) {                       /* Eq. 14: ||J_Pi||_F^2 */
+                double J[6];
+                orc_projection_jacobian(&cams[v], tc, J);
+                P = 0.0;
+                for (int k = 0; k < 6; ++k) P += J[k] * J[k];
+            } else {
+                P = 1.0 / (tc[2] * tc[2] + p->eta);                        /* Eq. 17 */
+            }
             if (vis) sum += P;
             if (border) {
                 if (bterms && nb < 4) bterms[4 * o + nb] = P;

@@ -39,6 +39,7 @@ FLAG_NO_VIS = 1 << 0
 FLAG_NO_PROJ = 1 << 1
 FLAG_EQUAL_LAMBDA = 1 << 2
 FLAG_NORM_ATTR = 1 << 3
+FLAG_FULL_JACOBIAN = 1 << 4
 
 
 class RefineError(RuntimeError):
@@ -61,7 +62,7 @@ class refine_scene(C.Structure):
 class refine_params(C.Structure):
     _fields_ = [("eta", C.c_float), ("luma", C.c_float * 3), ("e_ln_gem", C.c_double),
                 ("e_col", C.c_double), ("e_opa", C.c_double), ("flags", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("max_views", C.c_int32)]
 
 
 class refine_scene_stats(C.Structure):
@@ -155,6 +156,8 @@ _SIGNATURES = {
     "refine_queue_stats_get": (C.c_int, [_P, C.POINTER(refine_queue_stats)]),
     "refine_queue_destroy": (None, [_P]),
     "refine_queue_last_error": (C.c_char_p, [_P]),
+    "refine_write_ply": (C.c_int, [C.c_char_p, C.c_int64, C.c_int32, _P, _P, C.c_int64]),
+    "refine_read_ply": (C.c_int, [C.c_char_p, C.POINTER(C.c_int64), _P, _P, C.c_int64]),
     "refine_ctx_check": (C.c_int, [_P, _P]),
     "refine_ctx_set_timing": (C.c_int, [_P, C.c_int]),
     "refine_ctx_kernel_times": (C.c_int, [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
@@ -602,3 +605,31 @@ class Queue:
             self.close()
         except Exception:
             pass
+
+
+def write_ply(path: str, pos, attr) -> None:
+    """Writes host rows pos [3, n] float32 and attr [56, n] (float32 or
+    bfloat16 bits as uint16) as a 3DGS scene PLY (refine_write_ply)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    attr = np.ascontiguousarray(attr)
+    dt = REFINE_F32 if attr.dtype == np.float32 else REFINE_BF16
+    if dt == REFINE_BF16 and attr.dtype not in (np.uint16, np.int16):
+        raise TypeError("attr must be float32 or bfloat16 bits (uint16)")
+    n = pos.shape[1]
+    rc = refine_write_ply(os.fsencode(path), n, dt, pos.ctypes.data, attr.ctypes.data, n)  # noqa: F821
+    if rc != REFINE_OK:
+        raise RefineError(rc, f"refine_write_ply: cannot write {path}")
+
+
+def read_ply(path: str):
+    """Reads a 3DGS scene PLY into (pos [3, n], attr [56, n]) float32."""
+    n = C.c_int64()
+    rc = refine_read_ply(os.fsencode(path), C.byref(n), None, None, 0)  # noqa: F821
+    if rc != REFINE_OK:
+        raise RefineError(rc, f"refine_read_ply: {path} is not a scene PLY")
+    pos = np.empty((3, n.value), dtype=np.float32)
+    attr = np.empty((56, n.value), dtype=np.float32)
+    rc = refine_read_ply(os.fsencode(path), C.byref(n), pos.ctypes.data, attr.ctypes.data, n.value)  # noqa: F821
+    if rc != REFINE_OK:
+        raise RefineError(rc, f"refine_read_ply: {path}")
+    return pos, attr

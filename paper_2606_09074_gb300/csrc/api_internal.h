@@ -189,6 +189,7 @@ inline refine_status check_params(refine_ctx *c, const refine_params *p)
     if (!(isfinite(p->e_ln_gem) && p->e_ln_gem != 0.0 && isfinite(p->e_col) && p->e_col != 0.0 &&
           isfinite(p->e_opa) && p->e_opa != 0.0))
         return fail(c, REFINE_EINVAL, "params: calibration constants must be finite and nonzero");
+    if (p->max_views < 0) return fail(c, REFINE_EINVAL, "params: max_views must be >= 0");
     return REFINE_OK;
 }
 
@@ -227,7 +228,8 @@ inline refine_status read_status(refine_ctx *c, cudaStream_t s)
 // Scratch layout of one scene's score pass.
 struct ScenePlan {
     int64_t n = 0;
-    int V = 0;
+    int V = 0;        // views scored
+    int vstride = 1;  // input camera stride (view subsampling)
     bool multipass = false;
     int nb = 1;    // feature-pass blocks
     int bits = 4;  // processing-order grid resolution
@@ -249,12 +251,15 @@ struct SceneScratch {
     float *running;
 };
 
-inline ScenePlan plan_scene(int64_t n, int V)
+// V input cameras; with 0 < max_views < V every s-th view is scored,
+// s = ceil(V / max_views) (Table B.1's view subsampling).
+inline ScenePlan plan_scene(int64_t n, int V, int max_views = 0)
 {
     ScenePlan pl;
     pl.n = n;
-    pl.V = V;
-    pl.multipass = V > kViewsPerPass;
+    pl.vstride = (max_views > 0 && V > max_views) ? (V + max_views - 1) / max_views : 1;
+    pl.V = (V + pl.vstride - 1) / pl.vstride;
+    pl.multipass = pl.V > kViewsPerPass;
     pl.nb = feature_blocks(pl.n);
     pl.bits = cell_bits_for(pl.n);
     return pl;
@@ -304,7 +309,8 @@ inline refine_status enqueue_prep(refine_ctx *c, L &&run, const refine_scene *sc
     if (e == cudaSuccess && count) e = cudaMemsetAsync(x.need, 0, kCountSlots * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
     refine_status st;
-    if ((st = run(K_CAM_PREP, [&] { return launch_cam_prep(cams, pl.V, x.cams, status, s); }))) return st;
+    if ((st = run(K_CAM_PREP, [&] { return launch_cam_prep(cams, pl.V, pl.vstride, x.cams, status, s); })))
+        return st;
     if ((st = run(K_FEATURES, [&] {
              return launch_features(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, x.recs,
                                     x.partials, status, s);
@@ -369,7 +375,7 @@ inline refine_status score_impl(refine_ctx *c, const refine_scene *sc, const ref
     if (pin) p = *pin; else refine_params_default(&p);
     refine_status st = check_score_args(c, sc, cams, V, p, scores);
     if (st || sc->n == 0) return st;
-    const ScenePlan pl = plan_scene(sc->n, V);
+    const ScenePlan pl = plan_scene(sc->n, V, p.max_views);
     if ((st = ensure(c, c->score, scene_bytes(pl)))) return st;
     Carver cv(c->score.p);
     const SceneScratch x = carve_scene(cv, pl);
@@ -377,7 +383,7 @@ inline refine_status score_impl(refine_ctx *c, const refine_scene *sc, const ref
     if (need_dev) *need_dev = x.need;
     auto run = [&](int cls, auto &&f) { return launch(c, cls, s, f); };
     if ((st = enqueue_prep(c, run, sc, cams, pl, x, p, need_dev != nullptr, c->d_status, s))) return st;
-    for (int v0 = 0; v0 < V; v0 += kViewsPerPass) {
+    for (int v0 = 0; v0 < pl.V; v0 += kViewsPerPass) {
         ScoreLaunch a = make_score_launch(sc, pl, x, p, v0, scores, view_sum, need_dev != nullptr, c->d_status);
         a.grid = score_grid(c->num_sms, pl.n, a.vcount, c->shape);
         a.tiles_taken = x.tiles;

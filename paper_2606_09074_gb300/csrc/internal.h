@@ -90,7 +90,8 @@ struct ScoreLaunch {
     int grid;                   // CTAs (persistent)
 };
 
-cudaError_t launch_cam_prep(const refine_camera *cams, int V, CamRec *out, int *status,
+// Camera records of views 0, vstride, 2 vstride, ... (V of them).
+cudaError_t launch_cam_prep(const refine_camera *cams, int V, int vstride, CamRec *out, int *status,
                             cudaStream_t s);
 int feature_blocks(int64_t n);
 cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,

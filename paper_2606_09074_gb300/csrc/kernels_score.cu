@@ -11,12 +11,12 @@ namespace refine {
 // Camera preparation: refine_camera -> CamRec (P = K W and p = K t formed
 // in double and rounded once), with validation.
 // ---------------------------------------------------------------------
-__global__ void k_cam_prep(const refine_camera *__restrict__ cams, int V, CamRec *__restrict__ out,
+__global__ void k_cam_prep(const refine_camera *__restrict__ cams, int V, int vstride, CamRec *__restrict__ out,
                            int *status)
 {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
-    refine_camera c = cams[v];
+    refine_camera c = cams[(int64_t)v * vstride];
     bool ok = isfinite(c.fx) && isfinite(c.fy) && isfinite(c.cx) && isfinite(c.cy) &&
               isfinite(c.znear) && isfinite(c.zfar) && c.fx > 0.f && c.fy > 0.f &&
               c.width >= 1 && c.height >= 1 && c.znear > 0.f && c.zfar > c.znear;
@@ -52,10 +52,10 @@ __global__ void k_cam_prep(const refine_camera *__restrict__ cams, int V, CamRec
     out[v] = r;
 }
 
-cudaError_t launch_cam_prep(const refine_camera *cams, int V, CamRec *out, int *status,
+cudaError_t launch_cam_prep(const refine_camera *cams, int V, int vstride, CamRec *out, int *status,
                             cudaStream_t s)
 {
-    k_cam_prep<<<(V + 127) / 128, 128, 0, s>>>(cams, V, out, status);
+    k_cam_prep<<<(V + 127) / 128, 128, 0, s>>>(cams, V, vstride, out, status);
     return cudaGetLastError();
 }
 
@@ -503,13 +503,34 @@ __device__ __forceinline__ PairGeom pair_geom(const float4 &c0, const float4 &c1
     return r;
 }
 
-template <bool NOPROJ>
-__device__ __forceinline__ float weight(float z, float eta)
+// Projection term of a visible (primitive, view) pair.  PM (projection
+// mode): 0 = Eq. 17, 1/(z^2 + eta); 1 = Table 3 "w/o P", 1; 2 = Eq. 14 before
+// the simplification of Eq. 16, the Jacobian energy Tr(J^T J) = (fx^2 +
+// fy^2)/z^2 + ((fx x)^2 + (fy y)^2)/z^4, with fx x and fy y from the camera's
+// fx R0 and fy R1 rows (the same arithmetic on every path, so the weight does
+// not depend on the tile's classification).
+enum { kProjEq17 = 0, kProjNone = 1, kProjFullJ = 2 };
+
+template <int PM>
+__device__ __forceinline__ float weight(const CamRec &c, float z, float eta, float mx, float my, float mz)
 {
-    return NOPROJ ? 1.f : rcp_approx(fmaf(z, z, eta));
+    if (PM == kProjNone) return 1.f;
+    if (PM == kProjEq17) return rcp_approx(fmaf(z, z, eta));
+    const float4 tx = c.tx, ty = c.ty, k = c.k;
+    const float fxx = fmaf(tx.x, mx, fmaf(tx.y, my, fmaf(tx.z, mz, tx.w)));
+    const float fyy = fmaf(ty.x, mx, fmaf(ty.y, my, fmaf(ty.z, mz, ty.w)));
+    // explicit rounding intrinsics: never contracted into a neighbouring
+    // add, so every path (IN, MIXED, plain, batched) rounds identically
+    const float iz2 = rcp_approx(__fmul_rn(z, z));
+    return __fmul_rn(fmaf(fmaf(fxx, fxx, __fmul_rn(fyy, fyy)), iz2, __fadd_rn(k.x, k.y)), iz2);
 }
 
-template <bool NOPROJ, bool DET, bool COUNT, int GPT>
+__host__ __device__ inline int proj_mode(int flags)
+{
+    return (flags & REFINE_FLAG_NO_PROJ) ? kProjNone : (flags & REFINE_FLAG_FULL_JACOBIAN) ? kProjFullJ : kProjEq17;
+}
+
+template <int PM, bool DET, bool COUNT, int GPT>
 __device__ __forceinline__ void mixed_view(const CamRec &c, float eta, const PairIn (&p)[GPT],
                                            const bool (&valid)[GPT], float (&part)[GPT],
                                            unsigned long long (&cnt)[kCountSlots])
@@ -546,10 +567,11 @@ __device__ __forceinline__ void mixed_view(const CamRec &c, float eta, const Pai
         }
     }
 #pragma unroll
-    for (int g = 0; g < GPT; ++g) part[g] += vis[g] ? weight<NOPROJ>(q[g].z, eta) : 0.f;
+    for (int g = 0; g < GPT; ++g)
+        part[g] += vis[g] ? weight<PM>(c, q[g].z, eta, p[g].mx, p[g].my, p[g].mz) : 0.f;
 }
 
-template <bool NOPROJ, bool DET, bool COUNT, int GPT>
+template <int PM, bool DET, bool COUNT, int GPT>
 __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float eta, const PairIn (&p)[GPT],
                                           const bool (&valid)[GPT], const TileBox &tb,
                                           float (&acc)[GPT], float (&comp)[GPT],
@@ -590,10 +612,10 @@ __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float et
 #pragma unroll
                     for (int g = 0; g < GPT; ++g) {
                         const float z = fmaf(c2.x, p[g].mx, fmaf(c2.y, p[g].my, fmaf(c2.z, p[g].mz, c2.w)));
-                        part[g] += weight<NOPROJ>(z, eta);
+                        part[g] += weight<PM>(c, z, eta, p[g].mx, p[g].my, p[g].mz);
                     }
                 } else {
-                    mixed_view<NOPROJ, DET, COUNT, GPT>(c, eta, p, valid, part, cnt);
+                    mixed_view<PM, DET, COUNT, GPT>(c, eta, p, valid, part, cnt);
                 }
             }
             // Kahan-compensated sum of the 16-view partial sums
@@ -635,7 +657,7 @@ __device__ __forceinline__ void fence_proxy_async_shared()
 // Scores one tile of blockDim.x * GPT primitives of the processing
 // order starting at `base`; `next_base` (or -1) is the tile this CTA takes
 // next, whose primitives are pulled towards L2 meanwhile.
-template <bool NOPROJ, bool COUNT, int GPT>
+template <int PM, bool COUNT, int GPT>
 __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *cs, const SceneConsts &sc,
                                            int64_t base, int64_t next_base, unsigned long long (&cnt)[kCountSlots])
 {
@@ -696,9 +718,9 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
     }
 
     if (__any_sync(0xffffffffu, degen))
-        view_loop<NOPROJ, true, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tb, acc, comp, cnt);
+        view_loop<PM, true, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tb, acc, comp, cnt);
     else
-        view_loop<NOPROJ, false, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tb, acc, comp, cnt);
+        view_loop<PM, false, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tb, acc, comp, cnt);
 
 #pragma unroll
     for (int g = 0; g < GPT; ++g) {
@@ -727,7 +749,7 @@ __device__ __forceinline__ int cams_stageable(const CamRec *cams, int vcount)
            (uint64_t)vcount * sizeof(CamRec) <= (uint64_t)dyn;
 }
 
-template <bool NOPROJ, bool COUNT, int GPT>
+template <int PM, bool COUNT, int GPT>
 __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -777,12 +799,12 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
             if (threadIdx.x == 0) s_next = (long long)atomicAdd(a.tiles_taken, 1ull);
             __syncthreads();
             const long long nxt = s_next;
-            score_tile<NOPROJ, COUNT, GPT>(a, cs, sc, cur * tile, nxt < ntiles ? nxt * tile : -1, cnt);
+            score_tile<PM, COUNT, GPT>(a, cs, sc, cur * tile, nxt < ntiles ? nxt * tile : -1, cnt);
             cur = nxt;
         }
     } else {
         for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile)
-            score_tile<NOPROJ, COUNT, GPT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
+            score_tile<PM, COUNT, GPT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
     }
     if (COUNT) {
         const int lane = threadIdx.x & 31;
@@ -867,30 +889,40 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLau
             cur = sidx;
         }
         const SceneConsts sc = *a.consts;
-        if (a.flags & REFINE_FLAG_NO_PROJ)
-            score_tile<true, false, GPT>(a, cs, sc, base, -1, cnt);
+        const int pm = proj_mode(a.flags);
+        if (pm == kProjEq17)
+            score_tile<kProjEq17, false, GPT>(a, cs, sc, base, -1, cnt);
+        else if (pm == kProjNone)
+            score_tile<kProjNone, false, GPT>(a, cs, sc, base, -1, cnt);
         else
-            score_tile<false, false, GPT>(a, cs, sc, base, -1, cnt);
+            score_tile<kProjFullJ, false, GPT>(a, cs, sc, base, -1, cnt);
         __syncthreads();  // the cameras and s_scene are free again
     }
 }
 
-template <bool NOPROJ, bool COUNT, int GPT>
+template <int PM, bool COUNT, int GPT>
 static const void *score_fn()
 {
-    return reinterpret_cast<const void *>(&k_score<NOPROJ, COUNT, GPT>);
+    return reinterpret_cast<const void *>(&k_score<PM, COUNT, GPT>);
+}
+
+template <int PM, int GPT>
+static const void *pick_score_pg(bool count)
+{
+    return count ? score_fn<PM, true, GPT>() : score_fn<PM, false, GPT>();
 }
 
 template <int GPT>
-static const void *pick_score_g(bool noproj, bool count)
+static const void *pick_score_g(int pm, bool count)
 {
-    if (count) return noproj ? score_fn<true, true, GPT>() : score_fn<false, true, GPT>();
-    return noproj ? score_fn<true, false, GPT>() : score_fn<false, false, GPT>();
+    if (pm == kProjNone) return pick_score_pg<kProjNone, GPT>(count);
+    if (pm == kProjFullJ) return pick_score_pg<kProjFullJ, GPT>(count);
+    return pick_score_pg<kProjEq17, GPT>(count);
 }
 
-static const void *pick_score(bool noproj, bool count, int gpt)
+static const void *pick_score(int pm, bool count, int gpt)
 {
-    return gpt == 1 ? pick_score_g<1>(noproj, count) : pick_score_g<2>(noproj, count);
+    return gpt == 1 ? pick_score_g<1>(pm, count) : pick_score_g<2>(pm, count);
 }
 
 bool shape_valid(const ScoreShape &sh)
@@ -903,7 +935,7 @@ int score_grid(int num_sms, int64_t n, int vcount, const ScoreShape &sh)
     // Persistent grid: as many CTAs as fit per SM, capped by the tile count.
     int per_sm = 0;
     const size_t smem = (size_t)vcount * sizeof(CamRec);
-    const void *fn = pick_score(false, false, sh.gpt);
+    const void *fn = pick_score(kProjEq17, false, sh.gpt);
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kScoreThreads, smem) != cudaSuccess ||
         per_sm < 1) {
@@ -920,7 +952,7 @@ int score_grid(int num_sms, int64_t n, int vcount, const ScoreShape &sh)
 
 cudaError_t launch_score(const ScoreLaunch &a, const ScoreShape &sh, cudaStream_t s)
 {
-    const void *fn = pick_score((a.flags & REFINE_FLAG_NO_PROJ) != 0, a.need != nullptr, sh.gpt);
+    const void *fn = pick_score(proj_mode(a.flags), a.need != nullptr, sh.gpt);
     const size_t smem = (size_t)a.vcount * sizeof(CamRec);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -280,7 +280,7 @@ void issue_round(refine_queue *q, std::vector<QJob *> &round)
             R.h_launch[i] = make_score_launch(&j->scene, j->plan, j->sx, j->params, 0, j->scores, nullptr, false,
                                               j->status);
             R.h_tb[i + 1] = R.h_tb[i] + (j->req.n + tile - 1) / tile;
-            max_v = std::max(max_v, j->req.n_views);
+            max_v = std::max(max_v, j->plan.V);
         }
         const int k = (int)live.size();
         cudaStream_t m = q->score_stream;
@@ -572,14 +572,15 @@ refine_status refine_queue_submit(refine_queue *q, const refine_request *req, ui
     if (!q || !req || !ticket) return REFINE_EINVAL;
     const refine_request &r = *req;
     if (r.n < 1 || r.n > INT32_MAX || (r.dtype != REFINE_F32 && r.dtype != REFINE_BF16) || r.n_views < 1 ||
-        r.n_views > kViewsPerPass || !(r.ratio >= 0.0 && r.ratio < 1.0) || !r.pos_host || !r.attr_host ||
+        r.n_views > 65535 || !(r.ratio >= 0.0 && r.ratio < 1.0) || !r.pos_host || !r.attr_host ||
         !r.cams_host || (r.out_pos_host && !r.out_attr_host) || (!r.out_pos_host && (r.out_attr_host || r.kept_idx_host)))
         return REFINE_EINVAL;
     QJob *j = new QJob();
     j->req = r;
     j->params = r.params ? *r.params : q->params;
     if (!(j->params.eta > 0.f) || !isfinite(j->params.eta) || j->params.e_ln_gem == 0.0 || j->params.e_col == 0.0 ||
-        j->params.e_opa == 0.0) {
+        j->params.e_opa == 0.0 || j->params.max_views < 0 ||
+        plan_scene(r.n, r.n_views, j->params.max_views).V > kViewsPerPass) {
         delete j;
         return REFINE_EINVAL;
     }
@@ -587,7 +588,7 @@ refine_status refine_queue_submit(refine_queue *q, const refine_request *req, ui
     j->n_keep = keep_count(r.n, r.ratio);
     j->compact = r.out_pos_host != nullptr;
     j->footprint = footprint_of(r.n, r.dtype, r.n_views, r.ratio, j->compact);
-    j->plan = plan_scene(r.n, r.n_views);
+    j->plan = plan_scene(r.n, r.n_views, j->params.max_views);
     j->pinned_out = is_pinned(r.keep_mask_host) && is_pinned(r.scores_host) && is_pinned(r.out_pos_host) &&
                     is_pinned(r.out_attr_host) && is_pinned(r.kept_idx_host);
     if (j->footprint > q->budget) {

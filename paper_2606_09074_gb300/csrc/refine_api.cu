@@ -427,11 +427,12 @@ refine_status refine_batch_create(refine_ctx *c, const refine_job *jobs, int32_t
             delete b;
             return fail(c, st, "batch job %d: %s", j, std::string(c->err).c_str());
         }
-        if (jb.scene.n < 1 || jb.n_views > kViewsPerPass || !jb.keep_mask_dev ||
+        const ScenePlan jp = plan_scene(jb.scene.n, jb.n_views, p.max_views);
+        if (jb.scene.n < 1 || jp.V > kViewsPerPass || !jb.keep_mask_dev ||
             !(jb.ratio >= 0.0 && jb.ratio < 1.0)) {
             delete b;
             return fail(c, REFINE_EINVAL,
-                        "batch job %d: needs n >= 1, n_views <= %d, a keep mask and a ratio "
+                        "batch job %d: needs n >= 1, at most %d views scored, a keep mask and a ratio "
                         "in [0, 1)",
                         j, kViewsPerPass);
         }
@@ -441,9 +442,9 @@ refine_status refine_batch_create(refine_ctx *c, const refine_job *jobs, int32_t
             return fail(c, REFINE_EINVAL, "batch job %d: compaction output missing or shorter than n_keep", j);
         }
         b->n_keep.push_back(nk);
-        b->plans.push_back(plan_scene(jb.scene.n, jb.n_views));
+        b->plans.push_back(jp);
         total += scene_bytes(b->plans.back()) + select_bytes(jb.scene.n) + compact_bytes(jb.scene.n) + 768;
-        b->max_v = std::max(b->max_v, jb.n_views);
+        b->max_v = std::max(b->max_v, jp.V);
     }
     cudaError_t e = cudaMalloc(&b->scratch, total);
     if (e != cudaSuccess) {

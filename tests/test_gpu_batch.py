@@ -79,7 +79,7 @@ def test_batch_rejects_bad_jobs(env):
 
 def test_batch_mixed_storage_and_flags(env):
     """Scenes of both storage types share one batched launch; each equals
-    its own per-scene run."""
+    its own per-scene run, for every projection mode."""
     torch, rb, ctx = env
     ws = []
     for k, (seed, n, v) in enumerate([(41, 5000, 9), (42, 33_333, 40), (43, 700, 3)]):
@@ -89,14 +89,17 @@ def test_batch_mixed_storage_and_flags(env):
         ws.append(w)
     up = [upload(torch, rb, w) for w in ws]
     jobs = [{"pos": p, "attr": a, "cams": c, "ratio": 0.5} for (p, a, c) in up]
-    batch = rb.Batch(ctx, jobs)
-    batch.run()
-    nk_b, thr_b = batch.results()
-    for k, (p, a, c) in enumerate(up):
-        s = ctx.score(p, a, c)
-        m, thr, nk = ctx.select(s, 0.5)
-        assert torch.equal(batch.outputs[k]["scores"], s)
-        assert nk_b[k] == nk and thr_b[k] == thr
+    for flags in (rb.FLAG_NORM_ATTR, rb.FLAG_NORM_ATTR | rb.FLAG_NO_PROJ, rb.FLAG_NORM_ATTR | rb.FLAG_FULL_JACOBIAN):
+        prm = rb.default_params(flags=flags)
+        batch = rb.Batch(ctx, jobs, params=prm)
+        batch.run()
+        nk_b, thr_b = batch.results()
+        for k, (p, a, c) in enumerate(up):
+            s = ctx.score(p, a, c, params=prm)
+            m, thr, nk = ctx.select(s, 0.5)
+            assert torch.equal(batch.outputs[k]["scores"], s), (flags, k)
+            assert nk_b[k] == nk and thr_b[k] == thr
+        batch.close()
 
 
 def test_every_shape_gives_the_same_scores(env):

@@ -460,3 +460,39 @@ def test_borderline_alternatives_helper():
     assert oracle.valid_alternative(np.array([1.0, 2.75]), o, 1e-6).all()
     assert oracle.valid_alternative(np.array([1.0, 2.25]), o, 1e-6).all()
     assert not oracle.valid_alternative(np.array([1.0, 2.1]), o, 1e-6)[1]
+
+
+# ------------------------------------------------ Eq. 14 Jacobian energy
+
+@pytest.mark.parametrize("mean", [(0.0, 0.0, 3.0), (0.4, -0.25, 2.0), (-1.1, 0.7, 6.5)])
+def test_full_jacobian_term_closed_form(mean):
+    """With FULL_JACOBIAN the projection term is Eq. 14's energy of J_Pi
+    before the Eq. 16 simplification: for N = 1 and one view,
+    D = alpha (fx^2/z^2 + fy^2/z^2 + (fx^2 x^2 + fy^2 y^2)/z^4)."""
+    cam = ident_cam(fx=700.0, fy=520.0, w=4000, h=4000)
+    cams = np.array([cam], dtype=synth.CAMERA_DTYPE)
+    g = one_primitive(mean, (math.log(0.01),) * 3, logit=0.7)
+    o = oracle.score(g, cams, oracle.params(flags=oracle.NORM_ATTR | oracle.FULL_JACOBIAN))
+    x, y, z = mean
+    fx, fy = 700.0, 520.0
+    P = fx * fx / z ** 2 + fy * fy / z ** 2 + (fx * fx * x * x + fy * fy * y * y) / z ** 4
+    alpha = 1 / (1 + math.exp(-0.7))
+    assert o["S"][0] == pytest.approx(P, rel=1e-13)
+    assert o["scores"][0] == pytest.approx(alpha * P, rel=1e-12)
+
+
+def test_full_jacobian_term_matches_finite_differences():
+    """The energy equals the squared Frobenius norm of a central-difference
+    Jacobian of the projection Pi (Eq. 13), an independent derivative."""
+    cam = ident_cam(fx=640.0, fy=610.0, w=5000, h=5000, cx=2400.0, cy=2550.0)
+    oc = oracle.cameras(np.array([cam], dtype=synth.CAMERA_DTYPE))[0]
+    for tc in ([0.3, -0.2, 2.5], [-1.0, 0.8, 4.0]):
+        h = 1e-6
+        J = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3); e[k] = h
+            J[:, k] = (np.asarray(oracle.project(oc, np.add(tc, e))) - np.asarray(oracle.project(oc, np.subtract(tc, e)))) / (2 * h)
+        g = one_primitive(tc, (math.log(0.001),) * 3)
+        o = oracle.score(g, np.array([cam], dtype=synth.CAMERA_DTYPE),
+                         oracle.params(flags=oracle.NORM_ATTR | oracle.FULL_JACOBIAN))
+        assert o["S"][0] == pytest.approx(float((J ** 2).sum()), rel=1e-7)
