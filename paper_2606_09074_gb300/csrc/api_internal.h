@@ -485,9 +485,9 @@ inline refine_status enqueue_compact(refine_ctx *c, L &&run, const refine_scene 
              return launch_compact_count(mask, n, seg_cnt, seg_off, cs, out_stride, (int)cgrid, status, s);
          })))
         return st;
-    const int sgrid = compact_grid(c->num_sms, n);
+    const CmpShape sshape = compact_shape(c->num_sms, n, in->dtype);
     if ((st = run(K_CMP_SCATTER, [&] {
-             return launch_compact_scatter(*in, mask, seg_off, cs, out_pos, out_attr, out_stride, idx, sgrid, s);
+             return launch_compact_scatter(*in, mask, seg_off, cs, out_pos, out_attr, out_stride, idx, sshape, s);
          })))
         return st;
     *total_dev = &cs->total;

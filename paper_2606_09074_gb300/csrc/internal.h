@@ -156,9 +156,13 @@ constexpr int kCmpSeg = 256;  // elements per compaction segment (8 mask words)
 cudaError_t launch_compact_count(const uint32_t *mask, int64_t n, unsigned *seg_cnt,
                                  unsigned long long *seg_off, CmpState *cs, int64_t out_stride,
                                  int grid, int *status, cudaStream_t s);
-int compact_grid(int num_sms, int64_t n);
+struct CmpShape {
+    int grid;  // CTAs of the scatter
+    bool seg;  // k_compact_seg (a warp per segment) rather than k_compact_warp (a warp per mask word)
+};
+CmpShape compact_shape(int num_sms, int64_t n, int dtype);
 cudaError_t launch_compact_scatter(const refine_scene &in, const uint32_t *mask, const unsigned long long *seg_off,
                                    const CmpState *cs, float *out_pos, void *out_attr, int64_t out_stride,
-                                   int32_t *out_idx, int grid, cudaStream_t s);
+                                   int32_t *out_idx, CmpShape shape, cudaStream_t s);
 
 }  // namespace refine

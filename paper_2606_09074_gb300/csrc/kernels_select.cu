@@ -321,7 +321,7 @@ cudaError_t launch_mask_fill(uint32_t *mask, int64_t n, cudaStream_t s)
 // Compaction, pass 1.  Segment s covers elements [s*kCmpSeg, (s+1)*kCmpSeg)
 // (8 mask words).  Kept elements are counted per segment and the last CTA
 // turns the counts into exclusive offsets; the scatter of every row is
-// k_compact_seg.
+// k_compact_warp or k_compact_seg.
 // ---------------------------------------------------------------------
 constexpr int kCmpThreads = 1024;
 

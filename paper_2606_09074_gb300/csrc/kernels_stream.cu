@@ -1,21 +1,34 @@
-// Compaction, pass 2: the scatter of every row of the kept primitives.
+// Compaction, pass 2: the scatter of every row of the kept primitives, in
+// one of two forms chosen by compact_shape from the scene's size and type.
 //
-// One warp owns one segment of kCmpSeg = 256 primitives (8 mask words) at a
-// time; its output offset is the segment's offset from pass 1
-// (k_compact_count) plus the kept bits of the segment's earlier words, taken
-// with a shuffle scan over the 8 words.  For each word the warp inverts the
-// ranks of the kept bits once (lane d of the output reads from the lane
-// holding the d-th kept primitive).  Each of the 59 rows then moves with 8
-// coalesced loads (one contiguous 1 KB span of the row), 8 shuffles and 8
-// stores that together write one contiguous run of the output row, so only
-// the two ends of a run are partial sectors.  Two rows (16 loads) are in
-// flight per warp; the CTA is 8 warps with 2 KB of shared memory, held to
-// 3 CTAs per SM by its launch bounds.  No shared-memory staging of the rows.
+// Word form (k_compact_warp).  One warp handles one mask word (32
+// primitives) at a time; its output offset is the offset of its segment of
+// kCmpSeg = 256 primitives (from pass 1, k_compact_count) plus the kept bits
+// of the segment's earlier words.  The warp inverts the ranks of the kept
+// bits once (lane d of the output reads from the lane holding the d-th kept
+// primitive), then moves each of the 59 rows with one coalesced load, one
+// shuffle and one contiguous store; the loads of sixteen rows are in flight
+// at a time.  The CTA is 8 warps with a few hundred bytes of shared memory
+// and 40 registers per thread, so an SM keeps 48 warps, and their 768 row
+// loads, resident.
+//
+// Segment form (k_compact_seg, FP32 attributes only).  One warp owns a
+// whole segment (8 mask words); the offsets of its words come from a shuffle
+// scan of their kept counts.  Each row moves with 8 coalesced loads (one
+// contiguous 1 KB span of the row), 8 shuffles and 8 stores that together
+// write one contiguous run of the output row.  Two rows (16 loads) are in
+// flight per warp; 80 registers hold the per-word ranks and offsets, so 3
+// CTAs of 8 warps fit per SM.  It keeps a quarter of the word form's warps in
+// flight, which pays only when each warp has several segments to stream.
+//
+// No shared-memory staging of the rows in either form.
 #include "internal.h"
 
 namespace refine {
 
 constexpr int kCmpWarps = 8;
+constexpr int kCmpBatch = 16;  // rows in flight per warp
+
 __device__ __forceinline__ float shfl_row(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ __nv_bfloat16 shfl_row(__nv_bfloat16 v, int src)
 {
@@ -23,46 +36,91 @@ __device__ __forceinline__ __nv_bfloat16 shfl_row(__nv_bfloat16 v, int src)
     return __ushort_as_bfloat16(b);
 }
 
-constexpr int kSegRows = 2;  // rows in flight per warp (8 loads each)
-
 template <typename T, int NR>
-__device__ __forceinline__ void move_rows_seg(const T *__restrict__ in, int64_t S, const bool (&ld)[8],
-                                              const int (&src)[8], const int (&kept)[8], T *__restrict__ out,
-                                              const int (&off)[8], int64_t OS)
+__device__ __forceinline__ void move_rows(const T *__restrict__ in, int64_t S, bool ld, int src, T *__restrict__ out,
+                                          int64_t OS, bool st)
 {
-    const int lane = threadIdx.x & 31;
 #pragma unroll 1
-    for (int r0 = 0; r0 < NR; r0 += kSegRows) {
-        T v[kSegRows][8];
+    for (int r0 = 0; r0 < NR; r0 += kCmpBatch) {
+        T v[kCmpBatch];
 #pragma unroll
-        for (int k = 0; k < kSegRows; ++k)
+        for (int k = 0; k < kCmpBatch; ++k) v[k] = (ld && r0 + k < NR) ? in[k * S] : T(0.f);
 #pragma unroll
-            for (int w = 0; w < 8; ++w)
-                v[k][w] = (ld[w] && r0 + k < NR) ? in[(int64_t)k * S + 32 * w] : T(0.f);
-#pragma unroll
-        for (int k = 0; k < kSegRows; ++k) {
-            if (r0 + k >= NR) break;  // uniform
-#pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                const T x = shfl_row(v[k][w], src[w]);
-                if (lane < kept[w]) out[(int64_t)k * OS + off[w] + lane] = x;
-            }
+        for (int k = 0; k < kCmpBatch; ++k) {
+            const T x = shfl_row(v[k], src);
+            if (st && r0 + k < NR) out[k * OS] = x;
         }
-        in += kSegRows * S;
-        out += kSegRows * OS;
+        in += kCmpBatch * S;
+        out += kCmpBatch * OS;
     }
 }
 
 template <typename AT>
+__global__ void __launch_bounds__(32 * kCmpWarps) k_compact_warp(const float *__restrict__ pos,
+                                                                 const AT *__restrict__ attr, int64_t S, int64_t n,
+                                                                 const uint32_t *__restrict__ mask,
+                                                                 const unsigned long long *__restrict__ seg_off,
+                                                                 const CmpState *cs, float *__restrict__ out_pos,
+                                                                 AT *__restrict__ out_attr, int64_t OS,
+                                                                 int32_t *__restrict__ out_idx)
+{
+    __shared__ unsigned char src_of[kCmpWarps][32];
+    if (!cs->ok) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    constexpr int kWords = kCmpSeg / 32;
+    const int64_t words = (n + 31) / 32;
+    for (int64_t w = (int64_t)blockIdx.x * kCmpWarps + wib; w < words; w += (int64_t)gridDim.x * kCmpWarps) {
+        // lane k < (w mod 8) holds the k-th earlier word of the segment, lane
+        // 31 this word; bits past n cleared
+        const int64_t w0 = w & ~(int64_t)(kWords - 1);
+        const int64_t wl = lane == 31 ? w : w0 + lane;
+        uint32_t word = 0u;
+        if (lane == 31 || wl < w) {
+            word = __ldg(mask + wl);
+            const int64_t valid = n - wl * 32;
+            if (valid < 32) word &= (1u << valid) - 1u;
+        }
+        const uint32_t wk = __shfl_sync(0xffffffffu, word, 31);
+        const int kept = __popc(wk);
+        if (kept == 0) continue;  // uniform
+        const int before = __reduce_add_sync(0xffffffffu, lane == 31 ? 0u : (unsigned)__popc(word));
+        const int64_t base = w * 32;
+        const int64_t dst = (int64_t)__ldg(seg_off + w / kWords) + before + lane;
+        if ((wk >> lane) & 1u) src_of[wib][__popc(wk & ((1u << lane) - 1u))] = (unsigned char)lane;
+        __syncwarp();
+        const int src = lane < kept ? src_of[wib][lane] : lane;
+        __syncwarp();
+        const bool ld = base + lane < n;
+        const bool st = lane < kept;
+        if (out_idx && st) out_idx[dst] = (int32_t)(base + src);
+        move_rows<float, 3>(pos + base + lane, S, ld, src, out_pos + dst, OS, st);
+        move_rows<AT, 56>(attr + base + lane, S, ld, src, out_attr + dst, OS, st);
+    }
+}
+
+constexpr int kSegRows = 2;  // rows in flight per warp (8 loads each)
+
+// The 59 rows of one primitive are pos rows 0..2 then attr rows 0..55; for
+// FP32 attributes both are float, so one loop walks all 59.
+__device__ __forceinline__ const float *seg_row(const float *pos, const float *attr, int64_t S, int r)
+{
+    return r < 3 ? pos + (int64_t)r * S : attr + (int64_t)(r - 3) * S;
+}
+__device__ __forceinline__ float *seg_row(float *pos, float *attr, int64_t S, int r)
+{
+    return r < 3 ? pos + (int64_t)r * S : attr + (int64_t)(r - 3) * S;
+}
+
 __global__ void __launch_bounds__(32 * kCmpWarps, 3) k_compact_seg(const float *__restrict__ pos,
-                                                                   const AT *__restrict__ attr, int64_t S, int64_t n,
-                                                                   const uint32_t *__restrict__ mask,
+                                                                   const float *__restrict__ attr, int64_t S,
+                                                                   int64_t n, const uint32_t *__restrict__ mask,
                                                                    const unsigned long long *__restrict__ seg_off,
                                                                    const CmpState *cs, float *__restrict__ out_pos,
-                                                                   AT *__restrict__ out_attr, int64_t OS,
+                                                                   float *__restrict__ out_attr, int64_t OS,
                                                                    int32_t *__restrict__ out_idx)
 {
     constexpr int kWords = kCmpSeg / 32;
+    constexpr int kRows = 3 + 56;
     static_assert(kWords == 8, "a segment is 8 mask words");
     __shared__ unsigned char src_of[kCmpWarps][kWords][32];
     if (!cs->ok) return;
@@ -106,37 +164,68 @@ __global__ void __launch_bounds__(32 * kCmpWarps, 3) k_compact_seg(const float *
 #pragma unroll
             for (int w = 0; w < kWords; ++w)
                 if (lane < kept[w]) out_idx[o0 + off[w] + lane] = (int32_t)(base + 32 * w + src[w]);
-        move_rows_seg<float, 3>(pos + base + lane, S, ld, src, kept, out_pos + o0, off, OS);
-        move_rows_seg<AT, 56>(attr + base + lane, S, ld, src, kept, out_attr + o0, off, OS);
+        const float *in_p = pos + base + lane, *in_a = attr + base + lane;
+        float *out_p = out_pos + o0, *out_a = out_attr + o0;
+#pragma unroll 1
+        for (int r0 = 0; r0 < kRows; r0 += kSegRows) {
+            float v[kSegRows][kWords];
+#pragma unroll
+            for (int k = 0; k < kSegRows; ++k) {
+                const float *in = seg_row(in_p, in_a, S, r0 + k);
+#pragma unroll
+                for (int w = 0; w < kWords; ++w) v[k][w] = (ld[w] && r0 + k < kRows) ? in[32 * w] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < kSegRows; ++k) {
+                if (r0 + k >= kRows) break;  // uniform
+                float *out = seg_row(out_p, out_a, OS, r0 + k);
+#pragma unroll
+                for (int w = 0; w < kWords; ++w) {
+                    const float x = shfl_row(v[k][w], src[w]);
+                    if (lane < kept[w]) out[off[w] + lane] = x;
+                }
+            }
+        }
     }
 }
 
-// Segments are dealt round-robin over a grid of at most 6 CTAs per SM, twice
-// the 3 that the launch bounds keep resident: the second wave fills SMs whose
-// first CTAs finish early (3.5M primitives, FP32 rows: 0.214 ms against
-// 0.220 ms with one resident wave).
-int compact_grid(int num_sms, int64_t n)
+// The segment form for FP32 rows once every resident warp of it gets two
+// segments or more (n of 1.87M or more on 152 SMs); the word form otherwise.
+// Measured on 3.5M primitives, FP32 rows: 0.199 ms against 0.249 ms; BF16
+// rows: 0.164 ms both; 1M primitives: 0.084 ms against 0.067 ms.  Work is
+// dealt round-robin over at most 6 CTAs per SM: for the segment form that is
+// two waves of 3, the second filling SMs whose first CTAs finish early.
+CmpShape compact_shape(int num_sms, int64_t n, int dtype)
 {
     const int64_t nseg = (n + kCmpSeg - 1) / kCmpSeg;
-    int64_t g = (nseg + kCmpWarps - 1) / kCmpWarps;
+    const bool seg = dtype == REFINE_F32 && nseg >= 2 * (int64_t)num_sms * 3 * kCmpWarps;
+    const int64_t units = seg ? nseg : (n + 31) / 32;
+    int64_t g = (units + kCmpWarps - 1) / kCmpWarps;
     const int64_t cap = (int64_t)num_sms * 6;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    return (int)g;
+    return {(int)g, seg};
 }
 
 cudaError_t launch_compact_scatter(const refine_scene &in, const uint32_t *mask, const unsigned long long *seg_off,
                                    const CmpState *cs, float *out_pos, void *out_attr, int64_t out_stride,
-                                   int32_t *out_idx, int grid, cudaStream_t s)
+                                   int32_t *out_idx, CmpShape shape, cudaStream_t s)
 {
-    if (in.dtype == REFINE_BF16)
-        k_compact_seg<__nv_bfloat16><<<grid, 32 * kCmpWarps, 0, s>>>(
-            in.pos, static_cast<const __nv_bfloat16 *>(in.attr), in.row_stride, in.n, mask, seg_off, cs, out_pos,
-            static_cast<__nv_bfloat16 *>(out_attr), out_stride, out_idx);
-    else
-        k_compact_seg<float><<<grid, 32 * kCmpWarps, 0, s>>>(in.pos, static_cast<const float *>(in.attr),
-                                                              in.row_stride, in.n, mask, seg_off, cs, out_pos,
-                                                              static_cast<float *>(out_attr), out_stride, out_idx);
+    if (in.dtype == REFINE_BF16) {
+        const __nv_bfloat16 *a = static_cast<const __nv_bfloat16 *>(in.attr);
+        __nv_bfloat16 *oa = static_cast<__nv_bfloat16 *>(out_attr);
+        k_compact_warp<__nv_bfloat16><<<shape.grid, 32 * kCmpWarps, 0, s>>>(
+            in.pos, a, in.row_stride, in.n, mask, seg_off, cs, out_pos, oa, out_stride, out_idx);
+    } else {
+        const float *a = static_cast<const float *>(in.attr);
+        float *oa = static_cast<float *>(out_attr);
+        if (shape.seg)
+            k_compact_seg<<<shape.grid, 32 * kCmpWarps, 0, s>>>(in.pos, a, in.row_stride, in.n, mask, seg_off, cs,
+                                                                out_pos, oa, out_stride, out_idx);
+        else
+            k_compact_warp<float><<<shape.grid, 32 * kCmpWarps, 0, s>>>(in.pos, a, in.row_stride, in.n, mask,
+                                                                        seg_off, cs, out_pos, oa, out_stride, out_idx);
+    }
     return cudaGetLastError();
 }
 

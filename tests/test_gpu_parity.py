@@ -354,6 +354,37 @@ def test_padded_row_stride(torch, rb, ctx, dtype):
     assert torch.equal(i0, i1) and torch.equal(op0, op1) and torch.equal(oa0, oa1)
 
 
+@pytest.mark.parametrize("pattern,ratio,pad,opad", [("random", 0.5, 0, 0), ("random", 0.1, 37, 5),
+                                                     ("random", 0.97, 64, 0), ("blocks", 0.5, 3, 11)])
+def test_compact_large_fp32_ragged(torch, rb, ctx, pattern, ratio, pad, opad):
+    """FP32 scenes of about 1.9M primitives or more are scattered one warp
+    per 256-primitive segment: a ragged n (not a multiple of 32 or 256),
+    padded input and output rows, sparse and dense masks and masks with long
+    all-kept and all-pruned runs, bit-exact against the oracle's gather."""
+    n = 2_000_003
+    rng = np.random.default_rng(4242 + pad)
+    pos_h = rng.standard_normal((3, n), dtype=np.float32)
+    attr_h = rng.standard_normal((56, n), dtype=np.float32)
+    scores = rng.random(n, dtype=np.float32)
+    if pattern == "blocks":
+        scores += ((np.arange(n) // 700) % 3).astype(np.float32)
+    dev = torch.device("cuda", 0)
+    pos_p = torch.zeros((3, n + pad), dtype=torch.float32, device=dev)
+    attr_p = torch.zeros((56, n + pad), dtype=torch.float32, device=dev)
+    pos_p[:, :n] = torch.from_numpy(pos_h).to(dev)
+    attr_p[:, :n] = torch.from_numpy(attr_h).to(dev)
+    m, _, nk = ctx.select(torch.from_numpy(scores).to(dev), ratio)
+    op, oa, idx, cnt = ctx.compact(pos_p[:, :n], attr_p[:, :n], m, nk, out_row_stride=nk + opad,
+                                   return_count=True)
+    words = m.cpu().numpy().view(np.uint32)[: (n + 31) // 32]
+    kp, ki = oracle.compact(pos_h, words)
+    ka, _ = oracle.compact(attr_h, words)
+    assert cnt == nk == n - int(np.floor(ratio * n))
+    assert np.array_equal(idx.cpu().numpy(), ki)
+    assert np.array_equal(op[:, :nk].cpu().numpy(), kp[:, :nk])
+    assert np.array_equal(oa[:, :nk].cpu().numpy(), ka[:, :nk])
+
+
 @pytest.mark.parametrize("v,mv", [(250, 64), (150, 64), (64, 64), (10, 3), (7, 1)])
 def test_max_views_subsampling(torch, rb, ctx, v, mv):
     """max_views scores views 0, s, 2s, ... (s = ceil(V / max_views)) with
