@@ -222,6 +222,69 @@ def run_reference(args, rank: int, world: int):
 
 # ------------------------------------------------------------------- ours
 
+def end_to_end(args, torch, rb, ctx, w, attr, params, ratio, n_keep, pairs, V_all, stream):
+    """Host-to-host throughput through the public API, from page-locked
+    buffers: every step copies the scene and cameras in and the kept rows,
+    indices and threshold out.  The headline form keeps `--e2e-inflight`
+    requests in the request queue, so one request's copies overlap another's
+    compute and the two link directions run together; the sequential form
+    (refine_prune_host, one call after another) is reported beside it."""
+    n = w.scene.n
+    pos_h = torch.from_numpy(w.scene.pos).pin_memory()
+    attr_h = attr.cpu().pin_memory()
+    asz = attr.element_size() * 56
+    h2d = 12 * n + asz * n + 80 * V_all
+    d2h = (12 + asz + 4) * n_keep + 4 + 4
+
+    def outset():
+        return {"out_pos": torch.empty((3, n_keep), dtype=torch.float32, pin_memory=True),
+                "out_attr": torch.empty((56, n_keep), dtype=attr.dtype, pin_memory=True),
+                "idx": torch.empty(n_keep, dtype=torch.int32, pin_memory=True)}
+
+    k_e2e = max(3, min(args.steps, 60))
+    outs = outset()
+    for _ in range(2):
+        ctx.prune_host(pos_h, attr_h, w.cams, ratio, params=params, out=outs, stream=stream)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        ctx.prune_host(pos_h, attr_h, w.cams, ratio, params=params, out=outs, stream=stream)
+    dt_seq = (time.perf_counter() - t0) / k_e2e
+    sequential = {"value": pairs / dt_seq, "unit": "pairs/s", "ms_per_step": dt_seq * 1000, "steps": k_e2e,
+                  "api": "refine_prune_host, one call after another"}
+
+    D = args.e2e_inflight
+    if D < 2:
+        return {**sequential, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    dt_code = rb.REFINE_BF16 if attr.dtype == torch.bfloat16 else rb.REFINE_F32
+    fp = rb.Queue.footprint(n, dt_code, len(w.cams), ratio)
+    q = rb.Queue(ctx, budget_bytes=(D + 1) * fp, max_slots=D, params=params)
+    sets = [outset() for _ in range(D + 1)]
+    try:
+        def run(k_total):
+            inflight = []
+            for k in range(k_total):
+                if len(inflight) == D:
+                    res, _ = q.poll(inflight.pop(0), timeout_ms=120_000)
+                    if res["status"] != 0:
+                        raise RuntimeError(f"queued request failed: {res['status']} {q.last_error()}")
+                inflight.append(q.submit(pos_h, attr_h, w.cams, ratio, outputs=sets[k % (D + 1)], mask=False,
+                                         compact=True, pin=True))
+            for t in inflight:
+                res, _ = q.poll(t, timeout_ms=120_000)
+                if res["status"] != 0:
+                    raise RuntimeError(f"queued request failed: {res['status']} {q.last_error()}")
+        run(2 * D)
+        t0 = time.perf_counter()
+        run(k_e2e)
+        dt = (time.perf_counter() - t0) / k_e2e
+    finally:
+        q.close()
+    return {"value": pairs / dt, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1000, "steps": k_e2e,
+            "api": f"refine_queue_submit / refine_queue_poll, {D} requests in flight, page-locked host buffers",
+            "link_gbs": (h2d + d2h) / dt / 1e9, "sequential": sequential}
+
+
 def run_ours(args, rank: int, world: int):
     import torch
     from paper_2606_09074_gb300 import binding as rb
@@ -317,22 +380,7 @@ def run_ours(args, rank: int, world: int):
         # end to end through the public API from pinned host memory
         e2e = None
         if not args.no_e2e:
-            pos_h = torch.from_numpy(w.scene.pos).pin_memory()
-            attr_h = attr.cpu().pin_memory()
-            outs = {"out_pos": torch.empty((3, n_keep), dtype=torch.float32, pin_memory=True),
-                    "out_attr": torch.empty((56, n_keep), dtype=attr.dtype, pin_memory=True),
-                    "idx": torch.empty(n_keep, dtype=torch.int32, pin_memory=True)}
-            for _ in range(2):
-                ctx.prune_host(pos_h, attr_h, w.cams, ratio, params=params, out=outs, stream=stream)
-            k_e2e = max(3, min(args.steps, 60))
-            t0 = time.perf_counter()
-            for _ in range(k_e2e):
-                ctx.prune_host(pos_h, attr_h, w.cams, ratio, params=params, out=outs, stream=stream)
-            dt = (time.perf_counter() - t0) / k_e2e
-            asz = attr.element_size() * 56
-            e2e = {"value": pairs / dt, "unit": "pairs/s", "h2d_bytes_per_step": 12 * n + asz * n + 80 * V_all,
-                   "d2h_bytes_per_step": (12 + asz + 4) * n_keep + 4 + 4, "ms_per_step": dt * 1000,
-                   "steps": k_e2e, "api": "refine_prune_host (pinned host buffers)"}
+            e2e = end_to_end(args, torch, rb, ctx, w, attr, params, ratio, n_keep, pairs, V_all, stream)
         cpu = None
         if not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
@@ -687,6 +735,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-inflight", type=int, default=3,
+                    help="requests in flight in the end-to-end measurement (1: sequential calls only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
