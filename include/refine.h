@@ -107,7 +107,7 @@ typedef struct refine_scene {
 
 /* Method parameters.  Fill with refine_params_default() and override. */
 typedef struct refine_params {
-    float eta;        /* Eq. 17 and Eq. 18 stability constant (> 0)                  */
+    float eta;        /* Eq. 17 and Eq. 18 stability constant (>= FLT_MIN, finite)  */
     float luma[3];    /* weights of the perceptual luma Y of the SH DC colour          */
     double e_ln_gem;  /* Eq. 18 calibration E[ln F_gem] (nonzero)                      */
     double e_col;     /* Eq. 18 calibration E[F_col]    (nonzero)                      */

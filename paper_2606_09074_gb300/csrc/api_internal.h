@@ -4,6 +4,7 @@
 // a caller-supplied runner, so the same sequence serves the plain calls, the
 // graph-captured batch and the request queue.
 #pragma once
+#include <float.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stddef.h>
@@ -183,7 +184,8 @@ inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 inline refine_status check_params(refine_ctx *c, const refine_params *p)
 {
-    if (!(p->eta > 0.f) || !isfinite(p->eta)) return fail(c, REFINE_EINVAL, "params: eta must be finite and > 0");
+    if (!(p->eta >= FLT_MIN) || !isfinite(p->eta))
+        return fail(c, REFINE_EINVAL, "params: eta must be finite and at least FLT_MIN (1.18e-38)");
     for (int k = 0; k < 3; ++k)
         if (!isfinite(p->luma[k])) return fail(c, REFINE_EINVAL, "params: luma must be finite");
     if (!(isfinite(p->e_ln_gem) && p->e_ln_gem != 0.0 && isfinite(p->e_col) && p->e_col != 0.0 &&

@@ -188,6 +188,17 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
+// The same reciprocal without the handling of subnormal operands and
+// results: a single MUFU operation, against several instructions for the
+// form above.  Equal to rcp_approx for x in [2^-126, 2^126]; above that the
+// result (below 2^-126) flushes to zero.
+__device__ __forceinline__ float rcp_approx_ftz(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Order-preserving map of a float score to an unsigned key (-0 maps as +0).
 __device__ __forceinline__ uint32_t score_key(float f)
 {

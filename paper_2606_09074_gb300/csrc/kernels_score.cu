@@ -515,7 +515,9 @@ template <int PM>
 __device__ __forceinline__ float weight(const CamRec &c, float z, float eta, float mx, float my, float mz)
 {
     if (PM == kProjNone) return 1.f;
-    if (PM == kProjEq17) return rcp_approx(fmaf(z, z, eta));
+    // z^2 + eta >= eta >= 2^-126 (checked on the host), so the operand is
+    // never subnormal; weights below 2^-126 (z beyond 9.2e18) flush to zero
+    if (PM == kProjEq17) return rcp_approx_ftz(fmaf(z, z, eta));
     const float4 tx = c.tx, ty = c.ty, k = c.k;
     const float fxx = fmaf(tx.x, mx, fmaf(tx.y, my, fmaf(tx.z, mz, tx.w)));
     const float fyy = fmaf(ty.x, mx, fmaf(ty.y, my, fmaf(ty.z, mz, ty.w)));

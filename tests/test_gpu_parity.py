@@ -265,9 +265,10 @@ def test_nonfinite_and_invalid_inputs(torch, rb, ctx):
         ctx.select(torch.rand(10, device="cuda"), 1.0)
     with pytest.raises(rb.RefineError):
         ctx.score(pos, attr, cams, n_views=0)
-    p = rb.default_params(eta=0.0)
-    with pytest.raises(rb.RefineError):
-        ctx.score(pos, attr, cams, params=p)
+    for eta in (0.0, 1e-40):  # zero, and a subnormal float32: the Eq. 17 reciprocal needs eta >= FLT_MIN
+        p = rb.default_params(eta=eta)
+        with pytest.raises(rb.RefineError):
+            ctx.score(pos, attr, cams, params=p)
     # compaction into a too-short output is refused by the device
     s = ctx.score(pos, attr, cams)
     mask, _, nk = ctx.select(s, 0.5)
