@@ -84,8 +84,8 @@ struct ScoreLaunch {
     float *scores;
     float *view_sum;            // optional
     unsigned long long *need;   // optional diagnostic counters (kCountSlots), see k_score
-    unsigned long long *tiles_taken;  // k_score: tile counter (zero before the launch) for dynamic
-                                      // scheduling; NULL = static grid-stride order
+    unsigned long long *tiles_taken;  // k_score: warp-tile counter, zero before the launch (required;
+                                      // k_score_batch takes its items from BatchLaunch::counter)
     int *status;
     int grid;                   // CTAs (persistent)
 };

@@ -656,18 +656,18 @@ __device__ __forceinline__ void fence_proxy_async_shared()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Scores one tile of blockDim.x * GPT primitives of the processing
-// order starting at `base`; `next_base` (or -1) is the tile this CTA takes
-// next, whose primitives are pulled towards L2 meanwhile.
+// Scores one warp tile: the 32 * GPT primitives of the processing order
+// starting at `base`; `next_base` (or -1) is the tile this warp takes next,
+// whose primitives are pulled towards L2 meanwhile.
 template <int PM, bool COUNT, int GPT>
 __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *cs, const SceneConsts &sc,
                                            int64_t base, int64_t next_base, unsigned long long (&cnt)[kCountSlots])
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     if (next_base >= 0) {
 #pragma unroll
         for (int g = 0; g < GPT; ++g) {
-            const int64_t j = next_base + (int64_t)warp * 32 * GPT + g * 32 + lane;
+            const int64_t j = next_base + g * 32 + lane;
             if (j < a.n) prefetch_l2(a.recs + __ldg(a.perm + j));
         }
     }
@@ -679,7 +679,7 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, b2 = 0.f;
 #pragma unroll
     for (int g = 0; g < GPT; ++g) {
-        const int64_t j = base + (int64_t)warp * 32 * GPT + g * 32 + lane;
+        const int64_t j = base + g * 32 + lane;
         float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
         idx[g] = -1;
         acc[g] = 0.f;
@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
     __shared__ int s_ok;
     const uint32_t bytes = (uint32_t)a.vcount * (uint32_t)sizeof(CamRec);
     if (threadIdx.x == 0) {
-        s_ok = cams_stageable(a.cams, a.vcount);
+        s_ok = cams_stageable(a.cams, a.vcount) && a.tiles_taken != nullptr;
         if (s_ok) {
             mbar_init(&bar, 1);
             mbar_expect_tx(&bar, bytes);
@@ -786,30 +786,25 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 #pragma unroll
     for (int k = 0; k < kCountSlots; ++k) cnt[k] = 0;
     const SceneConsts sc = *a.consts;
-    const int64_t tile = (int64_t)blockDim.x * GPT;
-    if (a.tiles_taken) {
-        // Tiles are taken from a counter, one ahead (its records are pulled
-        // towards L2 while the current tile is scored), so CTAs that draw
-        // cheap tiles take more of them.
-        __shared__ long long s_next;
-        const long long ntiles = (long long)((a.n + tile - 1) / tile);
-        if (threadIdx.x == 0) s_next = (long long)atomicAdd(a.tiles_taken, 1ull);
-        __syncthreads();
-        long long cur = s_next;
-        while (cur < ntiles) {
-            __syncthreads();  // every thread has read s_next
-            if (threadIdx.x == 0) s_next = (long long)atomicAdd(a.tiles_taken, 1ull);
-            __syncthreads();
-            const long long nxt = s_next;
-            score_tile<PM, COUNT, GPT>(a, cs, sc, cur * tile, nxt < ntiles ? nxt * tile : -1, cnt);
-            cur = nxt;
-        }
-    } else {
-        for (int64_t base = (int64_t)blockIdx.x * tile; base < a.n; base += (int64_t)gridDim.x * tile)
-            score_tile<PM, COUNT, GPT>(a, cs, sc, base, base + (int64_t)gridDim.x * tile, cnt);
+    // Every warp takes its own tiles of 32 * GPT primitives from a counter,
+    // one ahead (the records of the next are pulled towards L2 while the
+    // current one is scored): warps that draw cheap tiles take more of them,
+    // and no warp waits for the others of its CTA.  Tile indices stay below
+    // 2^31 (n <= INT32_MAX).
+    const int lane = threadIdx.x & 31;
+    const int ntiles = (int)((a.n + 32 * GPT - 1) / (32 * GPT));
+    int cur = 0;
+    if (lane == 0) cur = (int)min((unsigned long long)ntiles, atomicAdd(a.tiles_taken, 1ull));
+    cur = __shfl_sync(0xffffffffu, cur, 0);
+    while (cur < ntiles) {
+        int nxt = 0;
+        if (lane == 0) nxt = (int)min((unsigned long long)ntiles, atomicAdd(a.tiles_taken, 1ull));
+        nxt = __shfl_sync(0xffffffffu, nxt, 0);
+        score_tile<PM, COUNT, GPT>(a, cs, sc, (int64_t)cur * (32 * GPT),
+                                   nxt < ntiles ? (int64_t)nxt * (32 * GPT) : -1, cnt);
+        cur = nxt;
     }
     if (COUNT) {
-        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int k = 0; k < kCountSlots; ++k) {
             unsigned long long v = cnt[k];
@@ -892,12 +887,13 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLau
         }
         const SceneConsts sc = *a.consts;
         const int pm = proj_mode(a.flags);
+        const int64_t wbase = base + (int64_t)(threadIdx.x >> 5) * 32 * GPT;  // this warp's part of the item
         if (pm == kProjEq17)
-            score_tile<kProjEq17, false, GPT>(a, cs, sc, base, -1, cnt);
+            score_tile<kProjEq17, false, GPT>(a, cs, sc, wbase, -1, cnt);
         else if (pm == kProjNone)
-            score_tile<kProjNone, false, GPT>(a, cs, sc, base, -1, cnt);
+            score_tile<kProjNone, false, GPT>(a, cs, sc, wbase, -1, cnt);
         else
-            score_tile<kProjFullJ, false, GPT>(a, cs, sc, base, -1, cnt);
+            score_tile<kProjFullJ, false, GPT>(a, cs, sc, wbase, -1, cnt);
         __syncthreads();  // the cameras and s_scene are free again
     }
 }
