@@ -26,7 +26,10 @@ struct ScoreShape {
     int ctas_per_sm = 0;  // cap on resident CTAs per SM of the batched kernel (0 = as many as fit)
 };
 bool shape_valid(const ScoreShape &sh);
-inline int64_t batch_tile(const ScoreShape &sh) { return (int64_t)sh.threads * sh.gpt; }
+// An item of the batched kernel: kBatchRounds warp tiles per warp of the
+// CTA, of one scene; the CTA's warps share them out dynamically.
+constexpr int kBatchRounds = 4;
+inline int64_t batch_tile(const ScoreShape &sh) { return (int64_t)sh.threads * sh.gpt * kBatchRounds; }
 constexpr int kFeatThreads = 256;
 
 // Spatial cells for the processing order of k_score: a 2^b x 2^b x 2^b grid

@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLau
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_scene, s_ok;
+    __shared__ int s_scene, s_ok, s_wt;
     __shared__ long long s_base;
     CamRec *cs = reinterpret_cast<CamRec *>(smem_raw);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -834,9 +834,11 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLau
     unsigned long long cnt[kCountSlots];
     int cur = -1;
     uint32_t phase = 0;
-    const int64_t tile = (int64_t)blockDim.x * GPT;
+    const int lane = threadIdx.x & 31;
+    const int64_t tile = (int64_t)THREADS * GPT * kBatchRounds;  // primitives per item
     for (;;) {
         if (threadIdx.x == 0) {
+            s_wt = 0;
             const unsigned long long item = atomicAdd(b.counter, 1ull);
             int sidx = -1;
             long long base = 0;
@@ -887,14 +889,22 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLau
         }
         const SceneConsts sc = *a.consts;
         const int pm = proj_mode(a.flags);
-        const int64_t wbase = base + (int64_t)(threadIdx.x >> 5) * 32 * GPT;  // this warp's part of the item
-        if (pm == kProjEq17)
-            score_tile<kProjEq17, false, GPT>(a, cs, sc, wbase, -1, cnt);
-        else if (pm == kProjNone)
-            score_tile<kProjNone, false, GPT>(a, cs, sc, wbase, -1, cnt);
-        else
-            score_tile<kProjFullJ, false, GPT>(a, cs, sc, wbase, -1, cnt);
-        __syncthreads();  // the cameras and s_scene are free again
+        // the item's warp tiles go to whichever warp of the CTA is free
+        const int wtiles = (int)((min(tile, a.n - base) + 32 * GPT - 1) / (32 * GPT));
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&s_wt, 1);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= wtiles) break;
+            const int64_t wbase = base + (int64_t)t * (32 * GPT);
+            if (pm == kProjEq17)
+                score_tile<kProjEq17, false, GPT>(a, cs, sc, wbase, -1, cnt);
+            else if (pm == kProjNone)
+                score_tile<kProjNone, false, GPT>(a, cs, sc, wbase, -1, cnt);
+            else
+                score_tile<kProjFullJ, false, GPT>(a, cs, sc, wbase, -1, cnt);
+        }
+        __syncthreads();  // the cameras, s_scene and s_wt are free again
     }
 }
 
