@@ -33,14 +33,16 @@ def upload(torch, rb, w):
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_batch_equals_single(env, dtype):
     torch, rb, ctx = env
-    specs = [(11, 3000, 7), (12, 40_000, 50), (13, 257, 3), (14, 123_457, 120), (15, 1, 1), (16, 70_001, 300)]
+    # the last scene is large enough for the single-scene compaction's segment form
+    specs = [(11, 3000, 7), (12, 40_000, 50), (13, 257, 3), (14, 123_457, 120), (15, 1, 1), (16, 70_001, 300),
+             (17, 1_900_003, 6)]
     ws = []
     for seed, n, v in specs:
         w = synth.random_scene(seed=seed, n=n, v=v, means="core_shell")
         if dtype == "bf16":
             w.scene = w.scene.to_bf16()
         ws.append(w)
-    ratios = [0.5, 0.66, 0.9, 0.0, 0.5, 0.3]
+    ratios = [0.5, 0.66, 0.9, 0.0, 0.5, 0.3, 0.5]
     up = [upload(torch, rb, w) for w in ws]
     jobs = [{"pos": p, "attr": a, "cams": c, "ratio": r} for (p, a, c), r in zip(up, ratios)]
     batch = rb.Batch(ctx, jobs)
