@@ -243,7 +243,7 @@ struct SceneScratch {
     double *partials;
     SceneConsts *consts;
     SceneStats *stats;
-    uint32_t *cell;
+    uint2 *cell;  // (cell, slot within the cell) of every primitive
     unsigned *counts;  // cell_count(bits) + 64 words; the last ones hold the scan's done counter
     unsigned *off_local;
     unsigned *bsum;
@@ -271,7 +271,7 @@ inline size_t scene_bytes(const ScenePlan &pl)
 {
     const size_t n = (size_t)pl.n, cells = (size_t)cell_count(pl.bits);
     return carve_size({sizeof(CamRec) * (size_t)pl.V, sizeof(PrimRec) * n, sizeof(double) * kFeatSums * 1024,
-                       sizeof(SceneConsts), sizeof(SceneStats), sizeof(uint32_t) * n,
+                       sizeof(SceneConsts), sizeof(SceneStats), sizeof(uint2) * n,
                        sizeof(unsigned) * (cells + 64), sizeof(unsigned) * cells,
                        sizeof(unsigned) * (cells / kScanThreads), sizeof(uint32_t) * n,
                        kCountSlots * sizeof(unsigned long long), sizeof(unsigned long long),
@@ -288,7 +288,7 @@ inline SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
     x.partials = cv.take<double>(kFeatSums * 1024);
     x.consts = cv.take<SceneConsts>(1);
     x.stats = cv.take<SceneStats>(1);
-    x.cell = cv.take<uint32_t>(n);
+    x.cell = cv.take<uint2>(n);
     x.counts = cv.take<unsigned>(cells + 64);
     x.off_local = cv.take<unsigned>(cells);
     x.bsum = cv.take<unsigned>(cells / kScanThreads);
@@ -329,7 +329,7 @@ inline refine_status enqueue_prep(refine_ctx *c, L &&run, const refine_scene *sc
                   [&] { return launch_cell_scan(x.counts, x.off_local, x.bsum, x.counts + cells, pl.bits, s); })))
         return st;
     return run(K_CELL_SCATTER,
-               [&] { return launch_cell_scatter(x.cell, n, x.counts, x.off_local, x.bsum, x.perm, c->num_sms, s); });
+               [&] { return launch_cell_scatter(x.cell, n, x.off_local, x.bsum, x.perm, c->num_sms, s); });
 }
 
 inline ScoreLaunch make_score_launch(const refine_scene *sc, const ScenePlan &pl, const SceneScratch &x,

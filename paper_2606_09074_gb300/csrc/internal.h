@@ -104,10 +104,10 @@ cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_
                                      const refine_params *p, int cell_bits, SceneConsts *consts,
                                      SceneStats *stats, cudaStream_t s);
 cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, int cell_bits, const SceneConsts *consts,
-                         uint32_t *cell, unsigned *counts, int num_sms, cudaStream_t s);
+                         uint2 *cell, unsigned *counts, int num_sms, cudaStream_t s);
 cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done, int cell_bits,
                              cudaStream_t s);
-cudaError_t launch_cell_scatter(const uint32_t *cell, int64_t n, unsigned *counts,
+cudaError_t launch_cell_scatter(const uint2 *cell, int64_t n,
                                 const unsigned *off_local, const unsigned *bsum, uint32_t *perm,
                                 int num_sms, cudaStream_t s);
 cudaError_t launch_score(const ScoreLaunch &a, const ScoreShape &sh, cudaStream_t s);

@@ -202,7 +202,7 @@ cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_
 // each view's frustum edges.  The order only affects speed: every
 // primitive's score is computed by one thread with the views in a fixed
 // order, whatever its position, so the sort need not be stable (the
-// scatter's atomics order the primitives of a cell arbitrarily).  Each
+// count atomics order the primitives of a cell arbitrarily).  Each
 // thread keeps kSortU primitives in flight.
 // ---------------------------------------------------------------------
 constexpr int kSortU = 4;
@@ -221,7 +221,7 @@ __device__ __forceinline__ uint32_t quantise(float x, float lo, float qs, float 
 }
 
 __global__ void k_cells(const float *__restrict__ pos, int64_t stride, int64_t n, int cell_bits,
-                        const SceneConsts *__restrict__ consts, uint32_t *__restrict__ cell,
+                        const SceneConsts *__restrict__ consts, uint2 *__restrict__ cell,
                         unsigned *__restrict__ counts)
 {
     const SceneConsts c = *consts;
@@ -244,8 +244,7 @@ __global__ void k_cells(const float *__restrict__ pos, int64_t stride, int64_t n
             const uint32_t id = spread3(quantise(x[u], c.lo[0], c.qscale[0], top)) |
                                 (spread3(quantise(y[u], c.lo[1], c.qscale[1], top)) << 1) |
                                 (spread3(quantise(z[u], c.lo[2], c.qscale[2], top)) << 2);
-            cell[j] = id;
-            atomicAdd(&counts[id], 1u);
+            cell[j] = make_uint2(id, atomicAdd(&counts[id], 1u));  // the cell and the slot in it
         }
     }
 }
@@ -259,7 +258,7 @@ static int sort_grid(int num_sms, int64_t n)
 }
 
 cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, int cell_bits, const SceneConsts *consts,
-                         uint32_t *cell, unsigned *counts, int num_sms, cudaStream_t s)
+                         uint2 *cell, unsigned *counts, int num_sms, cudaStream_t s)
 {
     k_cells<<<sort_grid(num_sms, n), 256, 0, s>>>(pos, stride, n, cell_bits, consts, cell, counts);
     return cudaGetLastError();
@@ -333,36 +332,31 @@ cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bs
     return cudaGetLastError();
 }
 
-__global__ void k_cell_scatter(const uint32_t *__restrict__ cell, int64_t n, unsigned *counts,
-                               const unsigned *__restrict__ off_local, const unsigned *__restrict__ boff,
-                               uint32_t *__restrict__ perm)
+// Primitive j goes to the start of its cell (block offset + offset within
+// the block) plus the slot that its count atomic returned in k_cells.
+__global__ void k_cell_scatter(const uint2 *__restrict__ cell, int64_t n, const unsigned *__restrict__ off_local,
+                               const unsigned *__restrict__ boff, uint32_t *__restrict__ perm)
 {
     const int64_t step = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += kSortU * step) {
-        uint32_t c[kSortU], slot[kSortU];
+        uint2 c[kSortU];
 #pragma unroll
         for (int u = 0; u < kSortU; ++u) {
             const int64_t j = i + u * step;
-            c[u] = j < n ? __ldg(cell + j) : 0u;
+            c[u] = j < n ? __ldg(cell + j) : make_uint2(0u, 0u);
         }
 #pragma unroll
         for (int u = 0; u < kSortU; ++u) {
             const int64_t j = i + u * step;
-            if (j < n) slot[u] = atomicSub(&counts[c[u]], 1u) - 1u;
-        }
-#pragma unroll
-        for (int u = 0; u < kSortU; ++u) {
-            const int64_t j = i + u * step;
-            if (j < n) perm[boff[c[u] / kScanThreads] + off_local[c[u]] + slot[u]] = (uint32_t)j;
+            if (j < n) perm[__ldg(boff + c[u].x / kScanThreads) + __ldg(off_local + c[u].x) + c[u].y] = (uint32_t)j;
         }
     }
 }
 
-cudaError_t launch_cell_scatter(const uint32_t *cell, int64_t n, unsigned *counts,
-                                const unsigned *off_local, const unsigned *bsum, uint32_t *perm,
-                                int num_sms, cudaStream_t s)
+cudaError_t launch_cell_scatter(const uint2 *cell, int64_t n, const unsigned *off_local, const unsigned *bsum,
+                                uint32_t *perm, int num_sms, cudaStream_t s)
 {
-    k_cell_scatter<<<sort_grid(num_sms, n), 256, 0, s>>>(cell, n, counts, off_local, bsum, perm);
+    k_cell_scatter<<<sort_grid(num_sms, n), 256, 0, s>>>(cell, n, off_local, bsum, perm);
     return cudaGetLastError();
 }
 

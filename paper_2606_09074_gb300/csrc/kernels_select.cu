@@ -268,7 +268,10 @@ cudaError_t launch_select_ties(const float *scores, int64_t n, SelState *st, uns
     return cudaGetLastError();
 }
 
-// Keep mask: one warp per 32-element word.
+// Keep mask: a warp builds kMaskWords consecutive 32-element words per
+// step, their loads issued together.
+constexpr int kMaskWords = 4;
+
 __global__ void k_select_mask(const float *__restrict__ scores, int64_t n, const SelState *st,
                               uint32_t *__restrict__ mask)
 {
@@ -278,15 +281,21 @@ __global__ void k_select_mask(const float *__restrict__ scores, int64_t n, const
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t w = warp0; w < words; w += nwarps) {
-        const int64_t i = w * 32 + lane;
-        bool keep = false;
-        if (i < n) {
-            const uint32_t k = score_key(__ldg(scores + i));
-            keep = k > kstar || (k == kstar && i <= cut);
+    for (int64_t w0 = warp0 * kMaskWords; w0 < words; w0 += nwarps * kMaskWords) {
+        float v[kMaskWords];
+#pragma unroll
+        for (int u = 0; u < kMaskWords; ++u) {
+            const int64_t i = (w0 + u) * 32 + lane;
+            v[u] = i < n ? __ldg(scores + i) : 0.f;
         }
-        const uint32_t word = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) mask[w] = word;
+#pragma unroll
+        for (int u = 0; u < kMaskWords; ++u) {
+            const int64_t i = (w0 + u) * 32 + lane;
+            const uint32_t k = score_key(v[u]);
+            const bool keep = i < n && (k > kstar || (k == kstar && i <= cut));
+            const uint32_t word = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0 && w0 + u < words) mask[w0 + u] = word;
+        }
     }
 }
 
