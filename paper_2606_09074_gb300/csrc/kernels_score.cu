@@ -152,38 +152,52 @@ __global__ void __launch_bounds__(32 * kFeatSums) k_features_finalize(const doub
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[k][0] = v;
     __syncthreads();
-    if (threadIdx.x != 0) return;
+    // The scalar tail in double, spread over three threads: thread t forms
+    // lambda~ of attribute t (Eq. 18), then its lambda, kappa (Eq. 19) and
+    // the grid box along axis t, each by the same expression as a one-thread
+    // evaluation would use.
+    __shared__ double lam_t[3];
+    const int t = threadIdx.x;
     const double N = (double)n;
-    SceneStats st;
-    const double ybar = red[0][0] / N;
-    st.F_col = red[1][0] / N - ybar * ybar;
-    if (st.F_col < 0.0) st.F_col = 0.0;
-    st.F_opa = red[2][0] / N;
-    st.F_gem = red[3][0] / N;
-    for (int k = 0; k < 3; ++k) st.mean_m[k] = red[4 + k][0] / N;
-    st.lambda_t[0] = log(st.F_gem + (double)p.eta) / p.e_ln_gem;
-    st.lambda_t[1] = st.F_col / p.e_col;
-    st.lambda_t[2] = st.F_opa / p.e_opa;
-    double tot = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        if (!(st.lambda_t[k] > 0.0)) st.lambda_t[k] = 0.0;
-        tot += st.lambda_t[k];
+    if (t < 3) {
+        double lt;
+        if (t == 0) {
+            lt = log(red[3][0] / N + (double)p.eta) / p.e_ln_gem;
+        } else if (t == 1) {
+            const double ybar = red[0][0] / N;
+            double fc = red[1][0] / N - ybar * ybar;
+            if (fc < 0.0) fc = 0.0;
+            lt = fc / p.e_col;
+            if (stats) stats->F_col = fc;
+        } else {
+            lt = (red[2][0] / N) / p.e_opa;
+        }
+        if (!(lt > 0.0)) lt = 0.0;
+        lam_t[t] = lt;
     }
-    SceneConsts c;
-    for (int k = 0; k < 3; ++k) {
-        st.lambda[k] = ((p.flags & REFINE_FLAG_EQUAL_LAMBDA) || tot == 0.0) ? 1.0 / 3.0 : st.lambda_t[k] / tot;
-        double kap = st.lambda[k];
-        if (p.flags & REFINE_FLAG_NORM_ATTR) kap = st.mean_m[k] > 0.0 ? st.lambda[k] / st.mean_m[k] : 0.0;
-        c.kappa[k] = (float)kap;
-        const double mean = red[7 + k][0] / N;
-        double var = red[10 + k][0] / N - mean * mean;
-        const double sd = var > 0.0 ? sqrt(var) : 0.0;
-        c.lo[k] = (float)(mean - 3.0 * sd);
-        c.qscale[k] = sd > 0.0 && isfinite(sd) ? (float)((1 << cell_bits) / (6.0 * sd)) : 0.f;
-        c.pad[k] = 0.f;
+    __syncthreads();
+    if (t >= 3) return;
+    const double tot = (lam_t[0] + lam_t[1]) + lam_t[2];
+    const double lambda = ((p.flags & REFINE_FLAG_EQUAL_LAMBDA) || tot == 0.0) ? 1.0 / 3.0 : lam_t[t] / tot;
+    const double mean_m = red[4 + t][0] / N;
+    double kap = lambda;
+    if (p.flags & REFINE_FLAG_NORM_ATTR) kap = mean_m > 0.0 ? lambda / mean_m : 0.0;
+    consts->kappa[t] = (float)kap;
+    const double mean = red[7 + t][0] / N;
+    const double var = red[10 + t][0] / N - mean * mean;
+    const double sd = var > 0.0 ? sqrt(var) : 0.0;
+    consts->lo[t] = (float)(mean - 3.0 * sd);
+    consts->qscale[t] = sd > 0.0 && isfinite(sd) ? (float)((1 << cell_bits) / (6.0 * sd)) : 0.f;
+    consts->pad[t] = 0.f;
+    if (stats) {
+        stats->lambda_t[t] = lam_t[t];
+        stats->lambda[t] = lambda;
+        stats->mean_m[t] = mean_m;
+        if (t == 0) {
+            stats->F_opa = red[2][0] / N;
+            stats->F_gem = red[3][0] / N;
+        }
     }
-    *consts = c;
-    if (stats) *stats = st;
 }
 
 cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_t n,

@@ -364,13 +364,27 @@ __global__ void __launch_bounds__(kCmpThreads) k_compact_count(const uint32_t *_
     __syncthreads();
     if (!is_last) return;
     __threadfence();
+    // thread t takes kCmpScanU consecutive segment counts per chunk (read
+    // from L2, where the other blocks' counts are)
+    constexpr int kCmpScanU = 4;
     unsigned long long run = 0;
     __shared__ unsigned long long chunk_end;
-    for (int64_t c0 = 0; c0 < nseg; c0 += blockDim.x) {
-        const int64_t sg = c0 + threadIdx.x;
-        const unsigned long long v = sg < nseg ? atomicAdd(&seg_cnt[sg], 0u) : 0ull;
-        const unsigned long long incl = block_prefix_sum(v, wsum) + run;
-        if (sg < nseg) seg_off[sg] = incl - v;
+    for (int64_t c0 = 0; c0 < nseg; c0 += (int64_t)blockDim.x * kCmpScanU) {
+        const int64_t sg0 = c0 + (int64_t)threadIdx.x * kCmpScanU;
+        unsigned v[kCmpScanU];
+        unsigned long long local = 0;
+#pragma unroll
+        for (int u = 0; u < kCmpScanU; ++u) {
+            v[u] = sg0 + u < nseg ? __ldcg(seg_cnt + sg0 + u) : 0u;
+            local += v[u];
+        }
+        const unsigned long long incl = block_prefix_sum(local, wsum) + run;
+        unsigned long long o = incl - local;
+#pragma unroll
+        for (int u = 0; u < kCmpScanU; ++u) {
+            if (sg0 + u < nseg) seg_off[sg0 + u] = o;
+            o += v[u];
+        }
         if (threadIdx.x == blockDim.x - 1) chunk_end = incl;
         __syncthreads();
         run = chunk_end;
