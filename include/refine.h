@@ -468,12 +468,17 @@ refine_status refine_read_ply(const char *path, int64_t *n_out, float *pos_host,
  * REFINE_OK, or the first error a kernel recorded since the last check. */
 refine_status refine_ctx_check(refine_ctx *ctx, refine_stream_t stream);
 
-/* Instrumentation.  When timing is enabled every kernel launch is
- * bracketed by CUDA events on its stream; refine_ctx_kernel_times
+/* Instrumentation.  With timing enabled kernel launches are bracketed by
+ * CUDA events on their stream: enable = REFINE_TIMING_ALL brackets every
+ * launch, REFINE_TIMING_SCORE only the score kernel's (two events per score
+ * pass, so that a timed loop is barely perturbed; each event pair costs
+ * about 2 us of stream time), 0 none.  refine_ctx_kernel_times
  * synchronises, then reports the accumulated device milliseconds and launch
  * counts per kernel class (names[i], ms[i], launches[i] for i < *count,
  * at most `cap` entries) and resets them.  refine_ctx_launch_count returns
  * the number of kernels the context has launched since creation. */
+#define REFINE_TIMING_ALL   1
+#define REFINE_TIMING_SCORE 2
 refine_status refine_ctx_set_timing(refine_ctx *ctx, int enable);
 refine_status refine_ctx_kernel_times(refine_ctx *ctx, const char **names, double *ms,
                                       int64_t *launches, int32_t cap, int32_t *count);

@@ -33,6 +33,8 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENONFINITE", 
                 6: "EBUSY", 7: "ECANCELLED", 8: "ENOTFOUND"}
 
 REFINE_F32 = 0
+TIMING_ALL = 1    # REFINE_TIMING_ALL
+TIMING_SCORE = 2  # REFINE_TIMING_SCORE
 REFINE_BF16 = 1
 
 FLAG_NO_VIS = 1 << 0
@@ -362,8 +364,11 @@ class Context:
     def status(self, stream=None) -> int:
         return refine_ctx_check(self.handle, _stream_handle(stream, self.device))  # noqa: F821
 
-    def set_timing(self, on: bool):
-        refine_ctx_set_timing(self.handle, 1 if on else 0)  # noqa: F821
+    def set_timing(self, on, score_only: bool = False):
+        """Brackets kernel launches with CUDA events: every launch, or only
+        the score kernel's (score_only: two events per pass)."""
+        mode = 0 if not on else (TIMING_SCORE if score_only else TIMING_ALL)
+        _check(self.handle, refine_ctx_set_timing(self.handle, mode))  # noqa: F821
 
     def kernel_times(self) -> dict:
         cap = 32

@@ -87,7 +87,7 @@ struct refine_ctx {
     int *d_status = nullptr;
     void *h_small = nullptr;  // pinned 4 KB for read-backs
     refine_api::Arena score, select, compact, host;
-    bool timing = false;
+    int timing = 0;  // 0, REFINE_TIMING_ALL or REFINE_TIMING_SCORE
     std::vector<refine_api::Pending> pending;
     std::vector<cudaEvent_t> pool;
     double ms[refine_api::K_NCLASS] = {0};
@@ -164,13 +164,14 @@ template <typename F>
 inline refine_status launch(refine_ctx *c, int cls, cudaStream_t s, F &&f)
 {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (c->timing) {
+    const bool timed = c->timing == REFINE_TIMING_ALL || (c->timing == REFINE_TIMING_SCORE && cls == K_SCORE);
+    if (timed) {
         a = take_event(c);
         cudaEventRecord(a, s);
     }
     cudaError_t e = f();
     if (e != cudaSuccess) return cuda_fail(c, e, kClassName[cls]);
-    if (c->timing) {
+    if (timed) {
         b = take_event(c);
         cudaEventRecord(b, s);
         c->pending.push_back({cls, a, b});

@@ -240,7 +240,9 @@ refine_status refine_ctx_check(refine_ctx *c, refine_stream_t stream)
 refine_status refine_ctx_set_timing(refine_ctx *c, int enable)
 {
     if (!c) return REFINE_EINVAL;
-    c->timing = enable != 0;
+    if (enable != 0 && enable != REFINE_TIMING_ALL && enable != REFINE_TIMING_SCORE)
+        return fail(c, REFINE_EINVAL, "set_timing: 0, REFINE_TIMING_ALL or REFINE_TIMING_SCORE");
+    c->timing = enable;
     return REFINE_OK;
 }
 

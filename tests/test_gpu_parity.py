@@ -422,3 +422,27 @@ def test_max_views_in_batch_and_queue(torch, rb, ctx):
         assert np.array_equal(np.asarray(out["scores"]).view(np.uint32), ref.cpu().numpy().view(np.uint32))
     finally:
         q.close()
+
+
+def test_timing_modes(torch, rb, ctx):
+    """Kernel timing brackets every launch, or only the score kernel's, and
+    reports per-class device times; other modes are refused."""
+    w = synth.config0(seed=8)
+    dev = torch.device("cuda", 0)
+    pos = torch.from_numpy(w.scene.pos).to(dev)
+    attr = torch.from_numpy(w.scene.attr).to(dev)
+    cams = rb.cameras_to_device(w.cams, dev)
+    ctx.kernel_times()
+    ctx.set_timing(True, score_only=True)
+    s = ctx.score(pos, attr, cams)
+    ctx.select(s, 0.5)
+    ctx.set_timing(False)
+    kt = ctx.kernel_times()
+    assert set(kt) == {"score"} and kt["score"]["launches"] == 1 and kt["score"]["ms"] > 0
+    ctx.set_timing(True)
+    s = ctx.score(pos, attr, cams)
+    ctx.select(s, 0.5)
+    ctx.set_timing(False)
+    kt = ctx.kernel_times()
+    assert {"features", "score", "select_mask"} <= set(kt) and all(v["ms"] > 0 for v in kt.values())
+    assert rb.refine_ctx_set_timing(ctx.handle, 3) == rb.REFINE_EINVAL
