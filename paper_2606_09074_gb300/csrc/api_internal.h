@@ -274,7 +274,7 @@ inline size_t scene_bytes(const ScenePlan &pl)
     return carve_size({sizeof(CamRec) * (size_t)pl.V, sizeof(PrimRec) * n, sizeof(double) * kFeatSums * 1024,
                        sizeof(SceneConsts), sizeof(SceneStats), sizeof(uint2) * n,
                        sizeof(unsigned) * (cells + 64), sizeof(unsigned) * cells,
-                       sizeof(unsigned) * (cells / kScanThreads), sizeof(uint32_t) * n,
+                       sizeof(unsigned) * (cells / kScanCells), sizeof(uint32_t) * n,
                        kCountSlots * sizeof(unsigned long long), sizeof(unsigned long long),
                        pl.multipass ? sizeof(float) * n : 0});
 }
@@ -292,7 +292,7 @@ inline SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
     x.cell = cv.take<uint2>(n);
     x.counts = cv.take<unsigned>(cells + 64);
     x.off_local = cv.take<unsigned>(cells);
-    x.bsum = cv.take<unsigned>(cells / kScanThreads);
+    x.bsum = cv.take<unsigned>(cells / kScanCells);
     x.perm = cv.take<uint32_t>(n);
     x.need = cv.take<unsigned long long>(kCountSlots);
     x.tiles = cv.take<unsigned long long>(1);

@@ -41,6 +41,7 @@ constexpr int kFeatThreads = 256;
 constexpr int kMinCellBits = 4;
 constexpr int kMaxCellBits = 7;
 constexpr int kScanThreads = 1024;
+constexpr int kScanCells = 4 * kScanThreads;  // cells per block of the cell scan (4 per thread)
 inline int cell_bits_for(int64_t n)
 {
     int b = kMinCellBits;

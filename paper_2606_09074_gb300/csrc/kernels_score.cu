@@ -279,8 +279,9 @@ cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, int cell_b
 }
 
 // Exclusive scan of the cell counts: local offsets within blocks of
-// kScanThreads cells, then the last block turns the block totals into block
-// offsets, so cell c starts at bsum[c / kScanThreads] + off_local[c].
+// kScanCells cells (4 consecutive cells per thread, one 16-byte load), then
+// the last block turns the block totals into block offsets, so cell c
+// starts at bsum[c / kScanCells] + off_local[c].
 __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *wsum)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -314,11 +315,12 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(const unsigned *__re
     __shared__ unsigned wsum[32];
     __shared__ unsigned is_last, carry;
     const int nblocks = gridDim.x;
-    const int c = blockIdx.x * kScanThreads + threadIdx.x;
-    const unsigned v = counts[c];
-    const unsigned ex = block_excl_scan(v, wsum);
-    off_local[c] = ex;
-    if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = ex + v;
+    const int64_t c4 = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;  // 4 cells from 4 * c4
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(counts) + c4);
+    const unsigned tot = v.x + v.y + v.z + v.w;
+    const unsigned ex = block_excl_scan(tot, wsum);
+    reinterpret_cast<uint4 *>(off_local)[c4] = make_uint4(ex, ex + v.x, ex + v.x + v.y, ex + v.x + v.y + v.z);
+    if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = ex + tot;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = (atomicAdd(done, 1u) == gridDim.x - 1);
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(const unsigned *__re
     __syncthreads();
     for (int b0 = 0; b0 < nblocks; b0 += kScanThreads) {
         const int bi = b0 + threadIdx.x;
-        const unsigned b = bi < nblocks ? atomicAdd(&bsum[bi], 0u) : 0u;
+        const unsigned b = bi < nblocks ? __ldcg(bsum + bi) : 0u;
         const unsigned bex = block_excl_scan(b, wsum) + carry;
         __syncthreads();
         if (bi < nblocks) bsum[bi] = bex;
@@ -342,7 +344,7 @@ cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bs
                              cudaStream_t s)
 {
     const int cells = cell_count(cell_bits);
-    k_cell_scan<<<cells / kScanThreads, kScanThreads, 0, s>>>(counts, off_local, bsum, done);
+    k_cell_scan<<<cells / kScanCells, kScanThreads, 0, s>>>(counts, off_local, bsum, done);
     return cudaGetLastError();
 }
 
@@ -362,7 +364,7 @@ __global__ void k_cell_scatter(const uint2 *__restrict__ cell, int64_t n, const 
 #pragma unroll
         for (int u = 0; u < kSortU; ++u) {
             const int64_t j = i + u * step;
-            if (j < n) perm[__ldg(boff + c[u].x / kScanThreads) + __ldg(off_local + c[u].x) + c[u].y] = (uint32_t)j;
+            if (j < n) perm[__ldg(boff + c[u].x / kScanCells) + __ldg(off_local + c[u].x) + c[u].y] = (uint32_t)j;
         }
     }
 }
