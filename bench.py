@@ -380,6 +380,9 @@ def run_ours(args, rank: int, world: int):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": recorded_traffic("score", args.workload),
                 "kernel": "k_score", "kernel_ms": score_ms,
+                "flops_basis": f"{FLOPS_PER_PAIR} FLOP per (primitive, view) pair, every pair counted at the full "
+                               f"visibility test; the kernel's tile classification skips pairs whose outcome is "
+                               f"implied and shortens others, so frac can exceed 1",
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                               f"{clk_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
                 "kernels_ms_per_step": {k: v["ms"] / b_steps for k, v in kt_all.items()},
