@@ -226,6 +226,9 @@ def test_select_edge_inputs(torch, rb, ctx):
         "few_values": rng.integers(0, 4, 100003).astype(np.float32),
         "one": np.array([3.0], dtype=np.float32),
         "large_random": rng.random(1_000_003).astype(np.float32),
+        # ties at scale: the tie-break spans hundreds of 4096-element segments
+        "zeros_heavy_2m": np.where(rng.random(2_000_017) < 0.7, 0.0,
+                                   rng.integers(0, 50, 2_000_017) / 64.0).astype(np.float32),
     }
     for name, s in cases.items():
         for ratio in (0.0, 0.1, 0.5, 0.66, 0.9, 0.9999):
@@ -355,35 +358,48 @@ def test_padded_row_stride(torch, rb, ctx, dtype):
     assert torch.equal(i0, i1) and torch.equal(op0, op1) and torch.equal(oa0, oa1)
 
 
-@pytest.mark.parametrize("pattern,ratio,pad,opad", [("random", 0.5, 0, 0), ("random", 0.1, 37, 5),
-                                                     ("random", 0.97, 64, 0), ("blocks", 0.5, 3, 11)])
-def test_compact_large_fp32_ragged(torch, rb, ctx, pattern, ratio, pad, opad):
-    """FP32 scenes of about 1.9M primitives or more are scattered one warp
-    per 256-primitive segment: a ragged n (not a multiple of 32 or 256),
-    padded input and output rows, sparse and dense masks and masks with long
-    all-kept and all-pruned runs, bit-exact against the oracle's gather."""
+@pytest.mark.parametrize("dtype,pattern,ratio,pad,opad,with_idx", [
+    ("f32", "random", 0.5, 0, 0, True), ("f32", "random", 0.1, 37, 5, True), ("f32", "random", 0.97, 64, 0, True),
+    ("f32", "blocks", 0.5, 3, 11, True), ("f32", "random", 0.5, 0, 0, False), ("bf16", "random", 0.66, 9, 2, True)])
+def test_compact_large_ragged(torch, rb, ctx, dtype, pattern, ratio, pad, opad, with_idx):
+    """Scenes of about 1.9M primitives or more: FP32 rows are scattered one
+    warp per 256-primitive segment, BF16 rows one warp per mask word.  A
+    ragged n (not a multiple of 32 or 256), padded input and output rows,
+    sparse and dense masks, masks with long all-kept and all-pruned runs, and
+    no index output: all bit-exact against the oracle's gather."""
     n = 2_000_003
     rng = np.random.default_rng(4242 + pad)
     pos_h = rng.standard_normal((3, n), dtype=np.float32)
     attr_h = rng.standard_normal((56, n), dtype=np.float32)
+    if dtype == "bf16":
+        attr_h = synth.f32_to_bf16_bits(attr_h)  # uint16 bit patterns
     scores = rng.random(n, dtype=np.float32)
     if pattern == "blocks":
         scores += ((np.arange(n) // 700) % 3).astype(np.float32)
     dev = torch.device("cuda", 0)
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
     pos_p = torch.zeros((3, n + pad), dtype=torch.float32, device=dev)
-    attr_p = torch.zeros((56, n + pad), dtype=torch.float32, device=dev)
+    attr_p = torch.zeros((56, n + pad), dtype=tdt, device=dev)
     pos_p[:, :n] = torch.from_numpy(pos_h).to(dev)
-    attr_p[:, :n] = torch.from_numpy(attr_h).to(dev)
+    if dtype == "bf16":
+        attr_p[:, :n] = torch.from_numpy(attr_h.view(np.int16)).to(dev).view(torch.bfloat16)
+    else:
+        attr_p[:, :n] = torch.from_numpy(attr_h).to(dev)
     m, _, nk = ctx.select(torch.from_numpy(scores).to(dev), ratio)
     op, oa, idx, cnt = ctx.compact(pos_p[:, :n], attr_p[:, :n], m, nk, out_row_stride=nk + opad,
-                                   return_count=True)
+                                   kept_idx=with_idx, return_count=True)
     words = m.cpu().numpy().view(np.uint32)[: (n + 31) // 32]
     kp, ki = oracle.compact(pos_h, words)
     ka, _ = oracle.compact(attr_h, words)
     assert cnt == nk == n - int(np.floor(ratio * n))
-    assert np.array_equal(idx.cpu().numpy(), ki)
+    if with_idx:
+        assert np.array_equal(idx.cpu().numpy(), ki)
+    else:
+        assert idx is None
     assert np.array_equal(op[:, :nk].cpu().numpy(), kp[:, :nk])
-    assert np.array_equal(oa[:, :nk].cpu().numpy(), ka[:, :nk])
+    got = oa[:, :nk].cpu()
+    got = got.view(torch.int16).numpy().view(np.uint16) if dtype == "bf16" else got.numpy()
+    assert np.array_equal(got, ka[:, :nk])
 
 
 @pytest.mark.parametrize("v,mv", [(250, 64), (150, 64), (64, 64), (10, 3), (7, 1)])
