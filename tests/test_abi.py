@@ -71,7 +71,6 @@ int main(void) {
 
 
 def test_camera_dtype_matches_struct():
-    import numpy as np
     from paper_2606_09074_gb300 import binding as b, synth
     assert synth.CAMERA_DTYPE.itemsize == ctypes.sizeof(b.refine_camera)
     assert synth.CAMERA_DTYPE.fields["width"][1] == b.refine_camera.width.offset
