@@ -134,6 +134,17 @@ typedef struct refine_scene_stats {
     int64_t bound_pairs;     /* of those: centre in the depth range but outside the image  */
     int64_t footprint_pairs; /* of those: within the conservative footprint radius, so the
                                 exact J W Sigma W^T J^T test decided them                  */
+    int64_t visible_mixed_pairs; /* pairs decided one by one and found visible             */
+    int64_t open_u_pairs;    /* pairs decided one by one whose tile left 0 < u < w open    */
+    int64_t open_v_pairs;    /* ... 0 < v < h open                                        */
+    int64_t open_z_pairs;    /* ... znear < z < zfar open                                 */
+    int64_t bound_u_pairs;   /* bound-stage pairs with 0 < u < w open                     */
+    int64_t bound_v_pairs;   /* bound-stage pairs with 0 < v < h open                     */
+    int64_t exact_u_pairs;   /* exact-test pairs whose centre lies beyond 0 < u < w, so
+                                the u extent of the footprint was formed                  */
+    int64_t exact_v_pairs;   /* ... beyond 0 < v < h, the v extent formed                 */
+    int64_t exact_warp_axes; /* warp-level evaluations of one extent of the exact test
+                                (32 lanes each): how densely the exact test ran           */
 } refine_scene_stats;
 
 typedef struct refine_ctx refine_ctx;

@@ -67,19 +67,25 @@ class refine_params(C.Structure):
                 ("max_views", C.c_int32)]
 
 
+_WORK_COUNTERS = ("visible_mixed_pairs", "open_u_pairs", "open_v_pairs", "open_z_pairs", "bound_u_pairs",
+                  "bound_v_pairs", "exact_u_pairs", "exact_v_pairs", "exact_warp_axes")
+
+
 class refine_scene_stats(C.Structure):
     _fields_ = [("F_col", C.c_double), ("F_opa", C.c_double), ("F_gem", C.c_double),
                 ("lambda_t", C.c_double * 3), ("lambda_", C.c_double * 3), ("mean_m", C.c_double * 3),
                 ("pairs", C.c_int64), ("tile_views", C.c_int64), ("in_pairs", C.c_int64),
                 ("out_pairs", C.c_int64), ("mixed_pairs", C.c_int64), ("bound_pairs", C.c_int64),
-                ("footprint_pairs", C.c_int64)]
+                ("footprint_pairs", C.c_int64)] + [(k, C.c_int64) for k in _WORK_COUNTERS]
 
     def as_dict(self):
-        return {"F_col": self.F_col, "F_opa": self.F_opa, "F_gem": self.F_gem,
-                "lambda_t": list(self.lambda_t), "lambda": list(self.lambda_),
-                "mean_m": list(self.mean_m), "pairs": self.pairs, "tile_views": self.tile_views,
-                "in_pairs": self.in_pairs, "out_pairs": self.out_pairs, "mixed_pairs": self.mixed_pairs,
-                "bound_pairs": self.bound_pairs, "footprint_pairs": self.footprint_pairs}
+        d = {"F_col": self.F_col, "F_opa": self.F_opa, "F_gem": self.F_gem,
+             "lambda_t": list(self.lambda_t), "lambda": list(self.lambda_),
+             "mean_m": list(self.mean_m), "pairs": self.pairs, "tile_views": self.tile_views,
+             "in_pairs": self.in_pairs, "out_pairs": self.out_pairs, "mixed_pairs": self.mixed_pairs,
+             "bound_pairs": self.bound_pairs, "footprint_pairs": self.footprint_pairs}
+        d.update({k: getattr(self, k) for k in _WORK_COUNTERS})
+        return d
 
 
 class refine_job(C.Structure):

@@ -245,7 +245,7 @@ struct SceneScratch {
     SceneConsts *consts;
     SceneStats *stats;
     uint2 *cell;  // (cell, slot within the cell) of every primitive
-    unsigned *counts;  // cell_count(bits) + 64 words; the last ones hold the scan's done counter
+    unsigned *counts;  // order_keys(bits) + 64 words; the last ones hold the scan's done counter
     unsigned *off_local;
     unsigned *bsum;
     uint32_t *perm;
@@ -270,7 +270,7 @@ inline ScenePlan plan_scene(int64_t n, int V, int max_views = 0)
 
 inline size_t scene_bytes(const ScenePlan &pl)
 {
-    const size_t n = (size_t)pl.n, cells = (size_t)cell_count(pl.bits);
+    const size_t n = (size_t)pl.n, cells = (size_t)order_keys(pl.bits);
     return carve_size({sizeof(CamRec) * (size_t)pl.V, sizeof(PrimRec) * n, sizeof(double) * kFeatSums * 1024,
                        sizeof(SceneConsts), sizeof(SceneStats), sizeof(uint2) * n,
                        sizeof(unsigned) * (cells + 64), sizeof(unsigned) * cells,
@@ -282,7 +282,7 @@ inline size_t scene_bytes(const ScenePlan &pl)
 inline SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
 {
     const int64_t n = pl.n;
-    const int cells = cell_count(pl.bits);
+    const int cells = order_keys(pl.bits);
     SceneScratch x;
     x.cams = cv.take<CamRec>(pl.V);
     x.recs = cv.take<PrimRec>(n);
@@ -307,7 +307,7 @@ inline refine_status enqueue_prep(refine_ctx *c, L &&run, const refine_scene *sc
                            int *status, cudaStream_t s)
 {
     const int64_t n = pl.n;
-    const int cells = cell_count(pl.bits);
+    const int cells = order_keys(pl.bits);
     cudaError_t e = cudaMemsetAsync(x.counts, 0, sizeof(unsigned) * (cells + 64), s);
     if (e == cudaSuccess && count) e = cudaMemsetAsync(x.need, 0, kCountSlots * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
@@ -323,7 +323,8 @@ inline refine_status enqueue_prep(refine_ctx *c, L &&run, const refine_scene *sc
                   [&] { return launch_features_finalize(x.partials, pl.nb, n, &p, pl.bits, x.consts, x.stats, s); })))
         return st;
     if ((st = run(K_CELLS, [&] {
-             return launch_cells(sc->pos, sc->row_stride, n, pl.bits, x.consts, x.cell, x.counts, c->num_sms, s);
+             return launch_cells(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, pl.bits, x.consts, x.cell,
+                                 x.counts, c->num_sms, s);
          })))
         return st;
     if ((st = run(K_CELL_SCAN,

@@ -42,7 +42,8 @@ struct SceneConsts {
     float kappa[3];   // lambda^k / mean(m^k)  (or lambda^k without NORM_ATTR)
     float lo[3];      // grid origin (mean - 3 sigma per axis)
     float qscale[3];  // cells per unit length per axis
-    float pad[3];
+    float big_ls;     // ln s_max above which a primitive is ordered with the large ones
+    float pad[2];
 };
 
 // Scene statistics (host-visible copy of refine_scene_stats).
@@ -54,8 +55,9 @@ struct SceneStats {
 };
 
 // Number of float sums the content-feature pass reduces per block:
-// y, y^2, a(1-a), gem ratio, m_gem, m_col, m_opa, mu (3), mu^2 (3).
-constexpr int kFeatSums = 13;
+// y, y^2, a(1-a), gem ratio, m_gem, m_col, m_opa, mu (3), mu^2 (3), and
+// ln s_max with its square (for the size split of the processing order).
+constexpr int kFeatSums = 15;
 
 // Per-thread content-feature sums (kFeatSums of them) and a non-finite trap.
 struct FeatSums {
@@ -95,6 +97,9 @@ __device__ __forceinline__ void primitive_record(FeatSums &acc, float mx, float 
     acc.s[10] = fmaf(mx, mx, acc.s[10]);
     acc.s[11] = fmaf(my, my, acc.s[11]);
     acc.s[12] = fmaf(mz, mz, acc.s[12]);
+    const float lsmax = fmaxf(ls0, fmaxf(ls1, ls2));
+    acc.s[13] += lsmax;
+    acc.s[14] = fmaf(lsmax, lsmax, acc.s[14]);
     acc.bad = fmaf(mx + my + mz + ls0 + ls1 + ls2 + qw + qx + qy + qz + logit + sumsq, 0.f, acc.bad);
 
     const float qn2 = fmaf(qw, qw, fmaf(qx, qx, fmaf(qy, qy, qz * qz)));

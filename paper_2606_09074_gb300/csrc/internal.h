@@ -49,6 +49,11 @@ inline int cell_bits_for(int64_t n)
     return b;
 }
 inline int cell_count(int bits) { return 1 << (3 * bits); }
+// Keys of the processing order: the cell, plus cell_count(bits) for the
+// primitives with large scales (ln s_max > SceneConsts::big_ls), which
+// thereby follow all the others.
+inline int order_keys(int bits) { return 2 * cell_count(bits); }
+constexpr double kSizeSplitSd = 1.28;
 
 // Diagnostic counters of k_score (written only when ScoreLaunch::need is set).
 enum {
@@ -58,6 +63,15 @@ enum {
     kCntMixedPairs,    // pairs evaluated one by one
     kCntBoundPairs,    // of those: centre outside the image, in the depth range
     kCntExactPairs,    // of those: within the conservative footprint radius
+    kCntVisMixed,      // pairs evaluated one by one and found visible
+    kCntOpenX,         // pairs evaluated one by one with the u axis open (U computed)
+    kCntOpenY,         //   ... with the v axis open (V computed)
+    kCntOpenZ,         //   ... with the depth range open (compared)
+    kCntBoundX,        // bound-stage pairs with the u axis open
+    kCntBoundY,        // bound-stage pairs with the v axis open
+    kCntExactX,        // exact-stage pairs whose u extent was needed (centre beyond u)
+    kCntExactY,        // exact-stage pairs whose v extent was needed
+    kCntExactWarpAxes, // warp-level executions of one axis of the exact test
     kCountSlots
 };
 
@@ -104,8 +118,8 @@ cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64
 cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_t n,
                                      const refine_params *p, int cell_bits, SceneConsts *consts,
                                      SceneStats *stats, cudaStream_t s);
-cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, int cell_bits, const SceneConsts *consts,
-                         uint2 *cell, unsigned *counts, int num_sms, cudaStream_t s);
+cudaError_t launch_cells(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n, int cell_bits,
+                         const SceneConsts *consts, uint2 *cell, unsigned *counts, int num_sms, cudaStream_t s);
 cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done, int cell_bits,
                              cudaStream_t s);
 cudaError_t launch_cell_scatter(const uint2 *cell, int64_t n,

@@ -66,7 +66,7 @@ cudaError_t launch_cam_prep(const refine_camera *cams, int V, int vstride, CamRe
 // float and reduced per block in a fixed double tree.
 // ---------------------------------------------------------------------
 template <typename AT>
-__global__ void __launch_bounds__(kFeatThreads) k_features(const float *__restrict__ pos,
+__global__ void __launch_bounds__(kFeatThreads, 4) k_features(const float *__restrict__ pos,
                                                            const AT *__restrict__ attr, int64_t S, int64_t n,
                                                            float eta, float l0, float l1, float l2,
                                                            PrimRec *__restrict__ recs,
@@ -188,7 +188,15 @@ __global__ void __launch_bounds__(32 * kFeatSums) k_features_finalize(const doub
     const double sd = var > 0.0 ? sqrt(var) : 0.0;
     consts->lo[t] = (float)(mean - 3.0 * sd);
     consts->qscale[t] = sd > 0.0 && isfinite(sd) ? (float)((1 << cell_bits) / (6.0 * sd)) : 0.f;
-    consts->pad[t] = 0.f;
+    if (t < 2) consts->pad[t] = 0.f;
+    if (t == 0) {
+        // The primitives whose ln s_max lies above its scene mean + 1.28 sd
+        // (the largest ~10 % for a normal spread) are ordered after all the
+        // others, so that the tiles of the rest carry small footprint bounds.
+        const double ml = red[13][0] / N, vl = red[14][0] / N - ml * ml;
+        const double big = ml + kSizeSplitSd * (vl > 0.0 ? sqrt(vl) : 0.0);
+        consts->big_ls = isfinite(big) ? (float)big : INFINITY;
+    }
     if (stats) {
         stats->lambda_t[t] = lam_t[t];
         stats->lambda[t] = lambda;
@@ -213,7 +221,10 @@ cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_
 // 2^b grid over the mean +- 3 sigma box of the centres, cells numbered in
 // Morton order (a counting sort: count, scan, scatter), so that the 32
 // lanes of a warp hold nearby primitives and tend to take the same side of
-// each view's frustum edges.  The order only affects speed: every
+// each view's frustum edges.  The primitives with the largest scales (ln
+// s_max above SceneConsts::big_ls) come after all the others, in their own
+// cells, so that a tile's footprint bound (set by its largest s_max) is not
+// set by a few large primitives among small ones.  The order only affects speed: every
 // primitive's score is computed by one thread with the views in a fixed
 // order, whatever its position, so the sort need not be stable (the
 // count atomics order the primitives of a cell arbitrarily).  Each
@@ -234,15 +245,17 @@ __device__ __forceinline__ uint32_t quantise(float x, float lo, float qs, float 
     return (uint32_t)fminf(fmaxf((x - lo) * qs, 0.f), top);
 }
 
-__global__ void k_cells(const float *__restrict__ pos, int64_t stride, int64_t n, int cell_bits,
-                        const SceneConsts *__restrict__ consts, uint2 *__restrict__ cell,
+template <typename AT>
+__global__ void k_cells(const float *__restrict__ pos, const AT *__restrict__ attr, int64_t stride, int64_t n,
+                        int cell_bits, const SceneConsts *__restrict__ consts, uint2 *__restrict__ cell,
                         unsigned *__restrict__ counts)
 {
     const SceneConsts c = *consts;
     const float top = (float)((1 << cell_bits) - 1);
+    const uint32_t big_key = 1u << (3 * cell_bits);
     const int64_t step = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += kSortU * step) {
-        float x[kSortU], y[kSortU], z[kSortU];
+        float x[kSortU], y[kSortU], z[kSortU], ls[kSortU];
 #pragma unroll
         for (int u = 0; u < kSortU; ++u) {
             const int64_t j = i + u * step;
@@ -250,15 +263,18 @@ __global__ void k_cells(const float *__restrict__ pos, int64_t stride, int64_t n
             x[u] = ok ? __ldg(pos + j) : 0.f;
             y[u] = ok ? __ldg(pos + stride + j) : 0.f;
             z[u] = ok ? __ldg(pos + 2 * stride + j) : 0.f;
+            ls[u] = ok ? fmaxf(ld_attr(attr + j), fmaxf(ld_attr(attr + stride + j), ld_attr(attr + 2 * stride + j)))
+                       : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < kSortU; ++u) {
             const int64_t j = i + u * step;
             if (j >= n) break;
-            const uint32_t id = spread3(quantise(x[u], c.lo[0], c.qscale[0], top)) |
-                                (spread3(quantise(y[u], c.lo[1], c.qscale[1], top)) << 1) |
-                                (spread3(quantise(z[u], c.lo[2], c.qscale[2], top)) << 2);
-            cell[j] = make_uint2(id, atomicAdd(&counts[id], 1u));  // the cell and the slot in it
+            const uint32_t id = (spread3(quantise(x[u], c.lo[0], c.qscale[0], top)) |
+                                 (spread3(quantise(y[u], c.lo[1], c.qscale[1], top)) << 1) |
+                                 (spread3(quantise(z[u], c.lo[2], c.qscale[2], top)) << 2)) +
+                                (ls[u] > c.big_ls ? big_key : 0u);
+            cell[j] = make_uint2(id, atomicAdd(&counts[id], 1u));  // the key and the slot in it
         }
     }
 }
@@ -271,10 +287,15 @@ static int sort_grid(int num_sms, int64_t n)
     return (int)g;
 }
 
-cudaError_t launch_cells(const float *pos, int64_t stride, int64_t n, int cell_bits, const SceneConsts *consts,
-                         uint2 *cell, unsigned *counts, int num_sms, cudaStream_t s)
+cudaError_t launch_cells(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n, int cell_bits,
+                         const SceneConsts *consts, uint2 *cell, unsigned *counts, int num_sms, cudaStream_t s)
 {
-    k_cells<<<sort_grid(num_sms, n), 256, 0, s>>>(pos, stride, n, cell_bits, consts, cell, counts);
+    if (dtype == REFINE_BF16)
+        k_cells<__nv_bfloat16><<<sort_grid(num_sms, n), 256, 0, s>>>(
+            pos, static_cast<const __nv_bfloat16 *>(attr), stride, n, cell_bits, consts, cell, counts);
+    else
+        k_cells<float><<<sort_grid(num_sms, n), 256, 0, s>>>(pos, static_cast<const float *>(attr), stride, n,
+                                                             cell_bits, consts, cell, counts);
     return cudaGetLastError();
 }
 
@@ -343,8 +364,7 @@ __global__ void __launch_bounds__(kScanThreads) k_cell_scan(const unsigned *__re
 cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done, int cell_bits,
                              cudaStream_t s)
 {
-    const int cells = cell_count(cell_bits);
-    k_cell_scan<<<cells / kScanCells, kScanThreads, 0, s>>>(counts, off_local, bsum, done);
+    k_cell_scan<<<order_keys(cell_bits) / kScanCells, kScanThreads, 0, s>>>(counts, off_local, bsum, done);
     return cudaGetLastError();
 }
 
@@ -448,15 +468,25 @@ __device__ __forceinline__ Range form_range(const float4 &a, const TileBox &t)
     return {mid - rad - sl, mid + rad + sl};
 }
 
-// 0 = MIXED, 1 = IN, 2 = OUT for one view and one tile.
+// Class of one view for one tile: kClsMixed, kClsIn or kClsOut in the low two
+// bits; for MIXED also the axes whose test some centre of the tile may fail
+// (kAxX: 0 < u < w, kAxY: 0 < v < h, kAxZ: znear < z < zfar) above them.  An
+// axis that is not flagged holds for every centre of the tile, with the same
+// float32 slack as the IN class, so a pair's test on it needs no evaluation.
+enum { kClsMixed = 0, kClsIn = 1, kClsOut = 2 };
+enum { kAxX = 4, kAxY = 8, kAxZ = 16 };
+
 __device__ __forceinline__ int classify(const CamRec &c, const TileBox &t)
 {
     const Range z = form_range(c.r2, t);
-    if (z.hi < c.lim.z || z.lo > c.lim.w) return 2;
+    if (z.hi < c.lim.z || z.lo > c.lim.w) return kClsOut;
     const Range U = form_range(c.r0, t), V = form_range(c.r1, t);
     const Range UW = form_range(c.uw, t), VH = form_range(c.vh, t);
-    if (z.lo > c.lim.z && z.hi < c.lim.w && U.lo > 0.f && UW.hi < 0.f && V.lo > 0.f && VH.hi < 0.f) return 1;
-    if (!(z.lo > 0.f)) return 0;
+    const bool zin = z.lo > c.lim.z && z.hi < c.lim.w;
+    const bool xin = U.lo > 0.f && UW.hi < 0.f, yin = V.lo > 0.f && VH.hi < 0.f;
+    if (zin && xin && yin) return kClsIn;
+    const int mixed = kClsMixed | (xin ? 0 : kAxX) | (yin ? 0 : kAxY) | (zin ? 0 : kAxZ);
+    if (!(z.lo > 0.f)) return mixed;
     // outside an edge by more than the footprint bound (times z^2)
     const Range TX = form_range(c.tx, t), TY = form_range(c.ty, t);
     const float tx2 = fmaxf(TX.lo * TX.lo, TX.hi * TX.hi), ty2 = fmaxf(TY.lo * TY.lo, TY.hi * TY.hi);
@@ -465,8 +495,8 @@ __device__ __forceinline__ int classify(const CamRec &c, const TileBox &t)
     const float by = t.b2 * fmaf(c.k.y, zz, ty2) * 1.00390625f;
     const float dl = fmaxf(-U.hi, UW.lo) * z.lo;  // > 0 when the box is left or right of the image
     const float dt = fmaxf(-V.hi, VH.lo) * z.lo;
-    if ((dl > 0.f && dl * dl > bx) || (dt > 0.f && dt * dt > by)) return 2;
-    return 0;
+    if ((dl > 0.f && dl * dl > bx) || (dt > 0.f && dt * dt > by)) return kClsOut;
+    return mixed;
 }
 
 template <bool DET>
@@ -555,7 +585,12 @@ __device__ __forceinline__ void mixed_view(const CamRec &c, float eta, const Pai
         q[g] = pair_geom(c0, c1, c2, lim, p[g]);
         vis[g] = q[g].inside;
         out |= q[g].inz & !q[g].inside;
-        if (COUNT) cnt[kCntMixedPairs] += valid[g] ? 1 : 0;
+        if (COUNT && valid[g]) {
+            cnt[kCntMixedPairs] += 1;
+            cnt[kCntOpenX] += 1;
+            cnt[kCntOpenY] += 1;
+            cnt[kCntOpenZ] += 1;
+        }
     }
     if (DET || __any_sync(0xffffffffu, out)) {
         const float4 k = c.k;
@@ -567,20 +602,136 @@ __device__ __forceinline__ void mixed_view(const CamRec &c, float eta, const Pai
             const bool o = q[g].inz & !q[g].inside;
             nq[g] = o & (q[g].ex2 <= p[g].b2 * fmaf(k.x, zz, tx * tx)) & (q[g].ey2 <= p[g].b2 * fmaf(k.y, zz, ty * ty));
             nearq |= nq[g];
-            if (COUNT) {
-                cnt[kCntBoundPairs] += (valid[g] && o) ? 1 : 0;
-                cnt[kCntExactPairs] += (valid[g] && nq[g]) ? 1 : 0;
+            if (COUNT && valid[g]) {
+                cnt[kCntBoundPairs] += o ? 1 : 0;
+                cnt[kCntBoundX] += o ? 1 : 0;
+                cnt[kCntBoundY] += o ? 1 : 0;
+                cnt[kCntExactPairs] += nq[g] ? 1 : 0;
+                // the determinant path evaluates both extents of every pair
+                cnt[kCntExactX] += q[g].inz ? 1 : 0;
+                cnt[kCntExactY] += q[g].inz ? 1 : 0;
             }
         }
         if (DET || __any_sync(0xffffffffu, nearq)) {
 #pragma unroll
             for (int g = 0; g < GPT; ++g)
                 vis[g] = q[g].inz & exact_box<DET>(c0, c1, c2, q[g].U, q[g].V, q[g].z, q[g].ex2, q[g].ey2, p[g]);
+            if (COUNT && (threadIdx.x & 31) == 0) cnt[kCntExactWarpAxes] += 2 * GPT;
         }
     }
 #pragma unroll
-    for (int g = 0; g < GPT; ++g)
+    for (int g = 0; g < GPT; ++g) {
         part[g] += vis[g] ? weight<PM>(c, q[g].z, eta, p[g].mx, p[g].my, p[g].mz) : 0.f;
+        if (COUNT) cnt[kCntVisMixed] += (valid[g] && vis[g]) ? 1 : 0;
+    }
+}
+
+// A MIXED view of a tile without underflowed scales, evaluated only on the
+// axes its classification left open (NX: 0 < u < w, NY: 0 < v < h, NZ: the
+// depth range); an axis that holds for every centre of the tile contributes
+// d = 0 to the box test, which it then passes for every Sigma2D, so leaving
+// it out changes no decision.  The stages are those of the full test, with
+// the same expressions (so the same float32 roundings): the centre test; for
+// centres outside, the footprint bound; and the exact footprint test, entered
+// per primitive slot g and per axis only when some lane of the warp needs it
+// (a lane whose bound test failed, or whose centre lies within that axis's
+// interval, passes or fails it without evaluation).
+template <int PM, bool COUNT, int GPT, bool NX, bool NY, bool NZ>
+__device__ __forceinline__ void mixed_view_ax(const CamRec &c, float eta, const PairIn (&p)[GPT],
+                                              const bool (&valid)[GPT], float (&part)[GPT],
+                                              unsigned long long (&cnt)[kCountSlots])
+{
+    const float4 c2 = c.r2, lim = c.lim;
+    float z[GPT], U[GPT], V[GPT], du[GPT], dv[GPT];
+    bool vis[GPT], o[GPT], anyo = false;
+#pragma unroll
+    for (int g = 0; g < GPT; ++g) {
+        z[g] = fmaf(c2.x, p[g].mx, fmaf(c2.y, p[g].my, fmaf(c2.z, p[g].mz, c2.w)));
+        bool inside = NZ ? (z[g] > lim.z) & (z[g] < lim.w) : true;
+        const bool inz = inside;
+        if (NX) {
+            const float4 c0 = c.r0;
+            U[g] = fmaf(c0.x, p[g].mx, fmaf(c0.y, p[g].my, fmaf(c0.z, p[g].mz, c0.w)));
+            du[g] = fmaxf(-U[g], fmaf(-lim.x, z[g], U[g]));
+            inside &= du[g] <= 0.f;
+        }
+        if (NY) {
+            const float4 c1 = c.r1;
+            V[g] = fmaf(c1.x, p[g].mx, fmaf(c1.y, p[g].my, fmaf(c1.z, p[g].mz, c1.w)));
+            dv[g] = fmaxf(-V[g], fmaf(-lim.y, z[g], V[g]));
+            inside &= dv[g] <= 0.f;
+        }
+        vis[g] = inside;
+        o[g] = inz & !inside;
+        anyo |= o[g];
+        if (COUNT && valid[g]) {
+            cnt[kCntMixedPairs] += 1;
+            cnt[kCntOpenX] += NX ? 1 : 0;
+            cnt[kCntOpenY] += NY ? 1 : 0;
+            cnt[kCntOpenZ] += NZ ? 1 : 0;
+        }
+    }
+    if (__any_sync(0xffffffffu, anyo)) {
+        const float4 k = c.k;
+        float ex2[GPT], ey2[GPT];
+        bool nq[GPT];
+#pragma unroll
+        for (int g = 0; g < GPT; ++g) {
+            const float zz = z[g] * z[g];
+            bool ok = o[g];
+            if (NX) {
+                const float ex = fmaxf(du[g], 0.f) * z[g];
+                ex2[g] = ex * ex;
+                const float tx = fmaf(-k.z, z[g], U[g]);
+                ok &= ex2[g] <= p[g].b2 * fmaf(k.x, zz, tx * tx);
+            }
+            if (NY) {
+                const float ey = fmaxf(dv[g], 0.f) * z[g];
+                ey2[g] = ey * ey;
+                const float ty = fmaf(-k.w, z[g], V[g]);
+                ok &= ey2[g] <= p[g].b2 * fmaf(k.y, zz, ty * ty);
+            }
+            nq[g] = ok;
+            if (COUNT && valid[g]) {
+                cnt[kCntBoundPairs] += o[g] ? 1 : 0;
+                cnt[kCntBoundX] += (NX && o[g]) ? 1 : 0;
+                cnt[kCntBoundY] += (NY && o[g]) ? 1 : 0;
+                cnt[kCntExactPairs] += nq[g] ? 1 : 0;
+                cnt[kCntExactX] += (NX && nq[g] && ex2[g] > 0.f) ? 1 : 0;
+                cnt[kCntExactY] += (NY && nq[g] && ey2[g] > 0.f) ? 1 : 0;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < GPT; ++g) {
+            bool xt = true, yt = true;
+            if (NX && __any_sync(0xffffffffu, nq[g] & (ex2[g] > 0.f))) {
+                const float4 c0 = c.r0;
+                const float gx = fmaf(-U[g], c2.x, z[g] * c0.x), gy = fmaf(-U[g], c2.y, z[g] * c0.y),
+                            gz = fmaf(-U[g], c2.z, z[g] * c0.z);
+                const float a0 = fmaf(p[g].L[0], gx, fmaf(p[g].L[1], gy, p[g].L[2] * gz));
+                const float a1 = fmaf(p[g].L[3], gx, fmaf(p[g].L[4], gy, p[g].L[5] * gz));
+                const float a2 = fmaf(p[g].L[6], gx, fmaf(p[g].L[7], gy, p[g].L[8] * gz));
+                xt = ex2[g] <= fmaf(a0, a0, fmaf(a1, a1, a2 * a2));
+                if (COUNT && (threadIdx.x & 31) == 0) cnt[kCntExactWarpAxes] += 1;
+            }
+            if (NY && __any_sync(0xffffffffu, nq[g] & (ey2[g] > 0.f))) {
+                const float4 c1 = c.r1;
+                const float gx = fmaf(-V[g], c2.x, z[g] * c1.x), gy = fmaf(-V[g], c2.y, z[g] * c1.y),
+                            gz = fmaf(-V[g], c2.z, z[g] * c1.z);
+                const float b0 = fmaf(p[g].L[0], gx, fmaf(p[g].L[1], gy, p[g].L[2] * gz));
+                const float b1 = fmaf(p[g].L[3], gx, fmaf(p[g].L[4], gy, p[g].L[5] * gz));
+                const float b2 = fmaf(p[g].L[6], gx, fmaf(p[g].L[7], gy, p[g].L[8] * gz));
+                yt = ey2[g] <= fmaf(b0, b0, fmaf(b1, b1, b2 * b2));
+                if (COUNT && (threadIdx.x & 31) == 0) cnt[kCntExactWarpAxes] += 1;
+            }
+            vis[g] |= nq[g] & xt & yt;
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < GPT; ++g) {
+        part[g] += vis[g] ? weight<PM>(c, z[g], eta, p[g].mx, p[g].my, p[g].mz) : 0.f;
+        if (COUNT) cnt[kCntVisMixed] += (valid[g] && vis[g]) ? 1 : 0;
+    }
 }
 
 template <int PM, bool DET, bool COUNT, int GPT>
@@ -596,11 +747,14 @@ __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float et
     for (int vb = 0; vb < vcount; vb += 32) {
         const int nv = min(32, vcount - vb);
         const unsigned vmask = nv == 32 ? 0xffffffffu : ((1u << nv) - 1u);
-        unsigned in_m = 0u, out_m = 0u;
+        unsigned in_m = 0u, out_m = 0u, ux_m = 0u, uy_m = 0u, uz_m = 0u;
         if (!DET) {
-            const int cls = lane < nv ? classify(cs[vb + lane], tb) : 0;
-            in_m = __ballot_sync(0xffffffffu, cls == 1);
-            out_m = __ballot_sync(0xffffffffu, cls == 2);
+            const int cls = lane < nv ? classify(cs[vb + lane], tb) : (kAxX | kAxY | kAxZ);
+            in_m = __ballot_sync(0xffffffffu, (cls & 3) == kClsIn);
+            out_m = __ballot_sync(0xffffffffu, (cls & 3) == kClsOut);
+            ux_m = __ballot_sync(0xffffffffu, (cls & kAxX) != 0);
+            uy_m = __ballot_sync(0xffffffffu, (cls & kAxY) != 0);
+            uz_m = __ballot_sync(0xffffffffu, (cls & kAxZ) != 0);
             if (COUNT && lane == 0) {
                 cnt[kCntTiles] += nv;
                 cnt[kCntInPairs] += (unsigned long long)__popc(in_m & vmask) * nvalid;
@@ -626,8 +780,18 @@ __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float et
                         const float z = fmaf(c2.x, p[g].mx, fmaf(c2.y, p[g].my, fmaf(c2.z, p[g].mz, c2.w)));
                         part[g] += weight<PM>(c, z, eta, p[g].mx, p[g].my, p[g].mz);
                     }
+                } else if (DET) {
+                    mixed_view<PM, true, COUNT, GPT>(c, eta, p, valid, part, cnt);
                 } else {
-                    mixed_view<PM, DET, COUNT, GPT>(c, eta, p, valid, part, cnt);
+                    const unsigned bit = 1u << b;
+                    if (uz_m & bit)
+                        mixed_view_ax<PM, COUNT, GPT, true, true, true>(c, eta, p, valid, part, cnt);
+                    else if (ux_m & uy_m & bit)
+                        mixed_view_ax<PM, COUNT, GPT, true, true, false>(c, eta, p, valid, part, cnt);
+                    else if (ux_m & bit)
+                        mixed_view_ax<PM, COUNT, GPT, true, false, false>(c, eta, p, valid, part, cnt);
+                    else
+                        mixed_view_ax<PM, COUNT, GPT, false, true, false>(c, eta, p, valid, part, cnt);
                 }
             }
             // Kahan-compensated sum of the 16-view partial sums

@@ -111,6 +111,15 @@ refine_status refine_score_ex(refine_ctx *c, const refine_scene *scene, const re
         stats_out->mixed_pairs = (int64_t)hn[kCntMixedPairs];
         stats_out->bound_pairs = (int64_t)hn[kCntBoundPairs];
         stats_out->footprint_pairs = (int64_t)hn[kCntExactPairs];
+        stats_out->visible_mixed_pairs = (int64_t)hn[kCntVisMixed];
+        stats_out->open_u_pairs = (int64_t)hn[kCntOpenX];
+        stats_out->open_v_pairs = (int64_t)hn[kCntOpenY];
+        stats_out->open_z_pairs = (int64_t)hn[kCntOpenZ];
+        stats_out->bound_u_pairs = (int64_t)hn[kCntBoundX];
+        stats_out->bound_v_pairs = (int64_t)hn[kCntBoundY];
+        stats_out->exact_u_pairs = (int64_t)hn[kCntExactX];
+        stats_out->exact_v_pairs = (int64_t)hn[kCntExactY];
+        stats_out->exact_warp_axes = (int64_t)hn[kCntExactWarpAxes];
     }
     return REFINE_OK;
 }

@@ -46,7 +46,7 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(refine_camera), sizeof(refine_scene), sizeof(refine_params), sizeof(refine_scene_stats));
   printf("%zu %zu %zu %zu\\n", offsetof(refine_camera, width), offsetof(refine_camera, zfar), offsetof(refine_scene, pos), offsetof(refine_scene, row_stride));
-  printf("%zu %zu %zu\\n", offsetof(refine_params, e_ln_gem), offsetof(refine_params, flags), offsetof(refine_scene_stats, mean_m));
+  printf("%zu %zu %zu %zu\\n", offsetof(refine_params, e_ln_gem), offsetof(refine_params, flags), offsetof(refine_scene_stats, mean_m), offsetof(refine_scene_stats, exact_warp_axes));
   printf("%zu %zu %zu\\n", sizeof(refine_request), sizeof(refine_result), sizeof(refine_queue_stats));
   printf("%zu %zu %zu %zu\\n", offsetof(refine_request, ratio), offsetof(refine_request, kept_idx_host), offsetof(refine_result, threshold), offsetof(refine_result, done_ms));
   printf("%zu %zu\\n", offsetof(refine_queue_stats, max_round), offsetof(refine_queue_stats, kernel_launches));
@@ -62,7 +62,7 @@ int main(void) {
     assert got[1] == [b.refine_camera.width.offset, b.refine_camera.zfar.offset, b.refine_scene.pos.offset,
                       b.refine_scene.row_stride.offset]
     assert got[2] == [b.refine_params.e_ln_gem.offset, b.refine_params.flags.offset,
-                      b.refine_scene_stats.mean_m.offset]
+                      b.refine_scene_stats.mean_m.offset, b.refine_scene_stats.exact_warp_axes.offset]
     assert got[3] == [C.sizeof(b.refine_request), C.sizeof(b.refine_result), C.sizeof(b.refine_queue_stats)]
     assert got[4] == [b.refine_request.ratio.offset, b.refine_request.kept_idx_host.offset,
                       b.refine_result.threshold.offset, b.refine_result.done_ms.offset]
