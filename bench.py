@@ -19,7 +19,6 @@ import json
 import math
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -29,11 +28,25 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic FP32 work per (primitive, view) pair of the score kernel, FMA
-# counted as 2 FLOPs (the operation table is in the design doc): camera transform
-# 18, J W rows 18, L g products 30, squared norms 10, footprint box test 14,
-# depth test 2, Eq. 17 weight 3 (one MUFU reciprocal), accumulation 1.
-FLOPS_PER_PAIR = 96
+# Algorithmic FP32 work of the score kernel, counted only for the stages a
+# (primitive, view) pair needed (the kernel's diagnostic counters say which),
+# an FMA as 2 FLOPs and a compare, max or MUFU reciprocal as 1:
+FLOP_COSTS = {
+    "tile_view": 118,     # interval classification of one view for one tile: z, U, V, U - w z,
+                          # V - h z over the tile box (22 each) and the six range tests
+    "in_pair": 10,        # tile entirely visible: depth z (3 FMA), z^2 + eta (FMA), reciprocal, add
+    "mixed_pair": 6,      # decided pair by pair: depth z (3 FMA)
+    "open_axis": 10,      # per open u or v axis: U (3 FMA), d = max(-U, U - w z) (FMA, max), compare
+    "open_depth": 2,      # open depth range: two compares
+    "visible_mixed": 4,   # visible pair decided one by one: z^2 + eta, reciprocal, add
+    "bound_pair": 1,      # z^2 of a centre outside the image
+    "bound_axis": 10,     # per open axis: e = max(d, 0) z, e^2, t = U - c z, t^2, f^2 z^2 + t^2,
+                          # times 9 s_max^2, compare
+    "exact_axis": 30,     # per needed extent: g = z P - U P2 (3 MUL, 3 FMA), L g (3 MUL, 6 FMA),
+                          # |L g|^2 (MUL, 2 FMA), compare
+    "kahan_block": 4,     # per primitive and 16-view block: compensated add of the block sum
+    "epilogue": 8,        # per primitive: Eq. 7 coupling and the Eq. 20 scaling
+}
 FP32_LANES_PER_SM = 128
 METRIC = "Gaussian×view pairs/s"
 
@@ -72,9 +85,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload_name: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel
-    source is unchanged since it was taken."""
+def recorded_profile(kernel: str, workload_name: str):
+    """The committed ncu record of a kernel on a workload (DRAM bytes and
+    pipe figures per launch), or None when the kernel source has changed
+    since it was taken."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}.json")
     try:
         with open(path) as f:
@@ -83,66 +97,105 @@ def recorded_traffic(kernel: str, workload_name: str):
         return None
     if rec.get("source_hash") != kernel_source_hash():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec
+
+
+def score_work_flops(st: dict, n: int, views: int) -> float:
+    """Algorithmic FP32 FLOPs of one score launch over all views, from the
+    kernel's own counts of how each (primitive, view) pair was decided
+    (refine_scene_stats): tiles found invisible cost nothing, tiles found
+    visible only the weight, and pairs decided one by one the stages they
+    entered (FLOP_COSTS)."""
+    c = FLOP_COSTS
+    return float(st["tile_views"] * c["tile_view"] + st["in_pairs"] * c["in_pair"]
+                 + st["mixed_pairs"] * c["mixed_pair"]
+                 + (st["open_u_pairs"] + st["open_v_pairs"]) * c["open_axis"]
+                 + st["open_z_pairs"] * c["open_depth"] + st["visible_mixed_pairs"] * c["visible_mixed"]
+                 + st["bound_pairs"] * c["bound_pair"] + (st["bound_u_pairs"] + st["bound_v_pairs"]) * c["bound_axis"]
+                 + (st["exact_u_pairs"] + st["exact_v_pairs"]) * c["exact_axis"]
+                 + n * ((views + 15) // 16) * c["kahan_block"] + n * c["epilogue"])
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock, power and clock-event reasons of the benchmarked GPU, read
+    through NVML (read-only queries; libnvidia-ml is loaded with ctypes):
+    one sample at the start and one at the end of the timed region
+    (sample()) and one every ~2 ms in between from a background thread."""
+    # nvmlClocksEventReason* bits of the public NVML header
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    NVML_CLOCK_SM = 1
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
+    def __init__(self, props, index: int, period_s: float = 0.002):
+        import ctypes
+        self.C = ctypes
+        self.period = period_s
+        self.samples = []  # (time, sm MHz, reasons bitmask, power W)
+        self.max_mhz = None
+        self.dev = None
+        self._stop = threading.Event()
+        self.th = None
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit_v2 failed")
+            h = ctypes.c_void_p()
+            ok = False
+            dom, bus, devn = (getattr(props, k, None) for k in ("pci_domain_id", "pci_bus_id", "pci_device_id"))
+            if None not in (dom, bus, devn):
+                bid = f"{dom:08X}:{bus:02X}:{devn:02X}.0".encode()
+                ok = self.lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bid), ctypes.byref(h)) == 0
+            if not ok:
+                ok = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) == 0
+            if not ok:
+                raise OSError("no NVML handle")
+            self.dev = h
+            mx = ctypes.c_uint()
+            if self.lib.nvmlDeviceGetMaxClockInfo(self.dev, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            self._reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        except (OSError, AttributeError):
+            self.dev = None
+
+    def sample(self):
+        if self.dev is None:
+            return
+        C = self.C
+        mhz, rs, mw = C.c_uint(), C.c_ulonglong(), C.c_uint()
+        if self.lib.nvmlDeviceGetClockInfo(self.dev, self.NVML_CLOCK_SM, C.byref(mhz)) != 0:
+            return
+        if self._reasons(self.dev, C.byref(rs)) != 0:
+            rs.value = 0
+        power = mw.value / 1000.0 if self.lib.nvmlDeviceGetPowerUsage(self.dev, C.byref(mw)) == 0 else None
+        self.samples.append((time.time(), float(mhz.value), int(rs.value), power))
+
+    def _run(self):
+        while not self._stop.is_set():
+            self.sample()
+            time.sleep(self.period)
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.gpu)],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
-            return
-        self.th = threading.Thread(target=self._read, daemon=True)
-        self.th.start()
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append((time.time(), line.strip()))
+        if self.dev is not None:
+            self.th = threading.Thread(target=self._run, daemon=True)
+            self.th.start()
 
     def stop(self):
-        if self.proc is None:
-            return
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
+        self._stop.set()
+        if self.th is not None:
+            self.th.join(timeout=5)
 
     def summary(self, t0, t1):
-        sm, mx, pw, reasons = [], [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for t, line in self.lines:
-            if not (t0 <= t <= t1 + 0.25):
-                continue
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1])); mx.append(float(parts[2]))
-                pw.append(float(parts[3]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "power_w_max": max(pw),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        sel = [x for x in self.samples if t0 <= x[0] <= t1]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0, "source": "nvml"}
+        reasons = set()
+        for _, _, r, _ in sel:
+            reasons.update(name for bit, name in self.REASONS.items() if r & bit)
+        pw = [x[3] for x in sel if x[3] is not None]
+        return {"sm_mhz": statistics.median(x[1] for x in sel), "sm_min_mhz": min(x[1] for x in sel),
+                "sm_max_mhz": self.max_mhz, "power_w_max": max(pw) if pw else None,
+                "reasons": sorted(reasons), "samples": len(sel), "source": "nvml"}
 
 
 def aggregate_over_ranks(local_ms: float, steps: int, pairs_per_step: int, world: int, dist=None,
@@ -330,9 +383,7 @@ def run_ours(args, rank: int, world: int):
     ctx.check()
     ctx.kernel_times()
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.5)
+    clocks = ClockSampler(torch.cuda.get_device_properties(dev), local)
     # inside the timed region only the score kernel is bracketed by events
     # (two per step); events around all 14 kernels would add ~0.06 ms a step
     ctx.set_timing(True, score_only=True)
@@ -342,11 +393,14 @@ def run_ours(args, rank: int, world: int):
         dist.barrier()
     torch.cuda.synchronize(dev)
     t_wall0 = time.time()
+    clocks.sample()
+    clocks.start()
     evs[0].record(stream)
     for k in range(args.steps):
         step()
         evs[k + 1].record(stream)
     torch.cuda.synchronize(dev)
+    clocks.sample()
     if dist:
         dist.barrier()
     t_wall1 = time.time()
@@ -369,25 +423,37 @@ def run_ours(args, rank: int, world: int):
                                            dist, dev)
     ms_step = total_ms / args.steps
 
-    # roofline of the dominant kernel (score): live CUDA-event timing
+    # roofline of the dominant kernel (score): live CUDA-event timing of the
+    # timed region; the work it did from one counting pass after it
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     clk_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * clk_max * 1e6 / 1e12
     sc = ktimes.get("score", {"ms": float("nan"), "launches": 1})
     score_ms = sc["ms"] / max(sc["launches"], 1)
-    achieved = pairs * FLOPS_PER_PAIR / (score_ms / 1000.0) / 1e12
+    score_ms_step = sc["ms"] / args.steps  # all passes of a step (one pass up to 512 views)
+    _, work = ctx.score(pos, attr, cams, params=params, stats=True, stream=stream)
+    flops = score_work_flops(work, n, V)
+    achieved = flops / (score_ms_step / 1000.0) / 1e12
+    prof = recorded_profile("score", args.workload) if args.storage == "f32" and not args.max_views else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": recorded_traffic("score", args.workload),
-                "kernel": "k_score", "kernel_ms": score_ms,
-                "flops_basis": f"{FLOPS_PER_PAIR} FLOP per (primitive, view) pair, every pair counted at the full "
-                               f"visibility test; the kernel's tile classification skips pairs whose outcome is "
-                               f"implied and shortens others, so frac can exceed 1",
+                "frac": achieved / peak_tflops, "traffic": prof.get("dram_bytes_per_launch") if prof else None,
+                "kernel": "k_score", "kernel_ms": score_ms, "flops_per_step": flops,
+                "flops_basis": "FP32 work of the stages each (primitive, view) pair needed, from the kernel's own "
+                               "pair-class counters of this scene: invisible tiles 0, visible tiles the Eq. 17 "
+                               "weight, pairs decided one by one their open axes, footprint bound and exact "
+                               "footprint test (FMA = 2, compare/max/reciprocal = 1)",
+                "pair_classes": {k: work[k] for k in ("pairs", "in_pairs", "out_pairs", "mixed_pairs",
+                                                      "bound_pairs", "footprint_pairs")},
                 "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                               f"{clk_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
                 "kernels_ms_per_step": {k: v["ms"] / b_steps for k, v in kt_all.items()},
                 "kernels_ms_per_step_basis": f"every kernel bracketed by CUDA events, {b_steps} steps after the "
                                              f"timed region"}
+    if prof:
+        roofline["ncu"] = {k: prof[k] for k in ("fp32_flops_executed", "fp32_executed_frac", "fma_pipe_pct",
+                                                "issue_active_pct", "thread_inst_per_pair", "source")
+                           if k in prof}
     clock_summary = clocks.summary(t_wall0, t_wall1)
 
     line = None
@@ -408,7 +474,7 @@ def run_ours(args, rank: int, world: int):
         lat = sorted(per_step)
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32" if w.scene.dtype == "f32" else "f32 (bf16 storage)", "data": "synthetic",
                 "config": {"workload": w.name, "n": n, "views": V, "ratio": ratio, "storage": w.scene.dtype,
                            "l2": f"inputs larger than L2 ({(236 * n) / 1e6:.0f} MB scene), no flush",
                            "parallelism": "replicas" if world > 1 else "single"},

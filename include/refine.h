@@ -495,6 +495,22 @@ refine_status refine_ctx_kernel_times(refine_ctx *ctx, const char **names, doubl
                                       int64_t *launches, int32_t cap, int32_t *count);
 int64_t refine_ctx_launch_count(const refine_ctx *ctx);
 
+/* Self-test of failure detection on the device (no counterpart in the
+ * paper: it tests the bounded wait that guards the score kernels' TMA
+ * camera staging, without faulting or hanging the GPU).  A one-thread kernel
+ * stages `bytes` bytes of context scratch into shared memory by a bulk copy
+ * whose mbarrier expects bytes + missing_bytes.
+ *   bytes          16..1024, a multiple of 16
+ *   missing_bytes  0..65536: with 0 the wait completes and the call returns
+ *                  REFINE_OK; otherwise the barrier phase can never complete,
+ *                  the wait gives up after wait_cycles SM clock cycles and
+ *                  the call returns REFINE_ETIMEOUT, read from the device
+ *                  status word like any device error (which it then clears)
+ *   wait_cycles    1..2e9 (about a second at the maximum SM clock)
+ * Synchronises `stream`.  The context stays usable afterwards. */
+refine_status refine_selftest_wait(refine_ctx *ctx, uint32_t bytes, uint32_t missing_bytes,
+                                   int64_t wait_cycles, refine_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

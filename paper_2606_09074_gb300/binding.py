@@ -171,6 +171,7 @@ _SIGNATURES = {
     "refine_ctx_kernel_times": (C.c_int, [_P, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int64), C.c_int32, C.POINTER(C.c_int32)]),
     "refine_ctx_launch_count": (C.c_int64, [_P]),
+    "refine_selftest_wait": (C.c_int, [_P, C.c_uint32, C.c_uint32, C.c_int64, _P]),
 }
 
 
@@ -387,6 +388,13 @@ class Context:
 
     def launch_count(self) -> int:
         return int(refine_ctx_launch_count(self.handle))  # noqa: F821
+
+    def selftest_wait(self, nbytes=1024, missing=0, cycles=2_000_000, stream=None) -> int:
+        """Runs the bounded-wait self-test (refine_selftest_wait) and returns
+        its status code (REFINE_OK, or REFINE_ETIMEOUT when ``missing`` bytes
+        never arrive)."""
+        return int(refine_selftest_wait(self.handle, nbytes, missing, cycles,  # noqa: F821
+                                        _stream_handle(stream, self.device)))
 
     def autotune(self, jobs, params=None, reps=3):
         """Times the batched score launch of ``jobs`` (device-tensor dicts as

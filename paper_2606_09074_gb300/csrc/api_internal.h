@@ -35,13 +35,14 @@ enum KClass {
     K_MASK_FILL,
     K_CMP_COUNT,
     K_CMP_SCATTER,
+    K_SELFTEST,
     K_NCLASS
 };
 const char *const kClassName[K_NCLASS] = {"cam_prep",      "features",     "features_finalize",
                                           "cells",         "cell_scan",    "cell_scatter",
                                           "score",         "select_pass",  "select_ties",
                                           "select_mask",   "mask_fill",    "compact_count",
-                                          "compact_scatter"};
+                                          "compact_scatter", "selftest"};
 
 struct Arena {
     void *p = nullptr;

@@ -128,6 +128,11 @@ cudaError_t launch_cell_scatter(const uint2 *cell, int64_t n,
 cudaError_t launch_score(const ScoreLaunch &a, const ScoreShape &sh, cudaStream_t s);
 int score_grid(int num_sms, int64_t n, int vcount, const ScoreShape &sh);
 
+// Self-test of the bounded mbarrier wait (refine_selftest_wait).
+constexpr uint32_t kSelftestMaxBytes = 1024;
+cudaError_t launch_wait_selftest(const void *src, uint32_t bytes, uint32_t missing, long long limit, int *status,
+                                 cudaStream_t s);
+
 // Batched score launch over the tiles of many scenes (each scene a single
 // pass of at most kViewsPerPass views).
 struct BatchLaunch {

@@ -1054,6 +1054,9 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLau
                 continue;  // the tile is left unscored; the loop's first barrier orders s_scene
             }
             if (!mbar_wait_bounded(&bar, phase)) {
+                // the item left unscored belongs to this scene: its own
+                // status word carries the error, and so does the launch's
+                set_status(a.status, kEtimeout);
                 set_status(b.status, kEtimeout);
                 mbar_wait_bounded(&bar, phase);
                 return;
@@ -1080,6 +1083,33 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLau
         }
         __syncthreads();  // the cameras, s_scene and s_wt are free again
     }
+}
+
+// Self-test of the bounded wait that guards the camera staging above: one
+// thread stages `bytes` by a bulk copy while the barrier expects `bytes +
+// missing` bytes.  With missing > 0 the phase cannot complete; the wait gives
+// up after `limit` cycles (long after the copy itself has landed) and the
+// kernel reports kEtimeout through the status word and returns.
+__global__ void k_wait_selftest(const unsigned char *src, uint32_t bytes, uint32_t missing, long long limit,
+                                int *status)
+{
+    __shared__ __align__(16) unsigned char buf[kSelftestMaxBytes];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, bytes + missing);
+    bulk_g2s(buf, src, bytes, &bar);
+    if (!mbar_wait_bounded(&bar, 0, limit)) {
+        set_status(status, kEtimeout);
+        mbar_wait_bounded(&bar, 0, limit);
+    }
+}
+
+cudaError_t launch_wait_selftest(const void *src, uint32_t bytes, uint32_t missing, long long limit, int *status,
+                                 cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(static_cast<const unsigned char *>(src), bytes, missing, limit, status);
+    return cudaGetLastError();
 }
 
 template <int PM, bool COUNT, int GPT>

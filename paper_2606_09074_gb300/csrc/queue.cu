@@ -13,8 +13,11 @@
 //   completion   polls the completion events of the requests in flight,
 //                finishes copies into pageable buffers, reads the request's
 //                status and threshold, frees its block and its slot.
-// Device status words are per request (and per round for the batched
-// launch), so an error is reported on the request that caused it.
+// Device status words are per request: the batched launch reports an error
+// on the status word of the request whose scene it concerns, so an error is
+// reported on the request that caused it, and no request reads a word that
+// belongs to its round (the round ring is reused while earlier requests may
+// still be finishing).
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -42,8 +45,7 @@ inline int64_t keep_count(int64_t n, double ratio) { return n - (int64_t)floor(r
 struct SlotHost {  // page-locked read-back of one slot
     unsigned int kstar;
     int status;
-    int round_status;
-    int pad;
+    int pad[2];
 };
 
 struct QJob {
@@ -242,7 +244,6 @@ refine_status issue_finish(refine_queue *q, QJob *j, const RoundRes &R)
     h->kstar = 0u;
     if (j->kstar) e = cudaMemcpyAsync(&h->kstar, j->kstar, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h->status, j->status, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h->round_status, R.d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && j->pinned_out) {
         const size_t es = elem_size(j->req.dtype);
         if (j->req.keep_mask_host)
@@ -391,7 +392,6 @@ void retire(refine_queue *q, QJob *j)
     const SlotHost &h = q->slot_host[j->slot];
     if (!st && j->issued) {
         if (h.status) st = (refine_status)h.status;
-        else if (h.round_status) st = (refine_status)h.round_status;
         if (!st && !j->pinned_out) st = finish_pageable(q, j);
     }
     refine_result r{};

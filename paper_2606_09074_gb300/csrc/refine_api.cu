@@ -289,6 +289,25 @@ refine_status refine_ctx_kernel_times(refine_ctx *c, const char **names, double 
 
 int64_t refine_ctx_launch_count(const refine_ctx *c) { return c ? c->launch_count : -1; }
 
+refine_status refine_selftest_wait(refine_ctx *c, uint32_t bytes, uint32_t missing_bytes, int64_t wait_cycles,
+                                   refine_stream_t stream)
+{
+    if (!c) return REFINE_EINVAL;
+    refine_status st = use_device(c);
+    if (st) return st;
+    if (bytes < 16 || bytes > kSelftestMaxBytes || bytes % 16 || missing_bytes > 65536 || wait_cycles < 1 ||
+        wait_cycles > kWaitCycles)
+        return fail(c, REFINE_EINVAL, "selftest_wait: bytes %u, missing %u or cycles %lld out of range", bytes,
+                    missing_bytes, (long long)wait_cycles);
+    if ((st = ensure(c, c->score, kSelftestMaxBytes))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((st = launch(c, K_SELFTEST, s, [&] {
+             return launch_wait_selftest(c->score.p, bytes, missing_bytes, (long long)wait_cycles, c->d_status, s);
+         })))
+        return st;
+    return read_status(c, s);
+}
+
 }  // extern "C"
 
 // ==================================================================== batch

@@ -7,16 +7,16 @@ some choice of those pairs.  Selection and compaction on identical scores
 are bit-exact.  Masks from the oracle's own scores agree except for
 primitives within 1e-5 of the threshold or with a borderline pair."""
 import math
+import os
 
 import numpy as np
 import pytest
 
 import oracle
 from paper_2606_09074_gb300 import synth
+from parity_helpers import RTOL, assert_score_parity, check_mask_vs_oracle_scores, unpack
 
 pytestmark = pytest.mark.gpu
-
-RTOL = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -65,27 +65,6 @@ def oracle_params_from(p, rb):
                          luma=[float(np.float32(x)) for x in p.luma], flags=p.flags)
 
 
-def assert_score_parity(s_gpu, S_gpu, ref, rtol=RTOL):
-    clean = ref["nborder"] == 0
-    for name, got, want in (("S", S_gpu, ref["S"]), ("score", s_gpu, ref["scores"])):
-        g = got.astype(np.float64)
-        zero = clean & (want == 0)
-        assert np.all(g[zero] == 0), f"{name}: nonzero where oracle is exactly 0"
-        nz = clean & (want != 0)
-        rel = np.abs(g[nz] - want[nz]) / np.abs(want[nz])
-        if rel.size:
-            worst = int(np.argmax(rel))
-            assert rel.max() <= rtol, (f"{name}: max rel err {rel.max():.3e} at {np.nonzero(nz)[0][worst]}",
-                                       g[nz][worst], want[nz][worst])
-    ok = oracle.valid_alternative(S_gpu.astype(np.float64), ref, rtol)
-    assert ok.all(), f"borderline primitives with no valid alternative: {np.nonzero(~ok)[0][:10]}"
-    return clean
-
-
-def unpack(mask_words, n):
-    return np.unpackbits(np.asarray(mask_words, dtype=np.uint32).view(np.uint8), bitorder="little")[:n].astype(bool)
-
-
 def check_select_exact(torch, ctx, s_gpu, ratio):
     t = torch.from_numpy(s_gpu.astype(np.float32)).cuda()
     mask, thr, nk = ctx.select(t, ratio)
@@ -96,15 +75,6 @@ def check_select_exact(torch, ctx, s_gpu, ratio):
     assert np.array_equal(got, m_ref), "keep mask differs from the oracle on identical scores"
     assert thr == np.float32(thr_ref)  # also covers -inf (nothing pruned) and +inf
     return mask, got, nk
-
-
-def check_mask_vs_oracle_scores(got_mask, ref, ratio, n):
-    m_ref, thr_ref, nk_ref = oracle.select(ref["scores"], ratio)
-    a, b = unpack(got_mask, n), unpack(m_ref, n)
-    diff = np.nonzero(a != b)[0]
-    band = (np.abs(ref["scores"] - thr_ref) <= RTOL * abs(thr_ref)) | (ref["nborder"] > 0)
-    assert np.all(band[diff]), f"mask differs outside the threshold band at {diff[~band[diff]][:10]}"
-    return 1.0 - diff.size / max(n, 1)
 
 
 def check_compact_exact(torch, ctx, scene, pos, attr, mask, nk):
@@ -315,19 +285,53 @@ def test_core_shell_1m_full(torch, rb, ctx):
     check_compact_exact(torch, ctx, w.scene, pos, attr, mask, nk)
 
 
-def test_core_shell_3p5m_sampled(torch, rb, ctx):
-    """N=3.5M, 250 views at 1600x1063, the benchmark's launch configuration:
-    a seeded 50k-primitive sample against the oracle (statistics from all
-    3.5M), exact selection and compaction of the full scene."""
+@pytest.fixture(scope="module")
+def c2_oracle():
+    """The FP64 oracle on every primitive of the 3.5M-primitive, 250-view
+    benchmark scene (float32 inputs; a few seconds on the host's cores)."""
     w = synth.config2()
+    oracle.set_threads(os.cpu_count() or 1)
+    return w, oracle.score(w.scene.params_f64(), w.cams)
+
+
+def test_core_shell_3p5m_full(torch, rb, ctx, c2_oracle):
+    """N=3.5M, 250 views at 1600x1063 in the benchmark's launch
+    configuration: every score against the FP64 oracle, the keep mask at
+    ratio 0.5 against the oracle's own selection outside the threshold band,
+    exact selection and compaction of the full scene."""
+    w, ref = c2_oracle
     s, S, st, (pos, attr) = gpu_score(torch, rb, ctx, w.scene, w.cams)
-    g = w.scene.params_f64()
-    idx = np.sort(np.random.default_rng(22).choice(w.scene.n, 50_000, replace=False))
-    ref = oracle.score_subset(g, idx, w.cams)
-    assert_score_parity(s[idx], S[idx], ref)
+    clean = assert_score_parity(s, S, ref)
+    assert clean.mean() > 0.97
     np.testing.assert_allclose(st["lambda"], ref["stats"]["lambda"], rtol=1e-6)
-    mask, _, nk = check_select_exact(torch, ctx, s, 0.5)
+    mask, words, nk = check_select_exact(torch, ctx, s, 0.5)
+    agree = check_mask_vs_oracle_scores(words, ref, 0.5, w.scene.n)
+    print(f"3.5M x 250 FP32: {clean.mean():.4%} of primitives outside the float32 band, "
+          f"mask agreement with the oracle {agree:.5%}")
+    assert agree > 0.9999
     check_compact_exact(torch, ctx, w.scene, pos, attr, mask, nk)
+
+
+def test_core_shell_3p5m_bf16_accuracy(torch, rb, ctx, c2_oracle):
+    """The precision form on the benchmark scene: rows 3-58 stored as
+    bfloat16.  On its own (rounded) inputs it matches the oracle within the
+    float32 tolerance (100k-primitive sample); against the oracle on the
+    float32 scene it was rounded from, the keep mask at ratio 0.5 agrees on
+    at least 99.9 % of the primitives, and the score error is reported."""
+    w, ref32 = c2_oracle
+    sb = w.scene.to_bf16()
+    s, S, _, _ = gpu_score(torch, rb, ctx, sb, w.cams)
+    idx = np.sort(np.random.default_rng(7).choice(w.scene.n, 100_000, replace=False))
+    refb = oracle.score_subset(sb.params_f64(), idx, w.cams)
+    assert_score_parity(s[idx], S[idx], refb)
+    ok = (ref32["nborder"] == 0) & (ref32["scores"] > 0)
+    rel = np.abs(s.astype(np.float64)[ok] - ref32["scores"][ok]) / ref32["scores"][ok]
+    _, words, _ = check_select_exact(torch, ctx, s, 0.5)
+    m_ref, _, _ = oracle.select(ref32["scores"], 0.5)
+    agree = float(np.mean(unpack(words, w.scene.n) == unpack(m_ref, w.scene.n)))
+    print(f"3.5M x 250 BF16 vs the FP64 oracle on the float32 scene: rel err mean {rel.mean():.3e} "
+          f"p99 {np.quantile(rel, 0.99):.3e} max {rel.max():.3e}; mask agreement {agree:.5%}")
+    assert agree >= 0.999
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])

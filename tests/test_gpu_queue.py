@@ -183,3 +183,67 @@ def test_destroy_with_work_in_flight(env):
     # the context still works afterwards
     ref = plain(torch, rb, ctx, w, r)
     assert ref["nk"] == w.scene.n - int(np.floor(r * w.scene.n))
+
+
+def test_queue_matches_oracle(env):
+    """Every request of a mixed round against the FP64 oracle on its own
+    scene: scores within the float32 tolerance, the keep mask agreeing with
+    the oracle's selection outside the threshold band, and the kept rows
+    equal to the oracle's gather with the returned mask."""
+    import oracle
+    from parity_helpers import assert_scores_only_parity, check_mask_vs_oracle_scores
+    torch, rb, ctx = env
+    sc = scenes()
+    q = rb.Queue(ctx, budget_bytes=8 << 30, max_slots=8)
+    try:
+        tickets = [q.submit(*host_inputs(w), r, scores=True) for (w, r) in sc]
+        for (w, r), t in zip(sc, tickets):
+            res, out = q.poll(t, timeout_ms=60_000)
+            assert res["status"] == 0
+            ref = oracle.score(w.scene.params_f64(), w.cams)
+            n = w.scene.n
+            assert_scores_only_parity(np.asarray(out["scores"]), ref)
+            words = np.asarray(out["mask"]).view(np.uint32)[: (n + 31) // 32]
+            assert check_mask_vs_oracle_scores(words, ref, r, n) > 0.999
+            kp, ki = oracle.compact(np.ascontiguousarray(w.scene.pos), words)
+            ka, _ = oracle.compact(np.ascontiguousarray(w.scene.attr), words)
+            assert res["n_keep"] == ki.shape[0]
+            assert np.array_equal(np.asarray(out["idx"]), ki)
+            assert np.array_equal(np.asarray(out["out_pos"]).view(np.uint32), kp.view(np.uint32))
+            oa = np.asarray(out["out_attr"])
+            assert np.array_equal(oa.view(np.uint16 if w.scene.dtype == "bf16" else np.uint32),
+                                  ka.view(np.uint16 if w.scene.dtype == "bf16" else np.uint32))
+    finally:
+        q.close()
+
+
+def test_errors_stay_with_their_request_while_the_round_ring_turns(env):
+    """Two slots: a long request holds one while short requests go through
+    the other, so the round ring (one entry per slot) is reused while the
+    long request is still in flight.  An invalid camera fails only its own
+    request; every other request, the long one included, succeeds and equals
+    the per-scene path."""
+    torch, rb, ctx = env
+    long_w = synth.random_scene(seed=61, n=1_500_000, v=300, means="core_shell")
+    short = [synth.random_scene(seed=62 + k, n=2000 + 37 * k, v=4 + k, means="core_shell") for k in range(8)]
+    bad = 5
+    cams_bad = short[bad].cams.copy()
+    cams_bad["zfar"][1] = cams_bad["znear"][1] * 0.5  # zfar < znear: an invalid camera
+    refs = [plain(torch, rb, ctx, w, 0.5) for w in short]
+    ref_long = plain(torch, rb, ctx, long_w, 0.5)
+    q = rb.Queue(ctx, budget_bytes=8 << 30, max_slots=2)
+    try:
+        t_long = q.submit(*host_inputs(long_w), 0.5, scores=True)
+        tickets = [q.submit(w.scene.pos, w.scene.attr, cams_bad if k == bad else w.cams, 0.5, scores=True)
+                   for k, w in enumerate(short)]
+        for k, t in enumerate(tickets):
+            res, out = q.poll(t, timeout_ms=120_000)
+            if k == bad:
+                assert res["status"] == rb.REFINE_EINVAL
+            else:
+                check_same(refs[k], res, out, short[k])
+        res, out = q.poll(t_long, timeout_ms=120_000)
+        check_same(ref_long, res, out, long_w)
+        assert q.stats()["rounds"] > 2  # the two ring entries were reused
+    finally:
+        q.close()

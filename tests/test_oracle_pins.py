@@ -496,3 +496,21 @@ def test_full_jacobian_term_matches_finite_differences():
         o = oracle.score(g, np.array([cam], dtype=synth.CAMERA_DTYPE),
                          oracle.params(flags=oracle.NORM_ATTR | oracle.FULL_JACOBIAN))
         assert o["S"][0] == pytest.approx(float((J ** 2).sum()), rel=1e-7)
+
+
+def test_score_subset_equals_full_score_at_its_indices():
+    """score_subset(g, idx) scores the primitives idx of the whole scene: the
+    same scores, view sums, borderline records and scene statistics as
+    score(g) at those indices, for sorted, unsorted and repeated indices
+    (its index path is what the sampled GPU parity checks rely on)."""
+    w = synth.random_scene(seed=5, n=3000, v=12, means="core_shell")
+    g = w.scene.params_f64()
+    full = oracle.score(g, w.cams)
+    rng = np.random.default_rng(55)
+    for idx in (np.sort(rng.choice(3000, 700, replace=False)), rng.permutation(3000)[:500],
+                np.array([0, 2999, 17, 17, 1500, 0], dtype=np.int64)):
+        sub = oracle.score_subset(g, idx, w.cams)
+        for key in ("scores", "S", "S_sure", "nborder", "bterms"):
+            assert np.array_equal(sub[key], full[key][idx]), key
+        assert sub["stats"] == full["stats"]
+    assert (full["scores"] > 0).mean() > 0.5  # the comparison covers visible primitives
