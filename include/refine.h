@@ -249,18 +249,20 @@ refine_status refine_prune_host(refine_ctx *ctx, int64_t n, int32_t dtype,
 /* ------------------------------------------------------------ batches
  * Many scenes in one go: per-scene preparation (content features, lambda,
  * processing order) and per-scene selection and compaction run on parallel
- * streams, and all scenes are scored by ONE persistent kernel launch over a
- * (scene, tile) work list.  The whole batch is captured into a CUDA graph
- * on its first run and replayed afterwards, so a run costs one graph launch.
- * Scores, masks and compacted outputs are bit-identical to the per-scene
- * entry points. */
+ * streams, and all scenes are scored by persistent kernel launches over a
+ * (scene, tile, camera block) work list: one launch per camera block level,
+ * launch p scoring the p-th block of views of every scene that has one
+ * (a single launch when every scene has at most camera_block views).  The
+ * whole batch is captured into a CUDA graph on its first run and replayed
+ * afterwards, so a run costs one graph launch.  Scores, masks and compacted
+ * outputs are bit-identical to the per-scene entry points. */
 
 /* One scene of a batch; every pointer is device memory owned by the caller
  * and must stay valid (and unchanged in address) for the batch's life. */
 typedef struct refine_job {
     refine_scene scene;            /* primitives (see refine_scene)                      */
     const refine_camera *cams_dev; /* n_views camera records                             */
-    int32_t n_views;               /* >= 1; at most 512 scored (see max_views)           */
+    int32_t n_views;               /* 1 .. 65535                                          */
     int32_t reserved;
     double ratio;                  /* pruning ratio in [0, 1)                             */
     float *scores_dev;             /* [n] written                                         */
@@ -274,7 +276,8 @@ typedef struct refine_job {
 typedef struct refine_batch refine_batch;
 
 /* Builds a batch of n_jobs scenes (1 <= n_jobs <= 4096, n >= 1 and
- * n_views <= 512 each, storage types may differ; the jobs array is copied).  Allocates
+ * n_views <= 65535 each, storage types may differ; the jobs array is copied),
+ * with the context's shape at this call (camera block included).  Allocates
  * all scratch up front (released by refine_batch_destroy).  EINVAL on a bad
  * job (refine_last_error(ctx) names it), ENOMEM if the scratch does not fit. */
 refine_status refine_batch_create(refine_ctx *ctx, const refine_job *jobs, int32_t n_jobs,
@@ -300,21 +303,28 @@ void refine_batch_destroy(refine_batch *batch);
 /* ------------------------------------------------------------ autotuner
  * Work-item shape of the score kernels.  A warp scores a tile of 32 or 64
  * consecutive primitives of the processing order against every view; the
- * batched kernel hands out CTA-sized items of such tiles.  Every primitive's
- * score is computed by one thread with the views in a fixed order, whatever
- * tile it is in, so the shape changes speed only: results are bit-identical
- * for every shape. */
+ * batched kernel hands out CTA-sized items of such tiles, and the views are
+ * taken in camera blocks (passes) of `camera_block` views.  Every
+ * primitive's score is computed by one thread with the views in a fixed
+ * order, whatever tile it is in, and its running Kahan pair is carried
+ * from one camera block to the next, so the shape changes speed only:
+ * results are bit-identical for every shape. */
 typedef struct refine_shape {
     int32_t tile;         /* primitives per warp tile: 32 or 64 (default 64)            */
     int32_t cta_threads;  /* threads per CTA of the batched kernel: 128 or 256          */
     int32_t ctas_per_sm;  /* cap on resident CTAs per SM (batched kernel), 0 = all fit */
-    int32_t reserved;
-    double ms;            /* refine_autotune: measured time of one batched score launch */
+    int32_t camera_block; /* views per score pass: 32..512, a multiple of 32 (default
+                             512); a scene with more views is scored in passes, and a
+                             batch scores pass p of all its scenes in one launch       */
+    double ms;            /* refine_autotune: measured time of the batched score launches */
 } refine_shape;
 
-/* Times the batched score launch of `jobs` (as refine_batch_create takes
- * them; their scores are written) under every candidate shape, `reps`
- * launches each after one warm-up, and makes the fastest the context's shape
+/* Times the batched score launches of `jobs` (as refine_batch_create takes
+ * them; their scores are written) under every candidate shape -- tile 64 or
+ * 32, CTAs of 256 or 128 threads, all CTAs that fit per SM or a cap, and
+ * camera blocks of 512, 256 and 128 views (a block that would split no scene
+ * differently from a larger one is not tried again) -- `reps` runs each
+ * after one warm-up, and makes the fastest the context's shape
  * (used by refine_score and by batches and queues created afterwards).
  * *best_out (may be NULL) receives it; table_out (may be NULL) receives up to
  * table_cap candidates in the order tried, *table_count their number.
@@ -324,7 +334,8 @@ refine_status refine_autotune(refine_ctx *ctx, const refine_job *jobs, int32_t n
                               refine_shape *table_out, int32_t table_cap, int32_t *table_count);
 
 /* Reads or sets the context's shape (EINVAL for a shape outside the
- * candidates: tile 32 or 64, cta_threads 128 or 256, ctas_per_sm >= 0). */
+ * candidates: tile 32 or 64, cta_threads 128 or 256, ctas_per_sm >= 0,
+ * camera_block 32..512 in steps of 32). */
 refine_status refine_ctx_get_shape(const refine_ctx *ctx, refine_shape *out);
 refine_status refine_ctx_set_shape(refine_ctx *ctx, const refine_shape *shape);
 
@@ -337,7 +348,9 @@ refine_status refine_ctx_set_shape(refine_ctx *ctx, const refine_shape *shape);
  *     and one device block from the queue's memory pool, into which its
  *     scene and cameras are copied.  All requests admitted together form a
  *     round: their preparation runs on their slot streams, ONE persistent
- *     launch scores all of them (the batched kernel), then selection,
+ *     launch scores all of them (the batched kernel; a request with more
+ *     views than the camera block has its further blocks scored right after
+ *     it, in order, on the same stream), then selection,
  *     compaction and the copies back run on the slot streams again.  A
  *     round is issued as soon as it is formed, while earlier rounds are
  *     still on the GPU, so requests that arrive meanwhile overlap with them
@@ -358,7 +371,7 @@ typedef struct refine_queue refine_queue;
 typedef struct refine_request {
     int64_t n;                       /* primitives, 1 .. 2^31 - 1                           */
     int32_t dtype;                   /* REFINE_F32 or REFINE_BF16 (attribute rows)          */
-    int32_t n_views;                 /* 1 .. 65535, at most 512 scored (see max_views)     */
+    int32_t n_views;                 /* 1 .. 65535                                          */
     const float *pos_host;           /* [3][n] float32 means                               */
     const void *attr_host;           /* [56][n] in dtype, rows as in refine_scene          */
     const refine_camera *cams_host;  /* [n_views]                                          */
@@ -392,7 +405,9 @@ typedef struct refine_queue_stats {
 } refine_queue_stats;
 
 /* Device bytes one request holds while admitted (scene, cameras, scratch,
- * scores, mask and, with compact != 0, the compacted rows). */
+ * scores, mask and, with compact != 0, the compacted rows), for the
+ * smallest camera block (so an upper bound for any queue's shape); 0 for
+ * arguments out of range. */
 uint64_t refine_queue_footprint(int64_t n, int32_t dtype, int32_t n_views, double ratio, int32_t compact);
 
 /* Creates a queue on ctx's device (ctx itself is not used by the queue's
@@ -427,10 +442,9 @@ const char *refine_queue_last_error(refine_queue *q);
 void refine_queue_destroy(refine_queue *q);
 
 /* Ratio pruning without any allocation.  The paper has no counterpart; this
- * entry point exists for callers that cannot allocate device memory -- code
- * recording a CUDA graph that must not contain allocation nodes, plug-ins
- * whose host engine owns every device allocation, real-time loops whose
- * memory is fixed at start-up -- and so cannot create a refine_ctx.
+ * entry point exists for callers that cannot allocate device memory --
+ * plug-ins whose host engine owns every device allocation, real-time loops
+ * whose memory is fixed at start-up -- and so cannot create a refine_ctx.
  *
  * Same inputs, outputs and result as refine_select (same kernels), but no
  * context: it runs on the calling thread's current device and keeps its
@@ -440,9 +454,10 @@ void refine_queue_destroy(refine_queue *q);
  * library routine.
  *   n        0 <= n <= 67,108,864 (2^26); larger n returns REFINE_EINVAL
  *   errbuf   host buffer of errlen bytes for a message, or NULL
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call on a device shares the one array and
+ * Every call looks up the array's device address (cudaGetSymbolAddress) on
+ * the calling thread's current device; the first call on a device also
+ * loads the library's device code there, so make that first call before any
+ * stream capture.  Every call on a device shares the one array and
  * each call resets it: calls whose work overlaps on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  NaN scores are
  * reported (REFINE_ENONFINITE) only when threshold_out is non-NULL, which

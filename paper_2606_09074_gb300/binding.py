@@ -97,7 +97,7 @@ class refine_job(C.Structure):
 
 class refine_shape(C.Structure):
     _fields_ = [("tile", C.c_int32), ("cta_threads", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("reserved", C.c_int32), ("ms", C.c_double)]
+                ("camera_block", C.c_int32), ("ms", C.c_double)]
 
 
 class refine_request(C.Structure):
@@ -402,21 +402,21 @@ class Context:
         context.  Returns (best, table) as dicts."""
         arr, outs, keep = _make_jobs(self, jobs, compact=False)  # outs must outlive the call
         best = refine_shape()
-        table = (refine_shape * 16)()
+        table = (refine_shape * 64)()
         cnt = C.c_int32()
         _check(self.handle, refine_autotune(self.handle, arr, len(jobs),  # noqa: F821
                                             C.byref(params) if params is not None else None, int(reps),
-                                            C.byref(best), table, 16, C.byref(cnt)))
+                                            C.byref(best), table, 64, C.byref(cnt)))
         del outs, keep
-        return _shape_dict(best), [_shape_dict(table[k]) for k in range(min(cnt.value, 16))]
+        return _shape_dict(best), [_shape_dict(table[k]) for k in range(min(cnt.value, 64))]
 
     def get_shape(self) -> dict:
         sh = refine_shape()
         _check(self.handle, refine_ctx_get_shape(self.handle, C.byref(sh)))  # noqa: F821
         return _shape_dict(sh)
 
-    def set_shape(self, tile=64, cta_threads=256, ctas_per_sm=0):
-        sh = refine_shape(tile, cta_threads, ctas_per_sm, 0, 0.0)
+    def set_shape(self, tile=64, cta_threads=256, ctas_per_sm=0, camera_block=512):
+        sh = refine_shape(tile, cta_threads, ctas_per_sm, camera_block, 0.0)
         _check(self.handle, refine_ctx_set_shape(self.handle, C.byref(sh)))  # noqa: F821
 
 
@@ -455,7 +455,8 @@ def _make_jobs(ctx, jobs, compact=True):
 
 
 def _shape_dict(sh) -> dict:
-    return {"tile": sh.tile, "cta_threads": sh.cta_threads, "ctas_per_sm": sh.ctas_per_sm, "ms": sh.ms}
+    return {"tile": sh.tile, "cta_threads": sh.cta_threads, "ctas_per_sm": sh.ctas_per_sm,
+            "camera_block": sh.camera_block, "ms": sh.ms}
 
 
 class Batch:

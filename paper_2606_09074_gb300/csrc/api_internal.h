@@ -234,6 +234,8 @@ struct ScenePlan {
     int64_t n = 0;
     int V = 0;        // views scored
     int vstride = 1;  // input camera stride (view subsampling)
+    int vpp = kViewsPerPass;  // views per pass (the camera block)
+    int passes = 1;
     bool multipass = false;
     int nb = 1;    // feature-pass blocks
     int bits = 4;  // processing-order grid resolution
@@ -252,18 +254,21 @@ struct SceneScratch {
     uint32_t *perm;
     unsigned long long *need;
     unsigned long long *tiles;  // k_score's tile counter
-    float *running;
+    float2 *running;  // (sum, compensation) per primitive between passes
 };
 
 // V input cameras; with 0 < max_views < V every s-th view is scored,
-// s = ceil(V / max_views) (Table B.1's view subsampling).
-inline ScenePlan plan_scene(int64_t n, int V, int max_views = 0)
+// s = ceil(V / max_views) (Table B.1's view subsampling).  The views scored
+// are processed in passes of `vpp` (the camera block of the shape).
+inline ScenePlan plan_scene(int64_t n, int V, int max_views = 0, int vpp = kViewsPerPass)
 {
     ScenePlan pl;
     pl.n = n;
     pl.vstride = (max_views > 0 && V > max_views) ? (V + max_views - 1) / max_views : 1;
     pl.V = (V + pl.vstride - 1) / pl.vstride;
-    pl.multipass = pl.V > kViewsPerPass;
+    pl.vpp = vpp;
+    pl.passes = (pl.V + vpp - 1) / vpp;
+    pl.multipass = pl.passes > 1;
     pl.nb = feature_blocks(pl.n);
     pl.bits = cell_bits_for(pl.n);
     return pl;
@@ -277,7 +282,7 @@ inline size_t scene_bytes(const ScenePlan &pl)
                        sizeof(unsigned) * (cells + 64), sizeof(unsigned) * cells,
                        sizeof(unsigned) * (cells / kScanCells), sizeof(uint32_t) * n,
                        kCountSlots * sizeof(unsigned long long), sizeof(unsigned long long),
-                       pl.multipass ? sizeof(float) * n : 0});
+                       pl.multipass ? sizeof(float2) * n : 0});
 }
 
 inline SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
@@ -297,7 +302,7 @@ inline SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
     x.perm = cv.take<uint32_t>(n);
     x.need = cv.take<unsigned long long>(kCountSlots);
     x.tiles = cv.take<unsigned long long>(1);
-    x.running = pl.multipass ? cv.take<float>(n) : nullptr;
+    x.running = pl.multipass ? cv.take<float2>(n) : nullptr;
     return x;
 }
 
@@ -343,7 +348,7 @@ inline ScoreLaunch make_score_launch(const refine_scene *sc, const ScenePlan &pl
     a.perm = x.perm;
     a.n = pl.n;
     a.cams = x.cams + v0;
-    a.vcount = pl.V - v0 < kViewsPerPass ? pl.V - v0 : kViewsPerPass;
+    a.vcount = pl.V - v0 < pl.vpp ? pl.V - v0 : pl.vpp;
     a.first = v0 == 0;
     a.last = v0 + a.vcount >= pl.V;
     a.eta = p.eta;
@@ -380,7 +385,7 @@ inline refine_status score_impl(refine_ctx *c, const refine_scene *sc, const ref
     if (pin) p = *pin; else refine_params_default(&p);
     refine_status st = check_score_args(c, sc, cams, V, p, scores);
     if (st || sc->n == 0) return st;
-    const ScenePlan pl = plan_scene(sc->n, V, p.max_views);
+    const ScenePlan pl = plan_scene(sc->n, V, p.max_views, c->shape.views_per_pass);
     if ((st = ensure(c, c->score, scene_bytes(pl)))) return st;
     Carver cv(c->score.p);
     const SceneScratch x = carve_scene(cv, pl);
@@ -388,7 +393,7 @@ inline refine_status score_impl(refine_ctx *c, const refine_scene *sc, const ref
     if (need_dev) *need_dev = x.need;
     auto run = [&](int cls, auto &&f) { return launch(c, cls, s, f); };
     if ((st = enqueue_prep(c, run, sc, cams, pl, x, p, need_dev != nullptr, c->d_status, s))) return st;
-    for (int v0 = 0; v0 < pl.V; v0 += kViewsPerPass) {
+    for (int v0 = 0; v0 < pl.V; v0 += pl.vpp) {
         ScoreLaunch a = make_score_launch(sc, pl, x, p, v0, scores, view_sum, need_dev != nullptr, c->d_status);
         a.grid = score_grid(c->num_sms, pl.n, a.vcount, c->shape);
         a.tiles_taken = x.tiles;

@@ -10,9 +10,11 @@
 
 namespace refine {
 
-// Cameras processed per score launch (144 bytes each in shared memory).  A
-// larger view set is split into passes of this size; pass boundaries fall
-// on multiples of 32 views so the summation order is independent of it.
+// Cameras processed per score launch at most (144 bytes each in shared
+// memory).  A larger view set is split into passes (camera blocks) of
+// ScoreShape::views_per_pass views, a multiple of 32; a primitive's running
+// Kahan pair (sum, compensation) is carried from pass to pass, so its sum
+// is the same whatever the block size.
 constexpr int kViewsPerPass = 512;
 constexpr int kScoreThreads = 256;     // threads per CTA of k_score
 
@@ -24,6 +26,7 @@ struct ScoreShape {
     int gpt = 2;          // primitives per thread: a warp's tile is 32 * gpt primitives (1 or 2)
     int threads = 256;    // threads per CTA of the batched kernel (128 or 256); k_score uses kScoreThreads
     int ctas_per_sm = 0;  // cap on resident CTAs per SM of the batched kernel (0 = as many as fit)
+    int views_per_pass = kViewsPerPass;  // camera block: views per score pass (32..512, a multiple of 32)
 };
 bool shape_valid(const ScoreShape &sh);
 // An item of the batched kernel: kBatchRounds warp tiles per warp of the
@@ -98,7 +101,7 @@ struct ScoreLaunch {
     float inv_views;            // 1 / |V|
     int flags;
     const SceneConsts *consts;
-    float *running;             // per-primitive running view sum between passes
+    float2 *running;            // per-primitive running (sum, Kahan compensation) between passes
     float *scores;
     float *view_sum;            // optional
     unsigned long long *need;   // optional diagnostic counters (kCountSlots), see k_score

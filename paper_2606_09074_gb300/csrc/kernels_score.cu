@@ -864,7 +864,11 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
             idx[g] = i;
             const PrimRec *r = a.recs + i;
             ra = __ldg(&r->a); rb = __ldg(&r->b); rc = __ldg(&r->c); rd = __ldg(&r->d);
-            if (!a.first) acc[g] = a.running[i];
+            if (!a.first) {
+                const float2 run = a.running[i];
+                acc[g] = run.x;
+                comp[g] = run.y;
+            }
         }
         p[g].mx = ra.x; p[g].my = ra.y; p[g].mz = ra.z; p[g].b2 = ra.w;
         p[g].L[0] = rb.x; p[g].L[1] = rb.y; p[g].L[2] = rb.z; p[g].L[3] = rb.w;
@@ -902,11 +906,11 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
     for (int g = 0; g < GPT; ++g) {
         const int64_t i = idx[g];
         if (i < 0) continue;
-        const float Ssum = acc[g] - comp[g];
         if (!a.last) {
-            a.running[i] = Ssum;
+            a.running[i] = make_float2(acc[g], comp[g]);
             continue;
         }
+        const float Ssum = acc[g] - comp[g];
         if (a.view_sum) a.view_sum[i] = Ssum;
         const float4 rd = __ldg(&a.recs[i].d);  // (L8, alpha, m_gem, m_col)
         const float coupled = fmaf(sc.kappa[0], rd.z, fmaf(sc.kappa[1], rd.w, sc.kappa[2] * rd.y));
@@ -1139,7 +1143,8 @@ static const void *pick_score(int pm, bool count, int gpt)
 
 bool shape_valid(const ScoreShape &sh)
 {
-    return (sh.gpt == 1 || sh.gpt == 2) && (sh.threads == 128 || sh.threads == 256);
+    return (sh.gpt == 1 || sh.gpt == 2) && (sh.threads == 128 || sh.threads == 256) && sh.ctas_per_sm >= 0 &&
+           sh.views_per_pass >= 32 && sh.views_per_pass <= kViewsPerPass && sh.views_per_pass % 32 == 0;
 }
 
 int score_grid(int num_sms, int64_t n, int vcount, const ScoreShape &sh)

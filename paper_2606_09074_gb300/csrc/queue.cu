@@ -143,11 +143,11 @@ struct refine_queue {
 
 namespace {
 
-uint64_t footprint_of(int64_t n, int dtype, int V, double ratio, bool compact)
+// V input cameras; pl the request's plan (views scored, camera block).
+uint64_t footprint_of(int64_t n, int dtype, int V, const ScenePlan &pl, double ratio, bool compact)
 {
     const size_t S = (size_t)dev_stride(n), es = elem_size(dtype);
     const int64_t nk = keep_count(n, ratio);
-    const ScenePlan pl = plan_scene(n, V);
     const size_t parts = carve_size({3 * S * 4, 56 * S * es, sizeof(refine_camera) * (size_t)V, 4 * (size_t)n,
                                      4 * (size_t)((n + 31) / 32), compact ? 3 * (size_t)nk * 4 : 0,
                                      compact ? 56 * (size_t)nk * es : 0, compact ? 4 * (size_t)nk : 0, 256});
@@ -281,7 +281,7 @@ void issue_round(refine_queue *q, std::vector<QJob *> &round)
             R.h_launch[i] = make_score_launch(&j->scene, j->plan, j->sx, j->params, 0, j->scores, nullptr, false,
                                               j->status);
             R.h_tb[i + 1] = R.h_tb[i] + (j->req.n + tile - 1) / tile;
-            max_v = std::max(max_v, j->plan.V);
+            max_v = std::max(max_v, R.h_launch[i].vcount);
         }
         const int k = (int)live.size();
         cudaStream_t m = q->score_stream;
@@ -304,6 +304,20 @@ void issue_round(refine_queue *q, std::vector<QJob *> &round)
             if (grid > bl.total_tiles) grid = (int)bl.total_tiles;
             e = launch_score_batch(bl, max_v, grid, q->shape, m);
             if (e == cudaSuccess) q->launches.fetch_add(1, std::memory_order_relaxed);
+        }
+        // Further camera blocks of requests with more views than one block:
+        // per-request launches of the plain score kernel, in block order,
+        // after the batched launch (which scored every first block).
+        for (QJob *j : live) {
+            for (int v0 = j->plan.vpp; v0 < j->plan.V && e == cudaSuccess; v0 += j->plan.vpp) {
+                ScoreLaunch a = make_score_launch(&j->scene, j->plan, j->sx, j->params, v0, j->scores, nullptr, false,
+                                                  j->status);
+                a.grid = score_grid(q->pc.num_sms, j->plan.n, a.vcount, q->shape);
+                a.tiles_taken = j->sx.tiles;
+                e = cudaMemsetAsync(j->sx.tiles, 0, sizeof(unsigned long long), m);
+                if (e == cudaSuccess) e = launch_score(a, q->shape, m);
+                if (e == cudaSuccess) q->launches.fetch_add(1, std::memory_order_relaxed);
+            }
         }
         if (e == cudaSuccess) e = cudaEventRecord(R.scored, m);
         if (e != cudaSuccess) st = cuda_fail(&q->pc, e, "queue: batched score");
@@ -479,9 +493,11 @@ extern "C" {
 uint64_t refine_queue_footprint(int64_t n, int32_t dtype, int32_t n_views, double ratio, int32_t compact)
 {
     if (n < 1 || n > INT32_MAX || (dtype != REFINE_F32 && dtype != REFINE_BF16) || n_views < 1 ||
-        n_views > kViewsPerPass || !(ratio >= 0.0 && ratio < 1.0))
+        n_views > 65535 || !(ratio >= 0.0 && ratio < 1.0))
         return 0;
-    return footprint_of(n, dtype, n_views, ratio, compact != 0);
+    // the smallest camera block: the running sums are included whenever a
+    // scene could take more than one pass
+    return footprint_of(n, dtype, n_views, plan_scene(n, n_views, 0, 32), ratio, compact != 0);
 }
 
 refine_status refine_queue_create(refine_ctx *c, uint64_t hbm_budget_bytes, int32_t max_slots,
@@ -579,16 +595,15 @@ refine_status refine_queue_submit(refine_queue *q, const refine_request *req, ui
     j->req = r;
     j->params = r.params ? *r.params : q->params;
     if (!(j->params.eta > 0.f) || !isfinite(j->params.eta) || j->params.e_ln_gem == 0.0 || j->params.e_col == 0.0 ||
-        j->params.e_opa == 0.0 || j->params.max_views < 0 ||
-        plan_scene(r.n, r.n_views, j->params.max_views).V > kViewsPerPass) {
+        j->params.e_opa == 0.0 || j->params.max_views < 0) {
         delete j;
         return REFINE_EINVAL;
     }
     j->req.params = nullptr;
     j->n_keep = keep_count(r.n, r.ratio);
     j->compact = r.out_pos_host != nullptr;
-    j->footprint = footprint_of(r.n, r.dtype, r.n_views, r.ratio, j->compact);
-    j->plan = plan_scene(r.n, r.n_views, j->params.max_views);
+    j->plan = plan_scene(r.n, r.n_views, j->params.max_views, q->shape.views_per_pass);
+    j->footprint = footprint_of(r.n, r.dtype, r.n_views, j->plan, r.ratio, j->compact);
     j->pinned_out = is_pinned(r.keep_mask_host) && is_pinned(r.scores_host) && is_pinned(r.out_pos_host) &&
                     is_pinned(r.out_attr_host) && is_pinned(r.kept_idx_host);
     if (j->footprint > q->budget) {

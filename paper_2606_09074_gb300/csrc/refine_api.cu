@@ -324,12 +324,19 @@ struct refine_batch {
     std::vector<long long *> total;
     void *scratch = nullptr;
     void *h_res = nullptr;  // pinned read-back area
-    ScoreLaunch *d_launch = nullptr;
-    long long *d_tile_begin = nullptr;
-    unsigned long long *d_counter = nullptr;
-    long long total_tiles = 0;
-    int max_v = 0;
-    int grid = 1;
+    // One batched score launch per pass level: level p scores views
+    // [p vpp, (p + 1) vpp) of every scene with more than p passes, so a
+    // scene's passes run in order, as refine_score runs them.
+    struct Level {
+        ScoreLaunch *d_launch = nullptr;       // [scenes] this pass of each scene taking part
+        long long *d_tile_begin = nullptr;     // [scenes + 1]
+        unsigned long long *d_counter = nullptr;
+        std::vector<int> jobs;                 // the scenes taking part
+        long long total_tiles = 0;
+        int max_v = 0;                         // largest camera block of the level
+        int grid = 1;
+    };
+    std::vector<Level> levels;
     ScoreShape shape;
     cudaStream_t main = nullptr;
     std::vector<cudaStream_t> lanes;
@@ -359,7 +366,9 @@ refine_status batch_record(refine_batch *b)
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamBeginCapture");
     refine_status st = REFINE_OK;
     cudaEvent_t fork = b->events[0], fork2 = b->events[1 + L];
-    e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), m);
+    e = cudaSuccess;
+    for (const refine_batch::Level &lv : b->levels)
+        if (e == cudaSuccess) e = cudaMemsetAsync(lv.d_counter, 0, sizeof(unsigned long long), m);
     if (e == cudaSuccess) e = cudaEventRecord(fork, m);
     for (int l = 0; l < L && e == cudaSuccess && !st; ++l) {
         cudaStream_t ls = b->lanes[l];
@@ -370,15 +379,16 @@ refine_status batch_record(refine_batch *b)
         if (e == cudaSuccess && !st) e = cudaEventRecord(b->events[1 + l], ls);
     }
     for (int l = 0; l < L && e == cudaSuccess && !st; ++l) e = cudaStreamWaitEvent(m, b->events[1 + l], 0);
-    if (e == cudaSuccess && !st) {
+    for (const refine_batch::Level &lv : b->levels) {
+        if (e != cudaSuccess || st) break;
         BatchLaunch bl;
-        bl.scenes = b->d_launch;
-        bl.tile_begin = b->d_tile_begin;
-        bl.n_scenes = S;
-        bl.total_tiles = b->total_tiles;
-        bl.counter = b->d_counter;
+        bl.scenes = lv.d_launch;
+        bl.tile_begin = lv.d_tile_begin;
+        bl.n_scenes = (int)lv.jobs.size();
+        bl.total_tiles = lv.total_tiles;
+        bl.counter = lv.d_counter;
         bl.status = c->d_status;
-        e = launch_score_batch(bl, b->max_v, b->grid, b->shape, m);
+        e = launch_score_batch(bl, lv.max_v, lv.grid, b->shape, m);
         if (e == cudaSuccess) ++launches;
     }
     if (e == cudaSuccess && !st) e = cudaEventRecord(fork2, m);
@@ -417,6 +427,22 @@ refine_status batch_record(refine_batch *b)
     return REFINE_OK;
 }
 
+// Tile prefix of a level for the work-item size of `sh`, copied to the
+// device (on `s`, or synchronously when s is NULL), and its grid.
+cudaError_t set_level_tiles(refine_batch *b, refine_batch::Level &lv, const ScoreShape &sh, cudaStream_t s)
+{
+    const long long tile = batch_tile(sh);
+    std::vector<long long> tb(lv.jobs.size() + 1, 0);
+    for (size_t k = 0; k < lv.jobs.size(); ++k) tb[k + 1] = tb[k] + (b->jobs[lv.jobs[k]].scene.n + tile - 1) / tile;
+    lv.total_tiles = tb.back();
+    lv.grid = score_batch_grid(b->ctx->num_sms, lv.max_v, sh);
+    if (lv.grid > lv.total_tiles) lv.grid = (int)lv.total_tiles;
+    if (lv.grid < 1) lv.grid = 1;
+    const size_t bytes = sizeof(long long) * tb.size();
+    return s ? cudaMemcpyAsync(lv.d_tile_begin, tb.data(), bytes, cudaMemcpyHostToDevice, s)
+             : cudaMemcpy(lv.d_tile_begin, tb.data(), bytes, cudaMemcpyHostToDevice);
+}
+
 void batch_free(refine_batch *b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -449,22 +475,19 @@ refine_status refine_batch_create(refine_ctx *c, const refine_job *jobs, int32_t
     b->ctx = c;
     b->params = p;
     b->jobs.assign(jobs, jobs + S);
-    size_t total = carve_size({sizeof(ScoreLaunch) * (size_t)S, sizeof(long long) * (size_t)(S + 1),
-                               sizeof(unsigned long long)});
+    b->shape = c->shape;
+    size_t total = 0;
+    int max_passes = 1;
     for (int j = 0; j < S; ++j) {
         const refine_job &jb = jobs[j];
         if ((st = check_score_args(c, &jb.scene, jb.cams_dev, jb.n_views, p, jb.scores_dev))) {
             delete b;
             return fail(c, st, "batch job %d: %s", j, std::string(c->err).c_str());
         }
-        const ScenePlan jp = plan_scene(jb.scene.n, jb.n_views, p.max_views);
-        if (jb.scene.n < 1 || jp.V > kViewsPerPass || !jb.keep_mask_dev ||
-            !(jb.ratio >= 0.0 && jb.ratio < 1.0)) {
+        const ScenePlan jp = plan_scene(jb.scene.n, jb.n_views, p.max_views, b->shape.views_per_pass);
+        if (jb.scene.n < 1 || !jb.keep_mask_dev || !(jb.ratio >= 0.0 && jb.ratio < 1.0)) {
             delete b;
-            return fail(c, REFINE_EINVAL,
-                        "batch job %d: needs n >= 1, at most %d views scored, a keep mask and a ratio "
-                        "in [0, 1)",
-                        j, kViewsPerPass);
+            return fail(c, REFINE_EINVAL, "batch job %d: needs n >= 1, a keep mask and a ratio in [0, 1)", j);
         }
         const int64_t nk = jb.scene.n - (int64_t)floor(jb.ratio * (double)jb.scene.n);
         if (jb.out_pos_dev && (!jb.out_attr_dev || jb.out_row_stride < nk)) {
@@ -474,8 +497,11 @@ refine_status refine_batch_create(refine_ctx *c, const refine_job *jobs, int32_t
         b->n_keep.push_back(nk);
         b->plans.push_back(jp);
         total += scene_bytes(b->plans.back()) + select_bytes(jb.scene.n) + compact_bytes(jb.scene.n) + 768;
-        b->max_v = std::max(b->max_v, jp.V);
+        max_passes = std::max(max_passes, jp.passes);
     }
+    for (int lv = 0; lv < max_passes; ++lv)
+        total += carve_size({sizeof(ScoreLaunch) * (size_t)S, sizeof(long long) * (size_t)(S + 1),
+                             sizeof(unsigned long long)});
     cudaError_t e = cudaMalloc(&b->scratch, total);
     if (e != cudaSuccess) {
         delete b;
@@ -486,28 +512,34 @@ refine_status refine_batch_create(refine_ctx *c, const refine_job *jobs, int32_t
         return cuda_fail(c, e, "batch pinned read-back");
     }
     Carver cv(b->scratch);
-    b->d_launch = cv.take<ScoreLaunch>(S);
-    b->d_tile_begin = cv.take<long long>(S + 1);
-    b->d_counter = cv.take<unsigned long long>(1);
-    std::vector<ScoreLaunch> hl(S);
-    std::vector<long long> tb(S + 1, 0);
-    b->shape = c->shape;
-    const long long tile = batch_tile(b->shape);
+    b->levels.resize(max_passes);
+    for (refine_batch::Level &lv : b->levels) {
+        lv.d_launch = cv.take<ScoreLaunch>(S);
+        lv.d_tile_begin = cv.take<long long>(S + 1);
+        lv.d_counter = cv.take<unsigned long long>(1);
+    }
     for (int j = 0; j < S; ++j) {
         b->sx.push_back(carve_scene(cv, b->plans[j]));
         b->sel_scr.push_back(cv.take<char>(select_bytes(jobs[j].scene.n)));
         b->cmp_scr.push_back(cv.take<char>(compact_bytes(jobs[j].scene.n)));
-        hl[j] = make_score_launch(&jobs[j].scene, b->plans[j], b->sx[j], p, 0, jobs[j].scores_dev, nullptr, false,
-                                  c->d_status);
-        tb[j + 1] = tb[j] + (jobs[j].scene.n + tile - 1) / tile;
     }
     b->kstar.assign(S, nullptr);
     b->total.assign(S, nullptr);
-    b->total_tiles = tb[S];
-    e = cudaMemcpy(b->d_launch, hl.data(), sizeof(ScoreLaunch) * S, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_tile_begin, tb.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice);
-    b->grid = score_batch_grid(c->num_sms, b->max_v, b->shape);
-    if (b->grid > b->total_tiles) b->grid = (int)b->total_tiles;
+    e = cudaSuccess;
+    for (int l = 0; l < max_passes && e == cudaSuccess; ++l) {
+        refine_batch::Level &lv = b->levels[l];
+        std::vector<ScoreLaunch> hl;
+        for (int j = 0; j < S; ++j) {
+            if (b->plans[j].passes <= l) continue;
+            const int v0 = l * b->plans[j].vpp;
+            hl.push_back(make_score_launch(&jobs[j].scene, b->plans[j], b->sx[j], p, v0, jobs[j].scores_dev, nullptr,
+                                           false, c->d_status));
+            lv.jobs.push_back(j);
+            lv.max_v = std::max(lv.max_v, hl.back().vcount);
+        }
+        e = cudaMemcpy(lv.d_launch, hl.data(), sizeof(ScoreLaunch) * hl.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = set_level_tiles(b, lv, b->shape, nullptr);
+    }
     const int L = std::min(8, S);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->main, cudaStreamNonBlocking);
     for (int l = 0; l < L && e == cudaSuccess; ++l) {
@@ -585,17 +617,20 @@ refine_shape shape_to_abi(const ScoreShape &sh, double ms)
     r.tile = 32 * sh.gpt;
     r.cta_threads = sh.threads;
     r.ctas_per_sm = sh.ctas_per_sm;
+    r.camera_block = sh.views_per_pass;
     r.ms = ms;
     return r;
 }
 
 bool shape_from_abi(const refine_shape &r, ScoreShape *sh)
 {
-    if ((r.tile != 32 && r.tile != 64) || (r.cta_threads != 128 && r.cta_threads != 256) || r.ctas_per_sm < 0)
-        return false;
-    sh->gpt = r.tile / 32;
-    sh->threads = r.cta_threads;
-    sh->ctas_per_sm = r.ctas_per_sm;
+    ScoreShape t;
+    t.gpt = r.tile / 32;
+    t.threads = r.cta_threads;
+    t.ctas_per_sm = r.ctas_per_sm;
+    t.views_per_pass = r.camera_block;
+    if ((r.tile != 32 && r.tile != 64) || !shape_valid(t)) return false;
+    *sh = t;
     return true;
 }
 
@@ -614,7 +649,9 @@ refine_status refine_ctx_set_shape(refine_ctx *c, const refine_shape *shape)
 {
     if (!c || !shape) return REFINE_EINVAL;
     ScoreShape sh;
-    if (!shape_from_abi(*shape, &sh)) return fail(c, REFINE_EINVAL, "shape: tile 32|64, cta_threads 128|256");
+    if (!shape_from_abi(*shape, &sh))
+        return fail(c, REFINE_EINVAL,
+                    "shape: tile 32|64, cta_threads 128|256, ctas_per_sm >= 0, camera_block 32..512 in steps of 32");
     c->shape = sh;
     return REFINE_OK;
 }
@@ -625,74 +662,89 @@ refine_status refine_autotune(refine_ctx *c, const refine_job *jobs, int32_t n_j
 {
     if (!c) return REFINE_EINVAL;
     if (reps < 1) return fail(c, REFINE_EINVAL, "autotune: reps must be >= 1");
-    refine_batch *b = nullptr;
-    refine_status st = refine_batch_create(c, jobs, n_jobs, params, &b);
-    if (st) return st;
-    cudaStream_t m = b->main;
-    auto run = [c](int cls, auto &&f) -> refine_status {
-        const cudaError_t e = f();
-        return e == cudaSuccess ? REFINE_OK : cuda_fail(c, e, kClassName[cls]);
-    };
-    const int S = (int)b->jobs.size();
-    for (int j = 0; j < S && !st; ++j)
-        st = enqueue_prep(c, run, &b->jobs[j].scene, b->jobs[j].cams_dev, b->plans[j], b->sx[j], b->params, false,
-                          c->d_status, m);
+    if (!jobs || n_jobs < 1) return fail(c, REFINE_EINVAL, "autotune: no jobs");
+    const ScoreShape keep = c->shape;
     std::vector<ScoreShape> cand;
-    for (int gpt : {2, 1})
-        for (int threads : {256, 128})
-            for (int cap : {0, threads == 256 ? 2 : 4}) {
-                ScoreShape sh;
-                sh.gpt = gpt;
-                sh.threads = threads;
-                sh.ctas_per_sm = cap;
-                cand.push_back(sh);
-            }
+    std::vector<double> ms;
+    std::vector<std::vector<int>> seen;  // passes per scene of each camera block tried
+    refine_status st = REFINE_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    std::vector<double> ms(cand.size(), 0.0);
-    std::vector<long long> tb(S + 1, 0);
-    for (size_t k = 0; k < cand.size() && e == cudaSuccess && !st; ++k) {
-        const ScoreShape &sh = cand[k];
-        const long long tile = batch_tile(sh);
-        for (int j = 0; j < S; ++j) tb[j + 1] = tb[j] + (b->jobs[j].scene.n + tile - 1) / tile;
-        e = cudaMemcpyAsync(b->d_tile_begin, tb.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice, m);
-        BatchLaunch bl;
-        bl.scenes = b->d_launch;
-        bl.tile_begin = b->d_tile_begin;
-        bl.n_scenes = S;
-        bl.total_tiles = tb[S];
-        bl.counter = b->d_counter;
-        bl.status = c->d_status;
-        int grid = score_batch_grid(c->num_sms, b->max_v, sh);
-        if (grid > bl.total_tiles) grid = (int)bl.total_tiles;
-        for (int r = -1; r < reps && e == cudaSuccess; ++r) {
-            if (r == 0) e = cudaEventRecord(e0, m);
-            if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), m);
-            if (e == cudaSuccess) e = launch_score_batch(bl, b->max_v, grid, sh, m);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "autotune events");
+    // Camera blocks (views per pass) that change how some scene is split.
+    for (int vpp : {512, 256, 128}) {
+        if (st) break;
+        std::vector<int> passes;
+        for (int j = 0; j < n_jobs; ++j) {
+            const int mv = params ? params->max_views : 0;
+            passes.push_back(plan_scene(jobs[j].scene.n, jobs[j].n_views, mv, vpp).passes);
         }
-        if (e == cudaSuccess) e = cudaEventRecord(e1, m);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float t = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-        ms[k] = (double)t / reps;
+        if (std::find(seen.begin(), seen.end(), passes) != seen.end()) continue;
+        seen.push_back(passes);
+        c->shape.views_per_pass = vpp;
+        refine_batch *b = nullptr;
+        if ((st = refine_batch_create(c, jobs, n_jobs, params, &b))) break;
+        cudaStream_t m = b->main;
+        auto run = [c](int cls, auto &&f) -> refine_status {
+            const cudaError_t err = f();
+            return err == cudaSuccess ? REFINE_OK : cuda_fail(c, err, kClassName[cls]);
+        };
+        const int S = (int)b->jobs.size();
+        for (int j = 0; j < S && !st; ++j)
+            st = enqueue_prep(c, run, &b->jobs[j].scene, b->jobs[j].cams_dev, b->plans[j], b->sx[j], b->params, false,
+                              c->d_status, m);
+        for (int gpt : {2, 1})
+            for (int threads : {256, 128})
+                for (int cap : {0, threads == 256 ? 2 : 4}) {
+                    if (st || e != cudaSuccess) break;
+                    ScoreShape sh;
+                    sh.gpt = gpt;
+                    sh.threads = threads;
+                    sh.ctas_per_sm = cap;
+                    sh.views_per_pass = vpp;
+                    for (refine_batch::Level &lv : b->levels)
+                        if (e == cudaSuccess) e = set_level_tiles(b, lv, sh, m);
+                    // one warm-up run, then `reps` timed runs of every level's launch
+                    for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+                        if (r == 0) e = cudaEventRecord(e0, m);
+                        for (const refine_batch::Level &lv : b->levels) {
+                            if (e != cudaSuccess) break;
+                            BatchLaunch bl;
+                            bl.scenes = lv.d_launch;
+                            bl.tile_begin = lv.d_tile_begin;
+                            bl.n_scenes = (int)lv.jobs.size();
+                            bl.total_tiles = lv.total_tiles;
+                            bl.counter = lv.d_counter;
+                            bl.status = c->d_status;
+                            e = cudaMemsetAsync(lv.d_counter, 0, sizeof(unsigned long long), m);
+                            if (e == cudaSuccess) e = launch_score_batch(bl, lv.max_v, lv.grid, sh, m);
+                        }
+                    }
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, m);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float t = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                    cand.push_back(sh);
+                    ms.push_back((double)t / reps);
+                }
+        if (e != cudaSuccess && !st) st = cuda_fail(c, e, "autotune");
+        if (!st) st = read_status(c, m);
+        refine_batch_destroy(b);
     }
-    if (e != cudaSuccess && !st) st = cuda_fail(c, e, "autotune");
-    if (!st) st = read_status(c, m);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (!st) {
-        size_t best = 0;
-        for (size_t k = 1; k < cand.size(); ++k)
-            if (ms[k] < ms[best]) best = k;
-        c->shape = cand[best];
-        if (best_out) *best_out = shape_to_abi(cand[best], ms[best]);
-        if (table_out)
-            for (size_t k = 0; k < cand.size() && (int)k < table_cap; ++k) table_out[k] = shape_to_abi(cand[k], ms[k]);
-        if (table_count) *table_count = (int32_t)cand.size();
-    }
-    refine_batch_destroy(b);
-    return st;
+    c->shape = keep;
+    if (st) return st;
+    size_t best = 0;
+    for (size_t k = 1; k < cand.size(); ++k)
+        if (ms[k] < ms[best]) best = k;
+    c->shape = cand[best];
+    if (best_out) *best_out = shape_to_abi(cand[best], ms[best]);
+    if (table_out)
+        for (size_t k = 0; k < cand.size() && (int)k < table_cap; ++k) table_out[k] = shape_to_abi(cand[k], ms[k]);
+    if (table_count) *table_count = (int32_t)cand.size();
+    return REFINE_OK;
 }
 
 }  // extern "C"

@@ -1,18 +1,15 @@
 // refine_select_noalloc: ratio pruning for callers that must not allocate.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// stream capture that must not add allocation nodes, plugins hosted by an
-// engine that owns every device allocation, and real-time loops whose
-// memory is fixed at start-up.  They cannot create a refine_ctx either
-// (creating one allocates).  This entry point runs the same radix-select
+// Some callers cannot call cudaMalloc at all: plug-ins hosted by an engine
+// that owns every device allocation, and real-time loops whose memory is
+// fixed at start-up.  They cannot create a refine_ctx either (creating one
+// allocates).  This entry point runs the same radix-select
 // kernels as refine_select, but its scratch -- the histogram/selection state
 // and the per-segment tie counts -- lives in the fixed device array below,
 // which every GPU that loads the library holds until the process exits.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
-
-#include <mutex>
 
 #include "internal.h"
 
@@ -33,10 +30,6 @@ struct NoallocScratch {
 
 // The scratch (about 74 KB).  Shared by every call on a device.
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
-
-// Device address of g_noalloc_scratch per device, looked up once.
-std::mutex g_mu;
-NoallocScratch *g_addr[256];
 
 void put_err(char *buf, size_t len, const char *msg)
 {
@@ -74,29 +67,26 @@ extern "C" refine_status refine_select_noalloc(const float *scores_dev, int64_t 
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
         put_err(errbuf, errlen, "refine_select_noalloc: no current CUDA device");
         return REFINE_ECUDA;
     }
-    NoallocScratch *scr = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
-            // One-time set-up on this device (the device is current here).
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                char m[200];
-                snprintf(m, sizeof m, "refine_select_noalloc: cudaGetSymbolAddress failed: %s",
-                         cudaGetErrorString(e));
-                put_err(errbuf, errlen, m);
-                return REFINE_ECUDA;
-            }
-            g_addr[dev] = static_cast<NoallocScratch *>(p);
-        }
-        scr = g_addr[dev];
+    // The array's device address on the current device, looked up on every
+    // call (after the first call on a device, which loads the library's
+    // device code there, a host-side lookup), so that it always belongs to
+    // the device's current context.  In host code g_noalloc_scratch names a
+    // host-side stand-in, never the device memory.
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char m[200];
+        snprintf(m, sizeof m, "refine_select_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        put_err(errbuf, errlen, m);
+        return REFINE_ECUDA;
     }
+    NoallocScratch *scr = static_cast<NoallocScratch *>(p);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int num_sms = 0;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) num_sms = 1;

@@ -107,4 +107,8 @@ def test_queue_footprint_host_only(lib):
     assert fp(n, b.REFINE_F32, 200, 0.5, compact=False) < f32
     assert fp(2 * n, b.REFINE_F32, 200, 0.5) > f32
     assert fp(0, b.REFINE_F32, 200, 0.5) == 0 and fp(n, 7, 200, 0.5) == 0
-    assert fp(n, b.REFINE_F32, 513, 0.5) == 0 and fp(n, b.REFINE_F32, 200, 1.0) == 0
+    # sized for the smallest camera block (32 views): from 33 views on a scene may take several passes and
+    # then holds a running (sum, compensation) pair per primitive
+    assert fp(n, b.REFINE_F32, 33, 0.5) >= fp(n, b.REFINE_F32, 32, 0.5) + 8 * n
+    assert fp(n, b.REFINE_F32, 1100, 0.5) > fp(n, b.REFINE_F32, 200, 0.5)
+    assert fp(n, b.REFINE_F32, 65536, 0.5) == 0 and fp(n, b.REFINE_F32, 200, 1.0) == 0

@@ -1,10 +1,11 @@
 """refine_select_noalloc: the allocation-free selection entry point for
-callers that cannot call cudaMalloc (graph capture without allocation
-nodes, engines that own all device memory, fixed-memory real-time loops).
-Its keep mask, threshold and kept count must equal refine_select's on the
-same scores, on two calls in a row through the C ABI (the fixed scratch
-array is reused and must be reset by each call).  This file is collected
-last so that a run stopping at the first failure has run every other test."""
+callers that cannot call cudaMalloc (engines that own all device memory,
+fixed-memory real-time loops).  Its keep mask, threshold and kept count must
+equal refine_select's on the same scores, on two calls in a row through the
+C ABI (the fixed scratch array is reused and must be reset by each call),
+also with nothing pruned and without the threshold read-back.  This file is
+collected last so that a run stopping at the first failure has run every
+other test."""
 import ctypes as C
 import math
 
@@ -49,6 +50,23 @@ def test_noalloc_matches_select_twice():
         assert nk == nk_b == n - math.floor(ratio * n)
         assert thr == thr_b
         assert torch.equal(mask_a, mask_b[:words])
+    # ratio 0: nothing pruned, every bit of the mask set; no threshold read-back
+    s = torch.from_numpy(cases[0][0]).to(dev)
+    n = s.numel()
+    words = (n + 31) // 32
+    mask_z = torch.zeros(words, dtype=torch.int32, device=dev)
+    st, thr, nk, err = _noalloc(rb, s, 0.0, mask_z, stream)
+    assert st == rb.REFINE_OK and nk == n and thr == -math.inf, err
+    mask_r, _, _ = ctx.select(s, 0.0)
+    assert torch.equal(mask_z, mask_r[:words])
+    mask_n = torch.zeros(words, dtype=torch.int32, device=dev)
+    nk_c = C.c_int64()
+    err_b = C.create_string_buffer(256)
+    st = rb.refine_select_noalloc(C.c_void_p(s.data_ptr()), n, 0.5, C.c_void_p(mask_n.data_ptr()), None,
+                                  C.byref(nk_c), err_b, C.sizeof(err_b), C.c_void_p(stream.cuda_stream))
+    torch.cuda.synchronize(dev)
+    mask_h, _, _ = ctx.select(s, 0.5)
+    assert st == rb.REFINE_OK and nk_c.value == n - n // 2 and torch.equal(mask_n, mask_h[:words])
     # sizes beyond the fixed scratch are refused with a message
     big = torch.empty(1, dtype=torch.float32, device=dev)
     thr = C.c_float()
