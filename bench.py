@@ -633,39 +633,38 @@ def _percentile(xs, q):
 
 
 class _OutputSets:
-    """Page-locked output buffers for the serving run: `copies` sets per
-    pool scene, each sized for the largest kept count (ratio 0.5)."""
+    """Page-locked output buffers for the serving run: `count` flat sets,
+    each large enough for the largest pool scene at ratio 0.5 (the queue
+    writes each output contiguously, so a larger buffer serves any job)."""
 
-    def __init__(self, torch, pool, copies):
+    def __init__(self, torch, n_max, count):
+        nk = n_max - n_max // 2
         self.free = []
         self.cv = threading.Condition()
-        for p, sc in enumerate(pool):
-            nk = sc["n"] - sc["n"] // 2
-            sets = []
-            for _ in range(copies):
-                sets.append({"mask": torch.empty((sc["n"] + 31) // 32, dtype=torch.int32, pin_memory=True),
-                             "out_pos": torch.empty(3 * nk, dtype=torch.float32, pin_memory=True),
-                             "out_attr": torch.empty(56 * nk, dtype=torch.bfloat16, pin_memory=True),
-                             "idx": torch.empty(nk, dtype=torch.int32, pin_memory=True)})
-            self.free.append(sets)
+        for _ in range(count):
+            self.free.append({"mask": torch.empty((n_max + 31) // 32, dtype=torch.int32, pin_memory=True),
+                              "out_pos": torch.empty(3 * nk, dtype=torch.float32, pin_memory=True),
+                              "out_attr": torch.empty(56 * nk, dtype=torch.bfloat16, pin_memory=True),
+                              "idx": torch.empty(nk, dtype=torch.int32, pin_memory=True)})
 
-    def take(self, p):
+    def take(self):
         with self.cv:
-            while not self.free[p]:
+            while not self.free:
                 self.cv.wait()
-            return self.free[p].pop()
+            return self.free.pop()
 
-    def give(self, p, s):
+    def give(self, s):
         with self.cv:
-            self.free[p].append(s)
+            self.free.append(s)
             self.cv.notify_all()
 
 
-def _serve_pass(torch, rb, ctx, pool, jobs, arrivals, budget, slots, outsets, keep_ref, agreement, agree_first=0):
-    """Submits `jobs` [(pool index, ratio)] at `arrivals` (seconds from the
-    start; None = as fast as output buffers allow) and collects them.
-    Returns per-job latencies (ms) and the wall time (s)."""
-    q = rb.Queue(ctx, budget_bytes=budget, max_slots=slots)
+def _serve_pass(torch, rb, pool, jobs, arrivals, q, outsets, on_done=None):
+    """Submits `jobs` [(pool index, ratio)] to queue `q` at `arrivals`
+    (seconds from the start; None = as fast as output buffers allow) and
+    collects them.  Returns per-job latencies (ms, arrival to the last output
+    byte in host memory), round sizes and the wall time (s).  on_done(k, p,
+    r, result, outputs) sees every job before its buffers are reused."""
     sub = []  # (ticket, pool index, ratio, outputs, arrival perf time, submit perf time)
     lock = threading.Lock()
     ready = threading.Semaphore(0)
@@ -678,7 +677,7 @@ def _serve_pass(torch, rb, ctx, pool, jobs, arrivals, budget, slots, outsets, ke
                 if delay > 0:
                     time.sleep(delay)
             t_arr = t_start + arrivals[k] if arrivals is not None else time.perf_counter()
-            outs = outsets.take(p)
+            outs = outsets.take()
             sc = pool[p]
             t_sub = time.perf_counter()
             t = q.submit(sc["pos"], sc["a16"], sc["cams"], r, outputs=outs, mask=True, compact=True)
@@ -689,66 +688,81 @@ def _serve_pass(torch, rb, ctx, pool, jobs, arrivals, budget, slots, outsets, ke
     th = threading.Thread(target=feeder, daemon=True)
     th.start()
     lat, rounds = [], []
-    for k in range(len(jobs)):
-        ready.acquire()
+    by_ticket, seen = {}, 0
+    for _ in range(len(jobs)):
+        ready.acquire()  # one more job submitted
+        ticket, res, _ = q.poll_any(timeout_ms=-1)  # results in completion order
         with lock:
-            t, p, r, outs, t_arr, t_sub = sub[k]
-        res, _ = q.poll(t, timeout_ms=-1)
+            while seen < len(sub):
+                by_ticket[sub[seen][0]] = (seen, sub[seen])
+                seen += 1
+            k, (t, p, r, outs, t_arr, t_sub) = by_ticket.pop(ticket)
         if res["status"] != 0:
             raise RuntimeError(f"serving job {k} failed: status {res['status']} {q.last_error()}")
         # queue clock: submit -> done; host clock: arrival -> submit
         lat.append(res["done_ms"] - res["submit_ms"] + (t_sub - t_arr) * 1000.0)
         rounds.append(res["round_size"])
-        if agreement is not None and (p, r) in keep_ref and k < agree_first:
-            nk = res["n_keep"]
-            keep = np.zeros(pool[p]["n"], dtype=bool)
-            keep[outs["idx"][:nk].numpy()] = True
-            agreement.append(float(np.mean(keep == keep_ref[(p, r)])))
-        outsets.give(p, outs)
+        if on_done is not None:
+            on_done(k, p, r, res, outs)
+        outsets.give(outs)
     wall = time.perf_counter() - t_start
     th.join()
-    st = q.stats()
-    q.close()
-    return lat, wall, rounds, st
+    return lat, rounds, wall
+
+
+def _pool_scene(seed):
+    """One serving-pool scene (FP32) in a worker process: positions, the
+    attribute rows, and the cameras."""
+    from paper_2606_09074_gb300 import synth
+    w = synth.job_scene(seed, dtype="f32")
+    return w.scene.pos, w.scene.attr, w.cams
+
+
+def _round_hist(rounds):
+    h = {}
+    for r in rounds:
+        h[str(r)] = h.get(str(r), 0) + 1
+    return dict(sorted(h.items(), key=lambda kv: int(kv[0])))
 
 
 def run_serve_mode(args):
-    """Serving workload: pruning jobs drawn as the 2,000-job stream (seeds
-    1000.., N log-uniform in [50k, 3.5M], V in 50..300, ratio from {0.5,
-    0.66, 0.9}, Poisson arrivals at 20/s from seed 999), served by the
-    request queue with BF16 storage from page-locked host memory, against the
-    plain FP32 per-scene path (refine_prune_host) as a single FIFO server."""
+    """Serving workload: `--jobs` pruning jobs (seeds 1000.., each with the
+    ratio its seed draws from {0.5, 0.66, 0.9}) arriving as a Poisson stream
+    at `--rate`/s (seed 999), served by the request queue with BF16 storage
+    from page-locked host memory, against the plain FP32 per-scene path
+    (refine_prune_host) as one FIFO server fed the same arrivals; then the
+    same jobs back to back (saturation), at the full HBM budget and at a
+    reduced one that makes admission bind.  Job k scores pool scene k mod
+    `--pool` (distinct seeded scenes drawn as in the batch workload, N
+    log-uniform in [50k, 3.5M]), generated ahead of the run."""
+    import multiprocessing as mp
+    from paper_2606_09074_gb300 import synth
+    P = args.pool
+    t_gen = time.perf_counter()
+    # generated in spawned workers before this process makes any CUDA call
+    with mp.get_context("spawn").Pool(max(1, min(P, (os.cpu_count() or 2) - 1))) as wp:
+        raw = wp.map(_pool_scene, [1000 + k for k in range(P)], chunksize=1)
+    t_gen = time.perf_counter() - t_gen
     import torch
     from paper_2606_09074_gb300 import binding as rb
-    from paper_2606_09074_gb300 import synth
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    P = args.pool
     pool = []
-    for k in range(P):
-        w = synth.job_scene(1000 + k, dtype="f32")
-        a16 = torch.from_numpy(synth.f32_to_bf16_bits(w.scene.attr).view(np.int16)).view(torch.bfloat16)
-        pool.append({"pos": torch.from_numpy(w.scene.pos).pin_memory(),
-                     "a32": torch.from_numpy(w.scene.attr).pin_memory(), "a16": a16.pin_memory(),
-                     "cams": w.cams, "n": w.scene.n, "V": len(w.cams)})
+    for pos, attr, cams in raw:
+        a16 = torch.from_numpy(synth.f32_to_bf16_bits(attr).view(np.int16)).view(torch.bfloat16)
+        pool.append({"pos": torch.from_numpy(pos).pin_memory(), "a32": torch.from_numpy(attr).pin_memory(),
+                     "a16": a16.pin_memory(), "cams": cams, "n": pos.shape[1], "V": len(cams)})
+    del raw
     ratio_of = lambda k: synth.job_spec(1000 + k)[3]  # noqa: E731
     jobs = [(k % P, ratio_of(k)) for k in range(args.jobs)]
     arrivals = synth.job_arrivals(args.jobs, rate=args.rate, seed=999)
     sat_jobs = [(k % P, ratio_of(k)) for k in range(args.sat_jobs)]
     ctx = rb.Context(0)
+    n_max = max(sc["n"] for sc in pool)
 
-    # keep masks of the plain FP32 per-scene path, for the mask agreement
-    keep_ref = {}
-    for p, r in sorted(set(jobs)):
-        sc = pool[p]
-        res = ctx.prune_host(sc["pos"], sc["a32"], sc["cams"], r)
-        keep = np.zeros(sc["n"], dtype=bool)
-        keep[res["idx"].numpy()] = True
-        keep_ref[(p, r)] = keep
-
-    def plain_server(job_list, arr):
+    def plain_server(job_list, arr, out):
         """The plain FP32 path as one FIFO server thread fed the same
-        arrivals (None = back to back): returns latencies (ms) and wall (s)."""
+        arrivals (None = back to back): latencies (ms) and wall (s)."""
         lat = []
         t_start = time.perf_counter()
         for k, (p, r) in enumerate(job_list):
@@ -758,50 +772,117 @@ def run_serve_mode(args):
                     time.sleep(delay)
             t_arr = t_start + arr[k] if arr is not None else time.perf_counter()
             sc = pool[p]
-            ctx.prune_host(sc["pos"], sc["a32"], sc["cams"], r, out=plain_out[p])
+            nk = sc["n"] - int(math.floor(r * sc["n"]))
+            o = {"out_pos": out["out_pos"][: 3 * nk].view(3, nk), "out_attr": out["out_attr"][: 56 * nk].view(56, nk),
+                 "idx": out["idx"][:nk]}
+            ctx.prune_host(sc["pos"], sc["a32"], sc["cams"], r, out=o)
             lat.append((time.perf_counter() - t_arr) * 1000.0)
         return lat, time.perf_counter() - t_start
 
-    plain_out = []
-    for sc in pool:
-        nk = sc["n"] - sc["n"] // 2
-        plain_out.append({"out_pos": torch.empty((3, nk), dtype=torch.float32, pin_memory=True),
-                          "out_attr": torch.empty((56, nk), dtype=torch.float32, pin_memory=True),
-                          "idx": torch.empty(nk, dtype=torch.int32, pin_memory=True)})
-    plain_lat, _ = plain_server(jobs, arrivals)
-    _, plain_wall = plain_server(sat_jobs, None)
+    nk_max = n_max - n_max // 2
+    plain_out = {"out_pos": torch.empty(3 * nk_max, dtype=torch.float32, pin_memory=True),
+                 "out_attr": torch.empty(56 * nk_max, dtype=torch.float32, pin_memory=True),
+                 "idx": torch.empty(nk_max, dtype=torch.int32, pin_memory=True)}
+    plain_server(sat_jobs[: min(8, len(sat_jobs))], None, plain_out)  # warm-up
+    plain_lat, plain_wall_p = plain_server(jobs, arrivals, plain_out)
+    _, plain_wall = plain_server(sat_jobs, None, plain_out)
     plain_sat = len(sat_jobs) / plain_wall
+    del plain_out
 
+    outsets = _OutputSets(torch, n_max, args.slots + 4)
     budget = int(args.budget_gb * (1 << 30))
-    outsets = _OutputSets(torch, pool, copies=args.copies)
-    # warm the queue path (pool growth, module loads) on a few jobs
-    _serve_pass(torch, rb, ctx, pool, sat_jobs[: min(8, len(sat_jobs))], None, budget, args.slots, outsets, {}, None)
-    agree = []
-    lat, wall, rounds, st = _serve_pass(torch, rb, ctx, pool, jobs, arrivals, budget, args.slots, outsets,
-                                        keep_ref, agree, agree_first=len(jobs))
-    lat_s, wall_s, rounds_s, st_s = _serve_pass(torch, rb, ctx, pool, sat_jobs, None, budget, args.slots, outsets,
-                                                keep_ref, None)
+    small_budget = int(args.small_budget_gb * (1 << 30))
+
+    # keep masks of the plain FP32 GPU path and of the FP64 oracle (on a
+    # seeded subset of the pool scenes, float32 inputs), for agreement
+    keep_gpu, keep_orc = {}, {}
+    orc_scenes = set(np.random.default_rng(5).choice(P, min(args.oracle_scenes, P), replace=False).tolist())
+    import oracle
+    oracle.set_threads(os.cpu_count() or 1)
+    for p, r in sorted(set(jobs)):
+        sc = pool[p]
+        res = ctx.prune_host(sc["pos"], sc["a32"], sc["cams"], r)
+        keep = np.zeros(sc["n"], dtype=bool)
+        keep[res["idx"].numpy()] = True
+        keep_gpu[(p, r)] = keep
+    t_orc = time.perf_counter()
+    orc_scores = {}
+    for p in sorted(orc_scenes):
+        sc = pool[p]
+        g = np.concatenate([sc["pos"].numpy(), sc["a32"].numpy()], axis=0).astype(np.float64)
+        orc_scores[p] = oracle.score(g, sc["cams"], detail=False)["scores"]
+    for p, r in sorted(set(jobs)):
+        if p in orc_scores:
+            m, _, _ = oracle.select(orc_scores[p], r)
+            keep_orc[(p, r)] = np.unpackbits(m.view(np.uint8), bitorder="little")[: pool[p]["n"]].astype(bool)
+    t_orc = time.perf_counter() - t_orc
+
+    agree_gpu, agree_orc = [], []
+
+    def record(k, p, r, res, outs):
+        nk = res["n_keep"]
+        keep = np.zeros(pool[p]["n"], dtype=bool)
+        keep[outs["idx"][:nk].numpy()] = True
+        agree_gpu.append(float(np.mean(keep == keep_gpu[(p, r)])))
+        if (p, r) in keep_orc:
+            agree_orc.append(float(np.mean(keep == keep_orc[(p, r)])))
+
+    def run(job_list, arr, bud, on_done=None, slots=args.slots):
+        q = rb.Queue(ctx, budget_bytes=bud, max_slots=slots)
+        try:
+            # warm-up on the same queue: its memory pool grows to the working
+            # set of a saturated run before the measured pass
+            _serve_pass(torch, rb, pool, sat_jobs[: min(4 * slots, len(sat_jobs))], None, q, outsets)
+            st0 = q.stats()
+            lat, rounds, wall = _serve_pass(torch, rb, pool, job_list, arr, q, outsets, on_done)
+            st = q.stats()
+        finally:
+            q.close()
+        st = {**st, "rounds": st["rounds"] - st0["rounds"], "dispatch_ms": st["dispatch_ms"] - st0["dispatch_ms"]}
+        return lat, rounds, wall, st
+
+    lat, rounds, wall, st = run(jobs, arrivals, budget, record)
+    lat_s, rounds_s, wall_s, st_s = run(sat_jobs, None, budget)
+    # more slots than the reduced budget can fill: admission is bounded by bytes
+    lat_b, rounds_b, wall_b, st_b = run(sat_jobs, None, small_budget, slots=args.small_budget_slots)
     served_sat = len(sat_jobs) / wall_s
     pairs = sum(pool[p]["n"] * pool[p]["V"] for p, _ in sat_jobs)
+    ns = [sc["n"] for sc in pool]
+
+    def side(lat_, rounds_, wall_, st_, n_jobs):
+        return {"jobs": n_jobs, "wall_s": wall_, "scenes_per_s": n_jobs / wall_,
+                "p50_ms": _percentile(lat_, 0.5), "p99_ms": _percentile(lat_, 0.99),
+                "mean_round": statistics.mean(rounds_), "max_round": max(rounds_),
+                "round_sizes": _round_hist(rounds_), "peak_bytes": st_["peak_bytes"], "rounds": st_["rounds"],
+                "slots": st_["slots"], "dispatch_ms_per_job": st_["dispatch_ms"] / max(n_jobs, 1)}
+
     line = {"mode": "serve", "metric": "scenes/s", "value": served_sat, "unit": "scenes/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32 (bf16 storage)", "data": "synthetic",
-            "poisson": {"jobs": len(jobs), "rate_per_s": args.rate, "wall_s": wall,
-                        "p50_ms": _percentile(lat, 0.5), "p99_ms": _percentile(lat, 0.99),
+            "poisson": {**side(lat, rounds, wall, st, len(jobs)), "rate_per_s": args.rate,
                         "plain_f32_p50_ms": _percentile(plain_lat, 0.5),
-                        "plain_f32_p99_ms": _percentile(plain_lat, 0.99),
-                        "mean_round": statistics.mean(rounds), "max_round": max(rounds)},
-            "saturation": {"jobs": len(sat_jobs), "served_scenes_per_s": served_sat,
+                        "plain_f32_p99_ms": _percentile(plain_lat, 0.99), "plain_f32_wall_s": plain_wall_p},
+            "saturation": {**side(lat_s, rounds_s, wall_s, st_s, len(sat_jobs)),
                            "served_pairs_per_s": pairs / wall_s, "plain_f32_scenes_per_s": plain_sat,
-                           "speedup_vs_plain_f32": served_sat / plain_sat,
-                           "p50_ms": _percentile(lat_s, 0.5), "p99_ms": _percentile(lat_s, 0.99),
-                           "mean_round": statistics.mean(rounds_s), "max_round": max(rounds_s)},
-            "mask_agreement_vs_plain_f32": {"min": min(agree), "mean": statistics.mean(agree),
-                                            "jobs": len(agree), "below_99.9": sum(a < 0.999 for a in agree)},
-            "queue": {"budget_bytes": budget, "slots": args.slots, "peak_bytes": max(st["peak_bytes"],
-                                                                                      st_s["peak_bytes"])},
-            "config": {"workload": f"serving: {args.jobs} Poisson jobs at {args.rate}/s + {args.sat_jobs} "
-                                   f"back-to-back; scenes from a pool of {P} (seeds 1000-{999 + P}), ratio per "
-                                   f"job seed, BF16 storage, budget {args.budget_gb} GB",
+                           "speedup_vs_plain_f32": served_sat / plain_sat},
+            "saturation_small_budget": {**side(lat_b, rounds_b, wall_b, st_b, len(sat_jobs)),
+                                        "budget_bytes": small_budget,
+                                        "speedup_vs_plain_f32": len(sat_jobs) / wall_b / plain_sat},
+            "mask_agreement_vs_plain_f32_gpu": {"min": min(agree_gpu), "mean": statistics.mean(agree_gpu),
+                                                "jobs": len(agree_gpu),
+                                                "below_99.9": sum(a < 0.999 for a in agree_gpu)},
+            "mask_agreement_vs_fp64_oracle": {"min": min(agree_orc) if agree_orc else None,
+                                              "mean": statistics.mean(agree_orc) if agree_orc else None,
+                                              "jobs": len(agree_orc), "scenes": sorted(orc_scenes),
+                                              "below_99.9": sum(a < 0.999 for a in agree_orc),
+                                              "oracle_s": t_orc},
+            "queue": {"budget_bytes": budget, "slots": args.slots},
+            "pool": {"scenes": P, "seeds": f"1000-{999 + P}", "n_min": min(ns), "n_max": max(ns),
+                     "n_mean": statistics.mean(ns), "generate_s": t_gen},
+            "config": {"workload": f"serving: {args.jobs} jobs, Poisson arrivals at {args.rate}/s (seed 999), then "
+                                   f"{args.sat_jobs} back to back; job k scores pool scene k mod {P} (seeds "
+                                   f"1000-{999 + P}, N log-uniform 50k-3.5M, V 50-300) with the ratio its seed "
+                                   f"draws; BF16 storage; HBM budget {args.budget_gb} GB (and "
+                                   f"{args.small_budget_gb} GB)",
                        "plain_path": "refine_prune_host, FP32, one FIFO server thread fed the same arrivals "
                                      "from page-locked host memory"}}
     print(json.dumps(line), flush=True)
@@ -827,13 +908,17 @@ def main(argv=None):
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--max-views", type=int, default=0,
                     help="score every ceil(V/max_views)-th view (Table B.1 subsampling); 0 = all")
-    ap.add_argument("--jobs", type=int, default=300, help="serve: Poisson jobs")
-    ap.add_argument("--sat-jobs", type=int, default=200, help="serve: back-to-back jobs")
+    ap.add_argument("--jobs", type=int, default=2000, help="serve: Poisson jobs")
+    ap.add_argument("--sat-jobs", type=int, default=2000, help="serve: back-to-back jobs")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
-    ap.add_argument("--pool", type=int, default=16, help="serve: distinct scenes")
-    ap.add_argument("--copies", type=int, default=2, help="serve: output buffer sets per scene")
-    ap.add_argument("--slots", type=int, default=8, help="serve: requests in flight")
+    ap.add_argument("--pool", type=int, default=128, help="serve: distinct scenes")
+    ap.add_argument("--slots", type=int, default=32, help="serve: requests in flight")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
+    ap.add_argument("--small-budget-gb", type=float, default=4.0, help="serve: reduced HBM budget")
+    ap.add_argument("--small-budget-slots", type=int, default=32,
+                    help="serve: slots of the reduced-budget run (more than its budget can fill)")
+    ap.add_argument("--oracle-scenes", type=int, default=16,
+                    help="serve: pool scenes whose keep masks are also checked against the FP64 oracle")
     ap.add_argument("--accuracy", action="store_true",
                     help="also report error and mask agreement against the FP64 oracle")
     args = ap.parse_args(argv)

@@ -341,20 +341,24 @@ refine_status refine_ctx_set_shape(refine_ctx *ctx, const refine_shape *shape);
 
 /* ------------------------------------------------------ request queue
  * A serving loop for pruning requests (Sec. 3.3 applied to a stream of
- * scenes).  Two native threads own the GPU work:
+ * scenes).  Three native threads own the GPU work:
  *   - the dispatcher admits pending requests in arrival order while the
  *     device bytes of the admitted ones fit the queue's HBM budget and a
  *     slot is free; each admitted request gets a slot (its own CUDA stream)
  *     and one device block from the queue's memory pool, into which its
- *     scene and cameras are copied.  All requests admitted together form a
- *     round: their preparation runs on their slot streams, ONE persistent
- *     launch scores all of them (the batched kernel; a request with more
- *     views than the camera block has its further blocks scored right after
- *     it, in order, on the same stream), then selection,
- *     compaction and the copies back run on the slot streams again.  A
- *     round is issued as soon as it is formed, while earlier rounds are
- *     still on the GPU, so requests that arrive meanwhile overlap with them
- *     (continuous batching);
+ *     scene and cameras are copied at once (the copies of all requests go
+ *     through one input-copy stream, in admission order, so that each ends
+ *     as early as the link allows), and its preparation follows on its
+ *     slot stream;
+ *   - the scorer batches continuously: as soon as the previous batched
+ *     launch has ended, ONE persistent launch scores every request whose
+ *     preparation has ended (those requests form a round; a request with
+ *     more views than the camera block has its further blocks scored right
+ *     after it, in order, on the same stream); selection and compaction
+ *     then run on the requests' slot streams and the copies back on one
+ *     output-copy stream.  Requests that arrive while others are on the GPU
+ *     thus join the next launch, and their copies overlap the others'
+ *     kernels;
  *   - the completion thread retires requests whose GPU work has finished:
  *     it finishes copies into pageable host buffers, records the result,
  *     frees the device block and returns its bytes to the budget.
@@ -394,6 +398,12 @@ typedef struct refine_result {
     float threshold;       /* as refine_select                                                      */
     float reserved;
     double submit_ms, admit_ms, done_ms;
+    /* The request's device timeline, in ms of device time since the queue
+     * was created (a different clock from the three above; -1 where the
+     * request did not get that far): its copy in ended, its preparation
+     * ended, the batched score launch that scored it ended, its selection
+     * and compaction ended, its copy out ended. */
+    double copied_ms, prepped_ms, scored_ms, computed_ms, read_ms;
 } refine_result;
 
 typedef struct refine_queue_stats {
@@ -402,6 +412,8 @@ typedef struct refine_queue_stats {
     uint64_t bytes_in_use, peak_bytes, budget_bytes;
     int32_t max_round, slots;
     int64_t kernel_launches;
+    double dispatch_ms;  /* host time the dispatcher spent issuing rounds (API calls)  */
+    double retire_ms;    /* host time the completion thread spent retiring requests   */
 } refine_queue_stats;
 
 /* Device bytes one request holds while admitted (scene, cameras, scratch,
@@ -429,6 +441,15 @@ refine_status refine_queue_submit(refine_queue *q, const refine_request *req, ui
  * Returns OK (see out->status for the request's own outcome), ETIMEOUT if it
  * is not done yet, ENOTFOUND for an unknown or already retired ticket. */
 refine_status refine_queue_poll(refine_queue *q, uint64_t ticket, refine_result *out, int32_t timeout_ms);
+
+/* Like refine_queue_poll for whichever request finishes first: waits up to
+ * timeout_ms for any submitted request to be done, then fills *ticket_out
+ * and *out and retires that ticket (among several done, the lowest ticket).
+ * Lets a server take results in completion order, so that a long request
+ * does not hold up the output buffers of the short ones that finish after
+ * it.  ETIMEOUT if none is done in time, ENOTFOUND if no request is
+ * outstanding. */
+refine_status refine_queue_poll_any(refine_queue *q, uint64_t *ticket_out, refine_result *out, int32_t timeout_ms);
 
 refine_status refine_queue_stats_get(refine_queue *q, refine_queue_stats *out);
 

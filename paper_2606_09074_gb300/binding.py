@@ -110,20 +110,23 @@ class refine_request(C.Structure):
 class refine_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("round_size", C.c_int32), ("n_keep", C.c_int64),
                 ("threshold", C.c_float), ("reserved", C.c_float), ("submit_ms", C.c_double),
-                ("admit_ms", C.c_double), ("done_ms", C.c_double)]
+                ("admit_ms", C.c_double), ("done_ms", C.c_double), ("copied_ms", C.c_double),
+                ("prepped_ms", C.c_double), ("scored_ms", C.c_double), ("computed_ms", C.c_double),
+                ("read_ms", C.c_double)]
 
 
 class refine_queue_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
                 ("rounds", C.c_int64), ("pending", C.c_int64), ("in_flight", C.c_int64),
                 ("bytes_in_use", C.c_uint64), ("peak_bytes", C.c_uint64), ("budget_bytes", C.c_uint64),
-                ("max_round", C.c_int32), ("slots", C.c_int32), ("kernel_launches", C.c_int64)]
+                ("max_round", C.c_int32), ("slots", C.c_int32), ("kernel_launches", C.c_int64),
+                ("dispatch_ms", C.c_double), ("retire_ms", C.c_double)]
 
 
 assert C.sizeof(refine_camera) == 80 and C.sizeof(refine_scene) == 40 and C.sizeof(refine_job) == 112
 assert C.sizeof(refine_params) == 48
 assert C.sizeof(refine_shape) == 24
-assert C.sizeof(refine_request) == 96 and C.sizeof(refine_result) == 48 and C.sizeof(refine_queue_stats) == 88
+assert C.sizeof(refine_request) == 96 and C.sizeof(refine_result) == 88 and C.sizeof(refine_queue_stats) == 104
 
 _P = C.c_void_p
 _SIGNATURES = {
@@ -161,6 +164,7 @@ _SIGNATURES = {
                                       C.POINTER(C.c_void_p)]),
     "refine_queue_submit": (C.c_int, [_P, C.POINTER(refine_request), C.POINTER(C.c_uint64)]),
     "refine_queue_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(refine_result), C.c_int32]),
+    "refine_queue_poll_any": (C.c_int, [_P, C.POINTER(C.c_uint64), C.POINTER(refine_result), C.c_int32]),
     "refine_queue_stats_get": (C.c_int, [_P, C.POINTER(refine_queue_stats)]),
     "refine_queue_destroy": (None, [_P]),
     "refine_queue_last_error": (C.c_char_p, [_P]),
@@ -605,6 +609,20 @@ class Queue:
         _, _, _, out = self._live.pop(int(ticket))
         d = {k: getattr(res, k) for k, _ in refine_result._fields_ if k != "reserved"}
         return d, out
+
+    def poll_any(self, timeout_ms: int = -1):
+        """The first request to finish: (ticket, result dict, outputs dict),
+        or None if none is done in time (refine_queue_poll_any)."""
+        res = refine_result()
+        t = C.c_uint64()
+        rc = refine_queue_poll_any(self.handle, C.byref(t), C.byref(res), int(timeout_ms))  # noqa: F821
+        if rc == REFINE_ETIMEOUT:
+            return None
+        if rc != REFINE_OK:
+            raise RefineError(rc, f"refine_queue_poll_any: {STATUS_NAMES.get(rc, rc)}")
+        _, _, _, out = self._live.pop(int(t.value))
+        d = {k: getattr(res, k) for k, _ in refine_result._fields_ if k != "reserved"}
+        return int(t.value), d, out
 
     def last_error(self) -> str:
         return refine_queue_last_error(self.handle).decode(errors="replace")  # noqa: F821

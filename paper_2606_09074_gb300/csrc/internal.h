@@ -29,10 +29,29 @@ struct ScoreShape {
     int views_per_pass = kViewsPerPass;  // camera block: views per score pass (32..512, a multiple of 32)
 };
 bool shape_valid(const ScoreShape &sh);
-// An item of the batched kernel: kBatchRounds warp tiles per warp of the
-// CTA, of one scene; the CTA's warps share them out dynamically.
+// An item of the batched kernel: `rounds` warp tiles per warp of the CTA
+// (1, 2 or 4), of one scene; the CTA's warps share them out dynamically.
+// Large items cost fewer CTA barriers and counter atomics; a launch with
+// little work takes smaller ones, so that every CTA gets several items and
+// the launch does not end on a few long ones (batch_rounds).  Warp tiles
+// stay 32 * gpt aligned within a scene either way.
 constexpr int kBatchRounds = 4;
-inline int64_t batch_tile(const ScoreShape &sh) { return (int64_t)sh.threads * sh.gpt * kBatchRounds; }
+inline int64_t batch_tile(const ScoreShape &sh, int rounds = kBatchRounds)
+{
+    return (int64_t)sh.threads * sh.gpt * rounds;
+}
+// The largest item (4, 2 or 1 rounds) that leaves at least 4 items per CTA
+// of a grid of `grid` CTAs over scenes of n[0..k) primitives.
+inline int batch_rounds(const ScoreShape &sh, const int64_t *n, int k, int grid)
+{
+    for (int r = kBatchRounds; r > 1; r /= 2) {
+        const int64_t t = batch_tile(sh, r);
+        int64_t items = 0;
+        for (int i = 0; i < k; ++i) items += (n[i] + t - 1) / t;
+        if (items >= 4 * (int64_t)grid) return r;
+    }
+    return 1;
+}
 constexpr int kFeatThreads = 256;
 
 // Spatial cells for the processing order of k_score: a 2^b x 2^b x 2^b grid
@@ -145,6 +164,7 @@ struct BatchLaunch {
     long long total_tiles;
     unsigned long long *counter;     // device, zero before the launch
     int *status;
+    int rounds;                      // warp tiles per warp in an item (batch_tile)
 };
 int score_batch_grid(int num_sms, int max_vcount, const ScoreShape &sh);
 cudaError_t launch_score_batch(const BatchLaunch &b, int max_vcount, int grid, const ScoreShape &sh, cudaStream_t s);

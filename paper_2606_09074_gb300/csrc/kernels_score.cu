@@ -1013,7 +1013,7 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLau
     int cur = -1;
     uint32_t phase = 0;
     const int lane = threadIdx.x & 31;
-    const int64_t tile = (int64_t)THREADS * GPT * kBatchRounds;  // primitives per item
+    const int64_t tile = (int64_t)THREADS * GPT * b.rounds;  // primitives per item
     for (;;) {
         if (threadIdx.x == 0) {
             s_wt = 0;

@@ -3,13 +3,22 @@
 // one batched launch, while earlier rounds are still on the GPU.
 //
 // Threads and streams:
-//   dispatcher   admits (FIFO, budget, slots) and issues a round: per request
-//                on its slot stream a pool allocation, the host->device copies
-//                and the preparation; on the score stream the round's work
-//                list and ONE k_score_batch launch; per request on its slot
-//                stream again the selection, the compaction, the copies back
-//                (asynchronous when the host buffers are page-locked) and a
-//                completion event.
+//   dispatcher   admits (FIFO, budget, slots) and issues each admitted
+//                request at once: a pool allocation and the host->device
+//                copies on the queue's one input-copy stream, then the
+//                preparation on the request's slot stream.
+//   scorer       continuous batching: as soon as the previous batched launch
+//                has ended, takes every request whose preparation has ended
+//                and scores them with ONE k_score_batch launch on the score
+//                stream (its round); per request on its slot stream again the
+//                selection and the compaction, the copies back on the queue's
+//                one output-copy stream (asynchronous when the host buffers
+//                are page-locked) and a completion event.
+// The copies of all requests go through one stream per direction, in
+// admission order: each request's copy then ends as early as the link
+// allows and its kernels overlap the next request's copy.  (Copies issued
+// on the slot streams shared the link and ended together, so the kernels
+// of a whole group of requests waited for all of their copies.)
 //   completion   polls the completion events of the requests in flight,
 //                finishes copies into pageable buffers, reads the request's
 //                status and threshold, frees its block and its slot.
@@ -74,6 +83,7 @@ struct QJob {
     long long *total = nullptr;
     refine_status host_status = REFINE_OK;
     bool issued = false;  // GPU work enqueued (its completion event is recorded)
+    bool copied = false, prepped = false, finishing = false;  // timeline events recorded for this request
 };
 
 struct RoundRes {  // one entry of the round ring
@@ -108,6 +118,7 @@ size_t elem_size(int dtype) { return dtype == REFINE_BF16 ? 2 : 4; }
 
 struct refine_queue {
     refine_ctx pc;  // private context of the dispatcher (error text, device, SM count)
+    refine_ctx sc;  // private context of the scorer (error text)
     refine_params params{};
     ScoreShape shape;  // the creating context's tuned shape
     uint64_t budget = 0;
@@ -115,8 +126,12 @@ struct refine_queue {
     std::chrono::steady_clock::time_point t0;
     cudaMemPool_t pool = nullptr;
     cudaStream_t score_stream = nullptr;
+    cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;  // all copies, FIFO per direction
     std::vector<cudaStream_t> slot_stream;
     std::vector<cudaEvent_t> prepped, done;
+    std::vector<cudaEvent_t> copied, computed, read_back;  // per slot: copy in done, kernels done, copy out done
+    std::vector<cudaEvent_t> scored_at;                     // per slot: the round's batched score done
+    cudaEvent_t ev_ref = nullptr;                           // device-time origin of the per-request timeline
     SlotHost *slot_host = nullptr;  // page-locked [slots]
     std::vector<RoundRes> ring;
     void *ring_dev = nullptr;
@@ -124,21 +139,23 @@ struct refine_queue {
     int64_t round_seq = 0;
 
     std::mutex mu;
-    std::condition_variable cv_dispatch, cv_complete, cv_poll;
+    std::condition_variable cv_dispatch, cv_score, cv_complete, cv_poll;
     std::deque<QJob *> pending;
+    std::deque<QJob *> prepping;  // admitted and issued, waiting for a batched score launch
     std::list<QJob *> inflight;
     std::unordered_map<uint64_t, refine_result> results;
     std::unordered_set<uint64_t> live;  // submitted, not yet returned by refine_queue_poll
     std::vector<int> free_slots;
     uint64_t used = 0, peak = 0;
     uint64_t next_ticket = 1;
-    bool stop = false, dispatcher_done = false;
+    bool stop = false, dispatcher_done = false, scorer_done = false;
     int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_rounds = 0;
     int max_round = 0;
+    double dispatch_ms = 0.0, retire_ms = 0.0;  // host time issuing rounds / retiring requests
     std::atomic<int64_t> launches{0};
     char err_copy[1024] = {0};
     char cerr[256] = {0};  // last failure seen by the completion thread
-    std::thread dispatcher, completer;
+    std::thread dispatcher, scorer, completer;
 };
 
 namespace {
@@ -187,10 +204,10 @@ void carve_job(QJob *j)
 }
 
 template <typename F>
-refine_status counted_run(refine_queue *q, int cls, F &&f)
+refine_status counted_run(refine_queue *q, refine_ctx *c, int cls, F &&f)
 {
     const cudaError_t e = f();
-    if (e != cudaSuccess) return cuda_fail(&q->pc, e, kClassName[cls]);
+    if (e != cudaSuccess) return cuda_fail(c, e, kClassName[cls]);
     q->launches.fetch_add(1, std::memory_order_relaxed);
     return REFINE_OK;
 }
@@ -198,9 +215,9 @@ refine_status counted_run(refine_queue *q, int cls, F &&f)
 // Issues the preparation of one admitted request on its slot stream.
 refine_status issue_prep(refine_queue *q, QJob *j)
 {
-    cudaStream_t s = q->slot_stream[j->slot];
+    cudaStream_t s = q->slot_stream[j->slot], cs = q->h2d_stream;
     refine_ctx *c = &q->pc;
-    cudaError_t e = cudaMallocFromPoolAsync(&j->block, j->footprint, q->pool, s);
+    cudaError_t e = cudaMallocFromPoolAsync(&j->block, j->footprint, q->pool, cs);
     if (e != cudaSuccess) {
         j->block = nullptr;
         return cuda_fail(c, e, "queue: device block");
@@ -208,21 +225,24 @@ refine_status issue_prep(refine_queue *q, QJob *j)
     carve_job(j);
     const int64_t n = j->req.n, S = dev_stride(n);
     const size_t es = elem_size(j->req.dtype);
-    e = cudaMemsetAsync(j->status, 0, sizeof(int), s);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(const_cast<float *>(j->scene.pos), (size_t)S * 4, j->req.pos_host, (size_t)n * 4,
-                              (size_t)n * 4, 3, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpy2DAsync(const_cast<float *>(j->scene.pos), (size_t)S * 4, j->req.pos_host, (size_t)n * 4,
+                          (size_t)n * 4, 3, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(const_cast<void *>(j->scene.attr), (size_t)S * es, j->req.attr_host, (size_t)n * es,
-                              (size_t)n * es, 56, cudaMemcpyHostToDevice, s);
+                              (size_t)n * es, 56, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(j->cams, j->req.cams_host, sizeof(refine_camera) * j->req.n_views,
-                            cudaMemcpyHostToDevice, s);
+                            cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(q->copied[j->slot], cs);
+    j->copied = e == cudaSuccess;
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, q->copied[j->slot], 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(j->status, 0, sizeof(int), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "queue: input copy");
-    auto run = [q](int cls, auto &&f) { return counted_run(q, cls, f); };
+    auto run = [q, c](int cls, auto &&f) { return counted_run(q, c, cls, f); };
     refine_status st = enqueue_prep(c, run, &j->scene, j->cams, j->plan, j->sx, j->params, false, j->status, s);
     if (st) return st;
     e = cudaEventRecord(q->prepped[j->slot], s);
+    j->prepped = e == cudaSuccess;
     return e == cudaSuccess ? REFINE_OK : cuda_fail(c, e, "queue: event");
 }
 
@@ -230,59 +250,79 @@ refine_status issue_prep(refine_queue *q, QJob *j)
 refine_status issue_finish(refine_queue *q, QJob *j, const RoundRes &R)
 {
     cudaStream_t s = q->slot_stream[j->slot];
-    refine_ctx *c = &q->pc;
+    refine_ctx *c = &q->sc;
     cudaError_t e = cudaStreamWaitEvent(s, R.scored, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(q->scored_at[j->slot], s);
     if (e != cudaSuccess) return cuda_fail(c, e, "queue: wait");
-    auto run = [q](int cls, auto &&f) { return counted_run(q, cls, f); };
+    auto run = [q, c](int cls, auto &&f) { return counted_run(q, c, cls, f); };
     const int64_t n = j->req.n, nk = j->n_keep;
     refine_status st = enqueue_select(c, run, j->scores, n, nk, j->mask, j->sel_scr, &j->kstar, j->status, s);
     if (!st && j->compact)
         st = enqueue_compact(c, run, &j->scene, j->mask, j->out_pos, j->out_attr, nk, j->idx, j->cmp_scr, &j->total,
                              j->status, s);
     if (st) return st;
+    // the copies back go through the output-copy stream, after the kernels
+    e = cudaEventRecord(q->computed[j->slot], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q->d2h_stream, q->computed[j->slot], 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "queue: event");
+    const cudaStream_t cs = q->d2h_stream;
     SlotHost *h = &q->slot_host[j->slot];
     h->kstar = 0u;
-    if (j->kstar) e = cudaMemcpyAsync(&h->kstar, j->kstar, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h->status, j->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (j->kstar) e = cudaMemcpyAsync(&h->kstar, j->kstar, sizeof(unsigned), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h->status, j->status, sizeof(int), cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess && j->pinned_out) {
         const size_t es = elem_size(j->req.dtype);
         if (j->req.keep_mask_host)
-            e = cudaMemcpyAsync(j->req.keep_mask_host, j->mask, 4 * (size_t)((n + 31) / 32), cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(j->req.keep_mask_host, j->mask, 4 * (size_t)((n + 31) / 32), cudaMemcpyDeviceToHost,
+                                cs);
         if (e == cudaSuccess && j->req.scores_host)
-            e = cudaMemcpyAsync(j->req.scores_host, j->scores, 4 * (size_t)n, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(j->req.scores_host, j->scores, 4 * (size_t)n, cudaMemcpyDeviceToHost, cs);
         if (e == cudaSuccess && j->compact) {
-            e = cudaMemcpyAsync(j->req.out_pos_host, j->out_pos, 12 * (size_t)nk, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(j->req.out_pos_host, j->out_pos, 12 * (size_t)nk, cudaMemcpyDeviceToHost, cs);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(j->req.out_attr_host, j->out_attr, 56 * es * (size_t)nk, cudaMemcpyDeviceToHost, s);
+                e = cudaMemcpyAsync(j->req.out_attr_host, j->out_attr, 56 * es * (size_t)nk, cudaMemcpyDeviceToHost,
+                                    cs);
             if (e == cudaSuccess && j->req.kept_idx_host)
-                e = cudaMemcpyAsync(j->req.kept_idx_host, j->idx, 4 * (size_t)nk, cudaMemcpyDeviceToHost, s);
+                e = cudaMemcpyAsync(j->req.kept_idx_host, j->idx, 4 * (size_t)nk, cudaMemcpyDeviceToHost, cs);
         }
     }
+    // the slot stream (its completion event, its block's release) follows the copies back
+    if (e == cudaSuccess) e = cudaEventRecord(q->read_back[j->slot], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, q->read_back[j->slot], 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "queue: read-back");
+    j->finishing = true;
     return REFINE_OK;
 }
 
-void issue_round(refine_queue *q, std::vector<QJob *> &round)
+// Scores `round` (requests whose preparation has ended, or whose issue
+// failed) with one batched launch and issues their selection, compaction
+// and copies back.  Returns the launch's completion event (NULL if nothing
+// was launched).  Runs on the scorer thread.
+cudaEvent_t issue_scoring(refine_queue *q, std::vector<QJob *> &round)
 {
-    RoundRes &R = q->ring[(size_t)(q->round_seq++ % q->slots)];
+    const double t_issue = now_ms(q->t0);
+    RoundRes &R = q->ring[(size_t)(q->round_seq++ % q->ring.size())];
     std::vector<QJob *> live;
     for (QJob *j : round) {
         j->round_size = (int)round.size();
-        j->host_status = issue_prep(q, j);
         if (!j->host_status) live.push_back(j);
     }
-    const long long tile = batch_tile(q->shape);
     refine_status st = REFINE_OK;
     if (!live.empty()) {
         int max_v = 0;
-        R.h_tb[0] = 0;
+        std::vector<int64_t> ns;
         for (size_t i = 0; i < live.size(); ++i) {
             QJob *j = live[i];
             R.h_launch[i] = make_score_launch(&j->scene, j->plan, j->sx, j->params, 0, j->scores, nullptr, false,
                                               j->status);
-            R.h_tb[i + 1] = R.h_tb[i] + (j->req.n + tile - 1) / tile;
             max_v = std::max(max_v, R.h_launch[i].vcount);
+            ns.push_back(j->req.n);
         }
+        const int full_grid = score_batch_grid(q->pc.num_sms, max_v, q->shape);
+        const int rounds = batch_rounds(q->shape, ns.data(), (int)ns.size(), full_grid);
+        const long long tile = batch_tile(q->shape, rounds);
+        R.h_tb[0] = 0;
+        for (size_t i = 0; i < live.size(); ++i) R.h_tb[i + 1] = R.h_tb[i] + (ns[i] + tile - 1) / tile;
         const int k = (int)live.size();
         cudaStream_t m = q->score_stream;
         cudaError_t e = cudaMemcpyAsync(R.d_launch, R.h_launch, sizeof(ScoreLaunch) * k, cudaMemcpyHostToDevice, m);
@@ -300,7 +340,8 @@ void issue_round(refine_queue *q, std::vector<QJob *> &round)
             bl.total_tiles = R.h_tb[k];
             bl.counter = R.d_counter;
             bl.status = R.d_status;
-            int grid = score_batch_grid(q->pc.num_sms, max_v, q->shape);
+            bl.rounds = rounds;
+            int grid = full_grid;
             if (grid > bl.total_tiles) grid = (int)bl.total_tiles;
             e = launch_score_batch(bl, max_v, grid, q->shape, m);
             if (e == cudaSuccess) q->launches.fetch_add(1, std::memory_order_relaxed);
@@ -320,7 +361,7 @@ void issue_round(refine_queue *q, std::vector<QJob *> &round)
             }
         }
         if (e == cudaSuccess) e = cudaEventRecord(R.scored, m);
-        if (e != cudaSuccess) st = cuda_fail(&q->pc, e, "queue: batched score");
+        if (e != cudaSuccess) st = cuda_fail(&q->sc, e, "queue: batched score");
     }
     for (QJob *j : round) {
         if (!j->host_status) j->host_status = st ? st : issue_finish(q, j, R);
@@ -333,8 +374,10 @@ void issue_round(refine_queue *q, std::vector<QJob *> &round)
         for (QJob *j : round) q->inflight.push_back(j);
         q->n_rounds++;
         q->max_round = std::max(q->max_round, (int)round.size());
+        q->dispatch_ms += now_ms(q->t0) - t_issue;
     }
     q->cv_complete.notify_one();
+    return (!live.empty() && !st) ? R.scored : nullptr;
 }
 
 bool admissible(const refine_queue *q, const QJob *j)
@@ -346,7 +389,7 @@ void dispatcher_main(refine_queue *q)
 {
     cudaSetDevice(q->pc.device);
     for (;;) {
-        std::vector<QJob *> round;
+        std::vector<QJob *> admitted;
         {
             std::unique_lock<std::mutex> lk(q->mu);
             q->cv_dispatch.wait(lk, [q] { return q->stop || (!q->pending.empty() && admissible(q, q->pending.front())); });
@@ -360,14 +403,64 @@ void dispatcher_main(refine_queue *q)
                 j->t_admit = t;
                 q->used += j->footprint;
                 q->n_admitted++;
-                round.push_back(j);
+                admitted.push_back(j);
             }
             q->peak = std::max(q->peak, q->used);
         }
-        issue_round(q, round);
+        // copies and preparation of each request, at once, in admission order
+        for (QJob *j : admitted) {
+            const double t_issue = now_ms(q->t0);
+            j->host_status = issue_prep(q, j);
+            std::lock_guard<std::mutex> lk(q->mu);
+            q->prepping.push_back(j);
+            q->dispatch_ms += now_ms(q->t0) - t_issue;
+            q->cv_score.notify_one();
+        }
     }
     std::lock_guard<std::mutex> lk(q->mu);
     q->dispatcher_done = true;
+    q->cv_score.notify_one();
+}
+
+// Continuous batching: each batched launch scores every request whose
+// preparation has ended by the time the previous launch has ended.
+void scorer_main(refine_queue *q)
+{
+    cudaSetDevice(q->pc.device);
+    cudaEvent_t last = nullptr;  // the previous batched launch's completion
+    for (;;) {
+        QJob *head = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(q->mu);
+            q->cv_score.wait(lk, [q] { return !q->prepping.empty() || q->dispatcher_done; });
+            if (q->prepping.empty()) break;  // the dispatcher has stopped and nothing is left
+            head = q->prepping.front();
+        }
+        // outside the lock: the oldest waiting request's preparation, then the
+        // previous launch (the requests prepared meanwhile join this one)
+        if (head->prepped && !head->host_status) cudaEventSynchronize(q->prepped[head->slot]);
+        if (last) cudaEventSynchronize(last);
+        cudaGetLastError();
+        std::vector<QJob *> ready;
+        {
+            std::lock_guard<std::mutex> lk(q->mu);
+            for (auto it = q->prepping.begin(); it != q->prepping.end();) {
+                QJob *j = *it;
+                const bool done = j->host_status || !j->prepped ||
+                                  cudaEventQuery(q->prepped[j->slot]) != cudaErrorNotReady;
+                if (done) {
+                    ready.push_back(j);
+                    it = q->prepping.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            cudaGetLastError();
+        }
+        if (!ready.empty()) last = issue_scoring(q, ready);
+    }
+    std::lock_guard<std::mutex> lk(q->mu);
+    q->scorer_done = true;
     q->cv_complete.notify_one();
 }
 
@@ -402,6 +495,7 @@ refine_status finish_pageable(refine_queue *q, QJob *j)
 
 void retire(refine_queue *q, QJob *j)
 {
+    const double t_retire = now_ms(q->t0);
     refine_status st = j->host_status;
     const SlotHost &h = q->slot_host[j->slot];
     if (!st && j->issued) {
@@ -415,6 +509,17 @@ void retire(refine_queue *q, QJob *j)
     r.threshold = (!st && j->kstar) ? key_to_score(h.kstar) : -INFINITY;
     r.submit_ms = j->t_submit;
     r.admit_ms = j->t_admit;
+    // device timeline: the slot's events still belong to this request
+    double *tl[5] = {&r.copied_ms, &r.prepped_ms, &r.scored_ms, &r.computed_ms, &r.read_ms};
+    cudaEvent_t ev[5] = {q->copied[j->slot], q->prepped[j->slot], q->scored_at[j->slot], q->computed[j->slot],
+                         q->read_back[j->slot]};
+    const bool reached[5] = {j->copied, j->prepped, j->finishing, j->finishing, j->finishing};
+    for (int k = 0; k < 5; ++k) {
+        float ms = -1.f;
+        if (!(j->issued && reached[k] && !st && cudaEventElapsedTime(&ms, q->ev_ref, ev[k]) == cudaSuccess)) ms = -1.f;
+        cudaGetLastError();
+        *tl[k] = ms;
+    }
     if (j->block) {
         cudaFreeAsync(j->block, q->slot_stream[j->slot]);
         cudaGetLastError();
@@ -426,6 +531,7 @@ void retire(refine_queue *q, QJob *j)
         q->free_slots.push_back(j->slot);
         q->n_completed++;
         q->results[j->ticket] = r;
+        q->retire_ms += now_ms(q->t0) - t_retire;
     }
     delete j;
     q->cv_dispatch.notify_one();
@@ -439,8 +545,8 @@ void completer_main(refine_queue *q)
         std::vector<QJob *> ready;
         {
             std::unique_lock<std::mutex> lk(q->mu);
-            q->cv_complete.wait(lk, [q] { return !q->inflight.empty() || q->dispatcher_done; });
-            if (q->inflight.empty() && q->dispatcher_done) break;
+            q->cv_complete.wait(lk, [q] { return !q->inflight.empty() || q->scorer_done; });
+            if (q->inflight.empty() && q->scorer_done) break;
             for (auto it = q->inflight.begin(); it != q->inflight.end();) {
                 QJob *j = *it;
                 bool fin = !j->issued;
@@ -472,8 +578,12 @@ void queue_free(refine_queue *q)
     for (cudaStream_t s : q->slot_stream)
         if (s) cudaStreamDestroy(s);
     if (q->score_stream) cudaStreamDestroy(q->score_stream);
-    for (cudaEvent_t e : q->prepped)
-        if (e) cudaEventDestroy(e);
+    if (q->h2d_stream) cudaStreamDestroy(q->h2d_stream);
+    if (q->d2h_stream) cudaStreamDestroy(q->d2h_stream);
+    for (auto *v : {&q->prepped, &q->copied, &q->computed, &q->read_back, &q->scored_at})
+        for (cudaEvent_t e : *v)
+            if (e) cudaEventDestroy(e);
+    if (q->ev_ref) cudaEventDestroy(q->ev_ref);
     for (cudaEvent_t e : q->done)
         if (e) cudaEventDestroy(e);
     for (RoundRes &r : q->ring)
@@ -516,6 +626,8 @@ refine_status refine_queue_create(refine_ctx *c, uint64_t hbm_budget_bytes, int3
     refine_queue *q = new refine_queue();
     q->pc.device = c->device;
     q->pc.num_sms = c->num_sms;
+    q->sc.device = c->device;
+    q->sc.num_sms = c->num_sms;
     q->shape = c->shape;
     q->params = p;
     q->budget = hbm_budget_bytes;
@@ -531,14 +643,21 @@ refine_status refine_queue_create(refine_ctx *c, uint64_t hbm_budget_bytes, int3
         e = cudaMemPoolSetAttribute(q->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->score_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->h2d_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->d2h_stream, cudaStreamNonBlocking);
     q->slot_stream.assign(max_slots, nullptr);
-    q->prepped.assign(max_slots, nullptr);
-    q->done.assign(max_slots, nullptr);
+    for (auto *v : {&q->prepped, &q->done, &q->copied, &q->computed, &q->read_back, &q->scored_at})
+        v->assign(max_slots, nullptr);
     for (int s = 0; s < max_slots && e == cudaSuccess; ++s) {
         e = cudaStreamCreateWithFlags(&q->slot_stream[s], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->prepped[s], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->done[s], cudaEventDisableTiming);
+        // the timeline events keep timestamps (refine_result's device times)
+        for (auto *v : {&q->prepped, &q->copied, &q->computed, &q->read_back, &q->scored_at})
+            if (e == cudaSuccess) e = cudaEventCreate(&(*v)[s]);
     }
+    if (e == cudaSuccess) e = cudaEventCreate(&q->ev_ref);
+    if (e == cudaSuccess) e = cudaEventRecord(q->ev_ref, q->h2d_stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(q->ev_ref);
     if (e == cudaSuccess) e = cudaMallocHost(&q->slot_host, sizeof(SlotHost) * max_slots);
     const size_t per_dev = carve_size({sizeof(ScoreLaunch) * (size_t)max_slots, sizeof(long long) * (max_slots + 1),
                                        sizeof(unsigned long long), sizeof(int)});
@@ -566,16 +685,28 @@ refine_status refine_queue_create(refine_ctx *c, uint64_t hbm_budget_bytes, int3
     for (int s = max_slots - 1; s >= 0; --s) q->free_slots.push_back(s);
     try {
         q->dispatcher = std::thread(dispatcher_main, q);
+        q->scorer = std::thread(scorer_main, q);
         q->completer = std::thread(completer_main, q);
     } catch (...) {
-        if (q->dispatcher.joinable()) {
-            {
-                std::lock_guard<std::mutex> lk(q->mu);
-                q->stop = true;
-            }
-            q->cv_dispatch.notify_all();
-            q->dispatcher.join();
+        // stop what started, in pipeline order (nothing has been submitted)
+        {
+            std::lock_guard<std::mutex> lk(q->mu);
+            q->stop = true;
         }
+        q->cv_dispatch.notify_all();
+        if (q->dispatcher.joinable()) q->dispatcher.join();
+        {
+            std::lock_guard<std::mutex> lk(q->mu);
+            q->dispatcher_done = true;
+        }
+        q->cv_score.notify_all();
+        if (q->scorer.joinable()) q->scorer.join();
+        {
+            std::lock_guard<std::mutex> lk(q->mu);
+            q->scorer_done = true;
+        }
+        q->cv_complete.notify_all();
+        if (q->completer.joinable()) q->completer.join();
         queue_free(q);
         return fail(c, REFINE_ENOMEM, "queue: cannot start threads");
     }
@@ -647,11 +778,35 @@ refine_status refine_queue_poll(refine_queue *q, uint64_t ticket, refine_result 
     return REFINE_OK;
 }
 
+refine_status refine_queue_poll_any(refine_queue *q, uint64_t *ticket_out, refine_result *out, int32_t timeout_ms)
+{
+    if (!q || !ticket_out || !out) return REFINE_EINVAL;
+    std::unique_lock<std::mutex> lk(q->mu);
+    if (q->live.empty()) return REFINE_ENOTFOUND;
+    auto ready = [&] { return !q->results.empty(); };
+    if (!ready()) {
+        if (timeout_ms == 0) return REFINE_ETIMEOUT;
+        if (timeout_ms < 0)
+            q->cv_poll.wait(lk, ready);
+        else if (!q->cv_poll.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready))
+            return REFINE_ETIMEOUT;
+    }
+    auto best = q->results.begin();
+    for (auto it = q->results.begin(); it != q->results.end(); ++it)
+        if (it->first < best->first) best = it;
+    *ticket_out = best->first;
+    *out = best->second;
+    q->live.erase(best->first);
+    q->results.erase(best);
+    return REFINE_OK;
+}
+
 const char *refine_queue_last_error(refine_queue *q)
 {
     if (!q) return "NULL queue";
     std::lock_guard<std::mutex> lk(q->mu);
-    snprintf(q->err_copy, sizeof q->err_copy, "%s%s%s", q->pc.err, q->pc.err[0] && q->cerr[0] ? "; " : "", q->cerr);
+    snprintf(q->err_copy, sizeof q->err_copy, "%s%s%s%s%s", q->pc.err, q->pc.err[0] && q->sc.err[0] ? "; " : "",
+             q->sc.err, (q->pc.err[0] || q->sc.err[0]) && q->cerr[0] ? "; " : "", q->cerr);
     return q->err_copy;
 }
 
@@ -671,6 +826,8 @@ refine_status refine_queue_stats_get(refine_queue *q, refine_queue_stats *out)
     out->max_round = q->max_round;
     out->slots = q->slots;
     out->kernel_launches = q->launches.load();
+    out->dispatch_ms = q->dispatch_ms;
+    out->retire_ms = q->retire_ms;
     return REFINE_OK;
 }
 
@@ -687,10 +844,15 @@ void refine_queue_destroy(refine_queue *q)
         q->pending.clear();
     }
     q->cv_dispatch.notify_all();
+    // the dispatcher stops admitting; the scorer then scores what was
+    // admitted and stops; the completion thread retires it and stops
     if (q->dispatcher.joinable()) q->dispatcher.join();
+    if (q->scorer.joinable()) q->scorer.join();
     if (q->completer.joinable()) q->completer.join();
     cudaSetDevice(q->pc.device);
     for (cudaStream_t s : q->slot_stream)
+        if (s) cudaStreamSynchronize(s);
+    for (cudaStream_t s : {q->h2d_stream, q->d2h_stream, q->score_stream})
         if (s) cudaStreamSynchronize(s);
     queue_free(q);
 }

@@ -335,6 +335,7 @@ struct refine_batch {
         long long total_tiles = 0;
         int max_v = 0;                         // largest camera block of the level
         int grid = 1;
+        int rounds = kBatchRounds;             // item size (batch_rounds)
     };
     std::vector<Level> levels;
     ScoreShape shape;
@@ -388,6 +389,7 @@ refine_status batch_record(refine_batch *b)
         bl.total_tiles = lv.total_tiles;
         bl.counter = lv.d_counter;
         bl.status = c->d_status;
+        bl.rounds = lv.rounds;
         e = launch_score_batch(bl, lv.max_v, lv.grid, b->shape, m);
         if (e == cudaSuccess) ++launches;
     }
@@ -431,11 +433,15 @@ refine_status batch_record(refine_batch *b)
 // device (on `s`, or synchronously when s is NULL), and its grid.
 cudaError_t set_level_tiles(refine_batch *b, refine_batch::Level &lv, const ScoreShape &sh, cudaStream_t s)
 {
-    const long long tile = batch_tile(sh);
+    std::vector<int64_t> ns;
+    for (int j : lv.jobs) ns.push_back(b->jobs[j].scene.n);
+    const int full_grid = score_batch_grid(b->ctx->num_sms, lv.max_v, sh);
+    lv.rounds = batch_rounds(sh, ns.data(), (int)ns.size(), full_grid);
+    const long long tile = batch_tile(sh, lv.rounds);
     std::vector<long long> tb(lv.jobs.size() + 1, 0);
-    for (size_t k = 0; k < lv.jobs.size(); ++k) tb[k + 1] = tb[k] + (b->jobs[lv.jobs[k]].scene.n + tile - 1) / tile;
+    for (size_t k = 0; k < lv.jobs.size(); ++k) tb[k + 1] = tb[k] + (ns[k] + tile - 1) / tile;
     lv.total_tiles = tb.back();
-    lv.grid = score_batch_grid(b->ctx->num_sms, lv.max_v, sh);
+    lv.grid = full_grid;
     if (lv.grid > lv.total_tiles) lv.grid = (int)lv.total_tiles;
     if (lv.grid < 1) lv.grid = 1;
     const size_t bytes = sizeof(long long) * tb.size();
@@ -717,6 +723,7 @@ refine_status refine_autotune(refine_ctx *c, const refine_job *jobs, int32_t n_j
                             bl.total_tiles = lv.total_tiles;
                             bl.counter = lv.d_counter;
                             bl.status = c->d_status;
+                            bl.rounds = lv.rounds;
                             e = cudaMemsetAsync(lv.d_counter, 0, sizeof(unsigned long long), m);
                             if (e == cudaSuccess) e = launch_score_batch(bl, lv.max_v, lv.grid, sh, m);
                         }

@@ -49,7 +49,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", offsetof(refine_params, e_ln_gem), offsetof(refine_params, flags), offsetof(refine_scene_stats, mean_m), offsetof(refine_scene_stats, exact_warp_axes));
   printf("%zu %zu %zu\\n", sizeof(refine_request), sizeof(refine_result), sizeof(refine_queue_stats));
   printf("%zu %zu %zu %zu\\n", offsetof(refine_request, ratio), offsetof(refine_request, kept_idx_host), offsetof(refine_result, threshold), offsetof(refine_result, done_ms));
-  printf("%zu %zu\\n", offsetof(refine_queue_stats, max_round), offsetof(refine_queue_stats, kernel_launches));
+  printf("%zu %zu %zu\\n", offsetof(refine_queue_stats, max_round), offsetof(refine_queue_stats, kernel_launches), offsetof(refine_queue_stats, retire_ms));
   printf("%zu %zu\\n", sizeof(refine_shape), offsetof(refine_shape, ms));
   return 0; }
 ''')
@@ -66,7 +66,8 @@ int main(void) {
     assert got[3] == [C.sizeof(b.refine_request), C.sizeof(b.refine_result), C.sizeof(b.refine_queue_stats)]
     assert got[4] == [b.refine_request.ratio.offset, b.refine_request.kept_idx_host.offset,
                       b.refine_result.threshold.offset, b.refine_result.done_ms.offset]
-    assert got[5] == [b.refine_queue_stats.max_round.offset, b.refine_queue_stats.kernel_launches.offset]
+    assert got[5] == [b.refine_queue_stats.max_round.offset, b.refine_queue_stats.kernel_launches.offset,
+                      b.refine_queue_stats.retire_ms.offset]
     assert got[6] == [C.sizeof(b.refine_shape), b.refine_shape.ms.offset]
 
 

@@ -247,3 +247,27 @@ def test_errors_stay_with_their_request_while_the_round_ring_turns(env):
         assert q.stats()["rounds"] > 2  # the two ring entries were reused
     finally:
         q.close()
+
+
+def test_poll_any_returns_in_completion_order(env):
+    """refine_queue_poll_any hands out every request exactly once, whichever
+    finishes first, with the same results as polling by ticket; with nothing
+    outstanding it reports ENOTFOUND."""
+    torch, rb, ctx = env
+    sc = scenes()
+    refs = [plain(torch, rb, ctx, w, r) for w, r in sc]
+    q = rb.Queue(ctx, budget_bytes=8 << 30, max_slots=4)
+    try:
+        tickets = {q.submit(*host_inputs(w), r, scores=True): k for k, (w, r) in enumerate(sc)}
+        got = set()
+        for _ in range(len(tickets)):
+            t, res, out = q.poll_any(timeout_ms=60_000)
+            assert t in tickets and t not in got
+            got.add(t)
+            k = tickets[t]
+            check_same(refs[k], res, out, sc[k][0])
+        assert got == set(tickets)
+        with pytest.raises(rb.RefineError):
+            q.poll_any(timeout_ms=0)
+    finally:
+        q.close()
