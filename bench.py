@@ -304,6 +304,34 @@ def end_to_end(args, torch, rb, ctx, w, attr, params, ratio, n_keep, pairs, V_al
     dt_seq = (time.perf_counter() - t0) / k_e2e
     sequential = {"value": pairs / dt_seq, "unit": "pairs/s", "ms_per_step": dt_seq * 1000, "steps": k_e2e,
                   "api": "refine_prune_host, one call after another"}
+    if not args.no_ply:
+        # the whole pruning as the paper times it (Table 2: sorting and saving
+        # the primitives included): each step also writes the kept scene as a
+        # 3DGS PLY file on the host
+        import tempfile
+        fd, path = tempfile.mkstemp(suffix=".ply")
+        os.close(fd)
+
+        def host_rows(o):
+            a = o["out_attr"]
+            a = a.view(torch.int16).numpy().view(np.uint16) if a.dtype == torch.bfloat16 else a.numpy()
+            return o["out_pos"].numpy(), a
+        k_ply = max(2, min(args.steps, 5))
+        try:
+            ctx.prune_host(pos_h, attr_h, w.cams, ratio, params=params, out=outs, stream=stream)
+            rb.write_ply(path, *host_rows(outs))
+            t0 = time.perf_counter()
+            for _ in range(k_ply):
+                ctx.prune_host(pos_h, attr_h, w.cams, ratio, params=params, out=outs, stream=stream)
+                rb.write_ply(path, *host_rows(outs))
+            dt_ply = (time.perf_counter() - t0) / k_ply
+            ply_bytes = os.path.getsize(path)
+        finally:
+            os.remove(path)
+        sequential["with_ply"] = {"value": pairs / dt_ply, "unit": "pairs/s", "ms_per_step": dt_ply * 1000,
+                                  "steps": k_ply, "ply_bytes": ply_bytes,
+                                  "api": "refine_prune_host + refine_write_ply of the kept scene (host temporary "
+                                         "directory), one step after another"}
 
     D = args.e2e_inflight
     if D < 2:
@@ -897,6 +925,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c0"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ply", action="store_true", help="end to end: leave out the timed PLY writing")
     ap.add_argument("--e2e-inflight", type=int, default=3,
                     help="requests in flight in the end-to-end measurement (1: sequential calls only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
