@@ -477,10 +477,10 @@ void refine_queue_destroy(refine_queue *q);
  *   errbuf   host buffer of errlen bytes for a message, or NULL
  * Every call looks up the array's device address (cudaGetSymbolAddress) on
  * the calling thread's current device; the first call on a device also
- * loads the library's device code there, so make that first call before any
- * stream capture.  Every call on a device shares the one array and
- * each call resets it: calls whose work overlaps on the GPU (other streams,
- * other threads) race and must be serialised by the caller.  NaN scores are
+ * loads the library's device code there.  Every call on a device shares the
+ * one array and each call resets it: calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * NaN scores are
  * reported (REFINE_ENONFINITE) only when threshold_out is non-NULL, which
  * makes the call synchronise `stream`. */
 refine_status refine_select_noalloc(const float *scores_dev, int64_t n, double ratio,

@@ -22,9 +22,7 @@ using namespace refine;
 namespace refine_api {
 
 enum KClass {
-    K_CAM_PREP = 0,
-    K_FEATURES,
-    K_FEAT_FINAL,
+    K_FEATURES = 0,
     K_CELLS,
     K_CELL_SCAN,
     K_CELL_SCATTER,
@@ -38,7 +36,7 @@ enum KClass {
     K_SELFTEST,
     K_NCLASS
 };
-const char *const kClassName[K_NCLASS] = {"cam_prep",      "features",     "features_finalize",
+const char *const kClassName[K_NCLASS] = {"features",
                                           "cells",         "cell_scan",    "cell_scatter",
                                           "score",         "select_pass",  "select_ties",
                                           "select_mask",   "mask_fill",    "compact_count",
@@ -248,7 +246,8 @@ struct SceneScratch {
     SceneConsts *consts;
     SceneStats *stats;
     uint2 *cell;  // (cell, slot within the cell) of every primitive
-    unsigned *counts;  // order_keys(bits) + 64 words; the last ones hold the scan's done counter
+    unsigned *counts;  // order_keys(bits) + 64 words; the two after the keys count the finished blocks of
+                       // the cell scan and of the feature pass
     unsigned *off_local;
     unsigned *bsum;
     uint32_t *perm;
@@ -318,15 +317,20 @@ inline refine_status enqueue_prep(refine_ctx *c, L &&run, const refine_scene *sc
     if (e == cudaSuccess && count) e = cudaMemsetAsync(x.need, 0, kCountSlots * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
     refine_status st;
-    if ((st = run(K_CAM_PREP, [&] { return launch_cam_prep(cams, pl.V, pl.vstride, x.cams, status, s); })))
-        return st;
+    FeatureTail tail;
+    tail.cams = cams;
+    tail.V = pl.V;
+    tail.vstride = pl.vstride;
+    tail.cam_out = x.cams;
+    tail.p = p;
+    tail.cell_bits = pl.bits;
+    tail.consts = x.consts;
+    tail.stats = x.stats;
+    tail.done = x.counts + cells + 1;  // zeroed with the counts above
     if ((st = run(K_FEATURES, [&] {
              return launch_features(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, p.eta, p.luma, x.recs,
-                                    x.partials, status, s);
+                                    x.partials, status, tail, s);
          })))
-        return st;
-    if ((st = run(K_FEAT_FINAL,
-                  [&] { return launch_features_finalize(x.partials, pl.nb, n, &p, pl.bits, x.consts, x.stats, s); })))
         return st;
     if ((st = run(K_CELLS, [&] {
              return launch_cells(sc->pos, sc->attr, sc->dtype, sc->row_stride, n, pl.bits, x.consts, x.cell,

@@ -130,16 +130,23 @@ struct ScoreLaunch {
     int grid;                   // CTAs (persistent)
 };
 
-// Camera records of views 0, vstride, 2 vstride, ... (V of them).
-cudaError_t launch_cam_prep(const refine_camera *cams, int V, int vstride, CamRec *out, int *status,
-                            cudaStream_t s);
+// What the feature pass's last block does after the sums: the scene
+// constants (Eq. 18-19, the processing-order grid and size split) and the
+// camera records of views 0, vstride, 2 vstride, ... (V of them).
+struct FeatureTail {
+    const refine_camera *cams;
+    int V, vstride;
+    CamRec *cam_out;
+    refine_params p;
+    int cell_bits;
+    SceneConsts *consts;
+    SceneStats *stats;
+    unsigned *done;  // count of finished blocks, zero before the launch
+};
 int feature_blocks(int64_t n);
 cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
                             float eta, const float luma[3], PrimRec *recs, double *partials, int *status,
-                            cudaStream_t s);
-cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_t n,
-                                     const refine_params *p, int cell_bits, SceneConsts *consts,
-                                     SceneStats *stats, cudaStream_t s);
+                            const FeatureTail &tail, cudaStream_t s);
 cudaError_t launch_cells(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n, int cell_bits,
                          const SceneConsts *consts, uint2 *cell, unsigned *counts, int num_sms, cudaStream_t s);
 cudaError_t launch_cell_scan(unsigned *counts, unsigned *off_local, unsigned *bsum, unsigned *done, int cell_bits,

@@ -11,11 +11,9 @@ namespace refine {
 // Camera preparation: refine_camera -> CamRec (P = K W and p = K t formed
 // in double and rounded once), with validation.
 // ---------------------------------------------------------------------
-__global__ void k_cam_prep(const refine_camera *__restrict__ cams, int V, int vstride, CamRec *__restrict__ out,
-                           int *status)
+__device__ void prep_camera(const refine_camera *__restrict__ cams, int v, int vstride, CamRec *__restrict__ out,
+                            int *status)
 {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
     refine_camera c = cams[(int64_t)v * vstride];
     bool ok = isfinite(c.fx) && isfinite(c.fy) && isfinite(c.cx) && isfinite(c.cy) &&
               isfinite(c.znear) && isfinite(c.zfar) && c.fx > 0.f && c.fy > 0.f &&
@@ -52,25 +50,97 @@ __global__ void k_cam_prep(const refine_camera *__restrict__ cams, int V, int vs
     out[v] = r;
 }
 
-cudaError_t launch_cam_prep(const refine_camera *cams, int V, int vstride, CamRec *out, int *status,
-                            cudaStream_t s)
+// Eq. (features) -> Eq. 18 -> Eq. 19 in double, by one block (every thread
+// calls it); also the grid box (mean +- 3 sigma of the means) and the size
+// split of the processing order.
+__device__ void finalize_features(const double *partials, int nblocks, int64_t n, const refine_params &p,
+                                  int cell_bits, SceneConsts *consts, SceneStats *stats)
 {
-    k_cam_prep<<<(V + 127) / 128, 128, 0, s>>>(cams, V, vstride, out, status);
-    return cudaGetLastError();
+    // each sum k is reduced by one warp over the block partials in a fixed
+    // order (lane-strided, then a shuffle tree), whichever warp it is
+    __shared__ double red[kFeatSums][1];
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int k = threadIdx.x >> 5; k < kFeatSums; k += nwarps) {
+        double v = 0.0;
+#pragma unroll 4
+        for (int b = lane; b < nblocks; b += 32) v += __ldcg(partials + (int64_t)b * kFeatSums + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][0] = v;
+    }
+    __syncthreads();
+    // The scalar tail in double, spread over three threads: thread t forms
+    // lambda~ of attribute t (Eq. 18), then its lambda, kappa (Eq. 19) and
+    // the grid box along axis t, each by the same expression as a one-thread
+    // evaluation would use.
+    __shared__ double lam_t[3];
+    const int t = threadIdx.x;
+    const double N = (double)n;
+    if (t < 3) {
+        double lt;
+        if (t == 0) {
+            lt = log(red[3][0] / N + (double)p.eta) / p.e_ln_gem;
+        } else if (t == 1) {
+            const double ybar = red[0][0] / N;
+            double fc = red[1][0] / N - ybar * ybar;
+            if (fc < 0.0) fc = 0.0;
+            lt = fc / p.e_col;
+            if (stats) stats->F_col = fc;
+        } else {
+            lt = (red[2][0] / N) / p.e_opa;
+        }
+        if (!(lt > 0.0)) lt = 0.0;
+        lam_t[t] = lt;
+    }
+    __syncthreads();
+    if (t >= 3) return;  // no barrier follows
+    const double tot = (lam_t[0] + lam_t[1]) + lam_t[2];
+    const double lambda = ((p.flags & REFINE_FLAG_EQUAL_LAMBDA) || tot == 0.0) ? 1.0 / 3.0 : lam_t[t] / tot;
+    const double mean_m = red[4 + t][0] / N;
+    double kap = lambda;
+    if (p.flags & REFINE_FLAG_NORM_ATTR) kap = mean_m > 0.0 ? lambda / mean_m : 0.0;
+    consts->kappa[t] = (float)kap;
+    const double mean = red[7 + t][0] / N;
+    const double var = red[10 + t][0] / N - mean * mean;
+    const double sd = var > 0.0 ? sqrt(var) : 0.0;
+    consts->lo[t] = (float)(mean - 3.0 * sd);
+    consts->qscale[t] = sd > 0.0 && isfinite(sd) ? (float)((1 << cell_bits) / (6.0 * sd)) : 0.f;
+    if (t < 2) consts->pad[t] = 0.f;
+    if (t == 0) {
+        // The primitives whose ln s_max lies above its scene mean + 1.28 sd
+        // (the largest ~10 % for a normal spread) are ordered after all the
+        // others, so that the tiles of the rest carry small footprint bounds.
+        const double ml = red[13][0] / N, vl = red[14][0] / N - ml * ml;
+        const double big = ml + kSizeSplitSd * (vl > 0.0 ? sqrt(vl) : 0.0);
+        consts->big_ls = isfinite(big) ? (float)big : INFINITY;
+    }
+    if (stats) {
+        stats->lambda_t[t] = lam_t[t];
+        stats->lambda[t] = lambda;
+        stats->mean_m[t] = mean_m;
+        if (t == 0) {
+            stats->F_opa = red[2][0] / N;
+            stats->F_gem = red[3][0] / N;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------
 // Content features.  One primitive per thread: its 59 attribute rows are
 // read with coalesced loads (all in flight at once), its record and its
-// feature terms formed (primitive_record), thirteen sums per thread kept in
-// float and reduced per block in a fixed double tree.
+// feature terms formed (primitive_record), fifteen sums per thread kept in
+// float and reduced per block in a fixed double tree.  The block that
+// finishes last (a count of finished blocks, no waiting) then forms the
+// scene constants from all blocks' sums (finalize_features) and the camera
+// records (prep_camera), which saves two small launches per scene.
 // ---------------------------------------------------------------------
 template <typename AT>
 __global__ void __launch_bounds__(kFeatThreads, 4) k_features(const float *__restrict__ pos,
                                                            const AT *__restrict__ attr, int64_t S, int64_t n,
                                                            float eta, float l0, float l1, float l2,
                                                            PrimRec *__restrict__ recs,
-                                                           double *__restrict__ partials, int *status)
+                                                           double *__restrict__ partials, int *status,
+                                                           FeatureTail tail)
 {
     FeatSums acc;
 #pragma unroll
@@ -108,6 +178,17 @@ __global__ void __launch_bounds__(kFeatThreads, 4) k_features(const float *__res
         __syncthreads();
     }
     if (threadIdx.x < kFeatSums) partials[(int64_t)blockIdx.x * kFeatSums + threadIdx.x] = red[threadIdx.x][0];
+
+    // the last block to finish: scene constants and camera records
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(tail.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int v = threadIdx.x; v < tail.V; v += blockDim.x) prep_camera(tail.cams, v, tail.vstride, tail.cam_out, status);
+    finalize_features(partials, gridDim.x, n, tail.p, tail.cell_bits, tail.consts, tail.stats);
 }
 
 // A single wave on a 152-SM part (4 CTAs of 256 threads per SM); the grid
@@ -122,99 +203,19 @@ int feature_blocks(int64_t n)
 
 cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
                             float eta, const float luma[3], PrimRec *recs, double *partials, int *status,
-                            cudaStream_t s)
+                            const FeatureTail &tail, cudaStream_t s)
 {
     const int nb = feature_blocks(n);
     if (dtype == REFINE_BF16)
         k_features<__nv_bfloat16><<<nb, kFeatThreads, 0, s>>>(pos, static_cast<const __nv_bfloat16 *>(attr), stride,
                                                               n, eta, luma[0], luma[1], luma[2], recs, partials,
-                                                              status);
+                                                              status, tail);
     else
         k_features<float><<<nb, kFeatThreads, 0, s>>>(pos, static_cast<const float *>(attr), stride, n, eta, luma[0],
-                                                      luma[1], luma[2], recs, partials, status);
+                                                      luma[1], luma[2], recs, partials, status, tail);
     return cudaGetLastError();
 }
 
-// Eq. (features) -> Eq. 18 -> Eq. 19 in double, one block; also the grid box
-// (mean +- 3 sigma of the means) of the processing order.
-__global__ void __launch_bounds__(32 * kFeatSums) k_features_finalize(const double *__restrict__ partials,
-                                                                      int nblocks, int64_t n, refine_params p,
-                                                                      int cell_bits, SceneConsts *consts,
-                                                                      SceneStats *stats)
-{
-    // warp k reduces sum k over the block partials in a fixed order
-    __shared__ double red[kFeatSums][1];
-    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double v = 0.0;
-#pragma unroll 4
-    for (int b = lane; b < nblocks; b += 32) v += partials[(int64_t)b * kFeatSums + k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[k][0] = v;
-    __syncthreads();
-    // The scalar tail in double, spread over three threads: thread t forms
-    // lambda~ of attribute t (Eq. 18), then its lambda, kappa (Eq. 19) and
-    // the grid box along axis t, each by the same expression as a one-thread
-    // evaluation would use.
-    __shared__ double lam_t[3];
-    const int t = threadIdx.x;
-    const double N = (double)n;
-    if (t < 3) {
-        double lt;
-        if (t == 0) {
-            lt = log(red[3][0] / N + (double)p.eta) / p.e_ln_gem;
-        } else if (t == 1) {
-            const double ybar = red[0][0] / N;
-            double fc = red[1][0] / N - ybar * ybar;
-            if (fc < 0.0) fc = 0.0;
-            lt = fc / p.e_col;
-            if (stats) stats->F_col = fc;
-        } else {
-            lt = (red[2][0] / N) / p.e_opa;
-        }
-        if (!(lt > 0.0)) lt = 0.0;
-        lam_t[t] = lt;
-    }
-    __syncthreads();
-    if (t >= 3) return;
-    const double tot = (lam_t[0] + lam_t[1]) + lam_t[2];
-    const double lambda = ((p.flags & REFINE_FLAG_EQUAL_LAMBDA) || tot == 0.0) ? 1.0 / 3.0 : lam_t[t] / tot;
-    const double mean_m = red[4 + t][0] / N;
-    double kap = lambda;
-    if (p.flags & REFINE_FLAG_NORM_ATTR) kap = mean_m > 0.0 ? lambda / mean_m : 0.0;
-    consts->kappa[t] = (float)kap;
-    const double mean = red[7 + t][0] / N;
-    const double var = red[10 + t][0] / N - mean * mean;
-    const double sd = var > 0.0 ? sqrt(var) : 0.0;
-    consts->lo[t] = (float)(mean - 3.0 * sd);
-    consts->qscale[t] = sd > 0.0 && isfinite(sd) ? (float)((1 << cell_bits) / (6.0 * sd)) : 0.f;
-    if (t < 2) consts->pad[t] = 0.f;
-    if (t == 0) {
-        // The primitives whose ln s_max lies above its scene mean + 1.28 sd
-        // (the largest ~10 % for a normal spread) are ordered after all the
-        // others, so that the tiles of the rest carry small footprint bounds.
-        const double ml = red[13][0] / N, vl = red[14][0] / N - ml * ml;
-        const double big = ml + kSizeSplitSd * (vl > 0.0 ? sqrt(vl) : 0.0);
-        consts->big_ls = isfinite(big) ? (float)big : INFINITY;
-    }
-    if (stats) {
-        stats->lambda_t[t] = lam_t[t];
-        stats->lambda[t] = lambda;
-        stats->mean_m[t] = mean_m;
-        if (t == 0) {
-            stats->F_opa = red[2][0] / N;
-            stats->F_gem = red[3][0] / N;
-        }
-    }
-}
-
-cudaError_t launch_features_finalize(const double *partials, int nblocks, int64_t n,
-                                     const refine_params *p, int cell_bits, SceneConsts *consts,
-                                     SceneStats *stats, cudaStream_t s)
-{
-    k_features_finalize<<<1, 32 * kFeatSums, 0, s>>>(partials, nblocks, n, *p, cell_bits, consts, stats);
-    return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------
 // Processing order.  Primitives are sorted by their cell in a 2^b x 2^b x
