@@ -446,12 +446,28 @@ struct PairIn {
     float b2;  // 9 s_max^2 (1 + 2^-10)
 };
 
-struct TileBox {
+struct __align__(16) TileBox {
     float cx, cy, cz;  // centre of the box of the tile's centres
     float hx, hy, hz;  // half extents
     float mx, my, mz;  // |centre| + half extent (magnitude bound)
     float b2;          // max over the tile of 9 s_max^2 (1 + 2^-10)
+    float pad[2];
 };
+
+// The tile box lives in the warp's shared-memory slot while its views are
+// scored and is read back for each classification, so that it holds no
+// registers across the view loop (the loads are volatile: never hoisted).
+__device__ __forceinline__ TileBox load_box(const TileBox *s)
+{
+    TileBox t;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(s);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(t.cx), "=f"(t.cy), "=f"(t.cz), "=f"(t.hx) : "r"(a));
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(t.hy), "=f"(t.hz), "=f"(t.mx), "=f"(t.my) : "r"(a + 16));
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(t.mz), "=f"(t.b2) : "r"(a + 32));
+    return t;
+}
 
 constexpr float kTileSlack = 6.103515625e-05f;  // 2^-14
 
@@ -737,7 +753,7 @@ __device__ __forceinline__ void mixed_view_ax(const CamRec &c, float eta, const 
 
 template <int PM, bool DET, bool COUNT, int GPT>
 __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float eta, const PairIn (&p)[GPT],
-                                          const bool (&valid)[GPT], const TileBox &tb,
+                                          const bool (&valid)[GPT], const TileBox *tbs,
                                           float (&acc)[GPT], float (&comp)[GPT],
                                           unsigned long long (&cnt)[kCountSlots])
 {
@@ -750,6 +766,7 @@ __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float et
         const unsigned vmask = nv == 32 ? 0xffffffffu : ((1u << nv) - 1u);
         unsigned in_m = 0u, out_m = 0u, ux_m = 0u, uy_m = 0u, uz_m = 0u;
         if (!DET) {
+            const TileBox tb = load_box(tbs);
             const int cls = lane < nv ? classify(cs[vb + lane], tb) : (kAxX | kAxY | kAxZ);
             in_m = __ballot_sync(0xffffffffu, (cls & 3) == kClsIn);
             out_m = __ballot_sync(0xffffffffu, (cls & 3) == kClsOut);
@@ -833,10 +850,12 @@ __device__ __forceinline__ void fence_proxy_async_shared()
 
 // Scores one warp tile: the 32 * GPT primitives of the processing order
 // starting at `base`; `next_base` (or -1) is the tile this warp takes next,
-// whose primitives are pulled towards L2 meanwhile.
+// whose primitives are pulled towards L2 meanwhile.  `tbs` is the warp's
+// shared-memory slot for the tile box.
 template <int PM, bool COUNT, int GPT>
 __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *cs, const SceneConsts &sc,
-                                           int64_t base, int64_t next_base, unsigned long long (&cnt)[kCountSlots])
+                                           int64_t base, int64_t next_base, TileBox *tbs,
+                                           unsigned long long (&cnt)[kCountSlots])
 {
     const int lane = threadIdx.x & 31;
     if (next_base >= 0) {
@@ -848,7 +867,6 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
     }
     PairIn p[GPT];
     float acc[GPT], comp[GPT];
-    int64_t idx[GPT];
     bool valid[GPT];
     bool degen = false;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, b2 = 0.f;
@@ -856,13 +874,11 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
     for (int g = 0; g < GPT; ++g) {
         const int64_t j = base + g * 32 + lane;
         float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
-        idx[g] = -1;
         acc[g] = 0.f;
         comp[g] = 0.f;
         valid[g] = j < a.n;
         if (valid[g]) {
             const int64_t i = __ldg(a.perm + j);
-            idx[g] = i;
             const PrimRec *r = a.recs + i;
             ra = __ldg(&r->a); rb = __ldg(&r->b); rc = __ldg(&r->c); rd = __ldg(&r->d);
             if (!a.first) {
@@ -885,28 +901,35 @@ __device__ __forceinline__ void score_tile(const ScoreLaunch &a, const CamRec *c
     }
     if (!__any_sync(0xffffffffu, valid[0])) return;  // warp past the end
 
-    TileBox tb;
     {
         const float l0 = warp_min(lo[0]), l1 = warp_min(lo[1]), l2 = warp_min(lo[2]);
         const float h0 = warp_max(hi[0]), h1 = warp_max(hi[1]), h2 = warp_max(hi[2]);
-        tb.b2 = warp_max(b2);
-        tb.cx = 0.5f * (l0 + h0); tb.hx = 0.5f * (h0 - l0);
-        tb.cy = 0.5f * (l1 + h1); tb.hy = 0.5f * (h1 - l1);
-        tb.cz = 0.5f * (l2 + h2); tb.hz = 0.5f * (h2 - l2);
-        tb.mx = fabsf(tb.cx) + tb.hx;
-        tb.my = fabsf(tb.cy) + tb.hy;
-        tb.mz = fabsf(tb.cz) + tb.hz;
+        const float tb2 = warp_max(b2);
+        __syncwarp();  // every lane is done with the previous tile's box
+        if (lane == 0) {
+            TileBox tb;
+            tb.b2 = tb2;
+            tb.cx = 0.5f * (l0 + h0); tb.hx = 0.5f * (h0 - l0);
+            tb.cy = 0.5f * (l1 + h1); tb.hy = 0.5f * (h1 - l1);
+            tb.cz = 0.5f * (l2 + h2); tb.hz = 0.5f * (h2 - l2);
+            tb.mx = fabsf(tb.cx) + tb.hx;
+            tb.my = fabsf(tb.cy) + tb.hy;
+            tb.mz = fabsf(tb.cz) + tb.hz;
+            tb.pad[0] = tb.pad[1] = 0.f;
+            *tbs = tb;
+        }
+        __syncwarp();
     }
 
     if (__any_sync(0xffffffffu, degen))
-        view_loop<PM, true, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tb, acc, comp, cnt);
+        view_loop<PM, true, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tbs, acc, comp, cnt);
     else
-        view_loop<PM, false, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tb, acc, comp, cnt);
+        view_loop<PM, false, COUNT, GPT>(cs, a.vcount, a.eta, p, valid, tbs, acc, comp, cnt);
 
 #pragma unroll
     for (int g = 0; g < GPT; ++g) {
-        const int64_t i = idx[g];
-        if (i < 0) continue;
+        if (!valid[g]) continue;
+        const int64_t i = __ldg(a.perm + base + g * 32 + lane);
         if (!a.last) {
             a.running[i] = make_float2(acc[g], comp[g]);
             continue;
@@ -931,10 +954,11 @@ __device__ __forceinline__ int cams_stageable(const CamRec *cams, int vcount)
 }
 
 template <int PM, bool COUNT, int GPT>
-__global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
+__global__ void __launch_bounds__(kScoreThreads, COUNT ? 1 : 4) k_score(ScoreLaunch a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ TileBox s_box[kScoreThreads / 32];
     CamRec *cs = reinterpret_cast<CamRec *>(smem_raw);
 
     // Stage this pass's cameras once per CTA (TMA bulk copy, mbarrier).
@@ -980,7 +1004,7 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
         if (lane == 0) nxt = (int)min((unsigned long long)ntiles, atomicAdd(a.tiles_taken, 1ull));
         nxt = __shfl_sync(0xffffffffu, nxt, 0);
         score_tile<PM, COUNT, GPT>(a, cs, sc, (int64_t)cur * (32 * GPT),
-                                   nxt < ntiles ? (int64_t)nxt * (32 * GPT) : -1, cnt);
+                                   nxt < ntiles ? (int64_t)nxt * (32 * GPT) : -1, &s_box[threadIdx.x >> 5], cnt);
         cur = nxt;
     }
     if (COUNT) {
@@ -1001,12 +1025,13 @@ __global__ void __launch_bounds__(kScoreThreads) k_score(ScoreLaunch a)
 // k_score, so a scene's scores are the same alone and in a batch; scenes
 // may differ in storage type (the records are float32) and in flags.
 template <int GPT, int THREADS>
-__global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLaunch b)
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_score_batch(BatchLaunch b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_scene, s_ok, s_wt;
     __shared__ long long s_base;
+    __shared__ TileBox s_box[THREADS / 32];
     CamRec *cs = reinterpret_cast<CamRec *>(smem_raw);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
@@ -1080,11 +1105,11 @@ __global__ void __launch_bounds__(THREADS, 768 / THREADS) k_score_batch(BatchLau
             if (t >= wtiles) break;
             const int64_t wbase = base + (int64_t)t * (32 * GPT);
             if (pm == kProjEq17)
-                score_tile<kProjEq17, false, GPT>(a, cs, sc, wbase, -1, cnt);
+                score_tile<kProjEq17, false, GPT>(a, cs, sc, wbase, -1, &s_box[threadIdx.x >> 5], cnt);
             else if (pm == kProjNone)
-                score_tile<kProjNone, false, GPT>(a, cs, sc, wbase, -1, cnt);
+                score_tile<kProjNone, false, GPT>(a, cs, sc, wbase, -1, &s_box[threadIdx.x >> 5], cnt);
             else
-                score_tile<kProjFullJ, false, GPT>(a, cs, sc, wbase, -1, cnt);
+                score_tile<kProjFullJ, false, GPT>(a, cs, sc, wbase, -1, &s_box[threadIdx.x >> 5], cnt);
         }
         __syncthreads();  // the cameras, s_scene and s_wt are free again
     }
