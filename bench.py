@@ -44,7 +44,7 @@ FLOP_COSTS = {
                           # times 9 s_max^2, compare
     "exact_axis": 30,     # per needed extent: g = z P - U P2 (3 MUL, 3 FMA), L g (3 MUL, 6 FMA),
                           # |L g|^2 (MUL, 2 FMA), compare
-    "kahan_block": 4,     # per primitive and 16-view block: compensated add of the block sum
+    "kahan_block": 4,     # per primitive and 32-view block: compensated add of the block sum
     "epilogue": 8,        # per primitive: Eq. 7 coupling and the Eq. 20 scaling
 }
 FP32_LANES_PER_SM = 128
@@ -113,7 +113,7 @@ def score_work_flops(st: dict, n: int, views: int) -> float:
                  + st["open_z_pairs"] * c["open_depth"] + st["visible_mixed_pairs"] * c["visible_mixed"]
                  + st["bound_pairs"] * c["bound_pair"] + (st["bound_u_pairs"] + st["bound_v_pairs"]) * c["bound_axis"]
                  + (st["exact_u_pairs"] + st["exact_v_pairs"]) * c["exact_axis"]
-                 + n * ((views + 15) // 16) * c["kahan_block"] + n * c["epilogue"])
+                 + n * ((views + 31) // 32) * c["kahan_block"] + n * c["epilogue"])
 
 
 class ClockSampler:

@@ -434,7 +434,7 @@ cudaError_t launch_cell_scatter(const uint2 *cell, int64_t n, const unsigned *of
 //    centre outside is first tested against Qx <= 9 s_max^2 ((U - cx z)^2 +
 //    fx^2 z^2) (as |g0|^2 = fx^2 (x^2 + z^2); inflated by 2^-10), and only
 //    lanes passing that bound need Qx and Qy.
-// Views are summed in blocks of 16, in view order (an invisible or skipped
+// Views are summed in blocks of 32, in view order (an invisible or skipped
 // view adds +0, which changes nothing), and the block sums are added to the
 // primitive's total with Kahan compensation, so a primitive's sum does not
 // depend on the tile it is in and its rounding error does not grow with V.
@@ -779,14 +779,11 @@ __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float et
                 cnt[kCntOutPairs] += (unsigned long long)__popc(out_m & vmask) * nvalid;
             }
         }
-#pragma unroll 1
-        for (int half = 0; half < 2; ++half) {
-            const unsigned hm = (half ? 0xffff0000u : 0x0000ffffu) & vmask;
-            if (!hm) break;
+        {
             float part[GPT];
 #pragma unroll
             for (int g = 0; g < GPT; ++g) part[g] = 0.f;
-            unsigned todo = hm & ~out_m;
+            unsigned todo = vmask & ~out_m;
             while (todo) {
                 const int b = __ffs(todo) - 1;
                 todo &= todo - 1u;
@@ -812,7 +809,7 @@ __device__ __forceinline__ void view_loop(const CamRec *cs, int vcount, float et
                         mixed_view_ax<PM, COUNT, GPT, false, true, false>(c, eta, p, valid, part, cnt);
                 }
             }
-            // Kahan-compensated sum of the 16-view partial sums
+            // Kahan-compensated sum of the 32-view partial sums
 #pragma unroll
             for (int g = 0; g < GPT; ++g) {
                 const float y = part[g] - comp[g];
