@@ -242,7 +242,7 @@ struct ScenePlan {
 struct SceneScratch {
     CamRec *cams;
     PrimRec *recs;
-    double *partials;
+    float2 *partials;  // per feature-pass block, float-float sums
     SceneConsts *consts;
     SceneStats *stats;
     uint2 *cell;  // (cell, slot within the cell) of every primitive
@@ -276,7 +276,7 @@ inline ScenePlan plan_scene(int64_t n, int V, int max_views = 0, int vpp = kView
 inline size_t scene_bytes(const ScenePlan &pl)
 {
     const size_t n = (size_t)pl.n, cells = (size_t)order_keys(pl.bits);
-    return carve_size({sizeof(CamRec) * (size_t)pl.V, sizeof(PrimRec) * n, sizeof(double) * kFeatSums * 1024,
+    return carve_size({sizeof(CamRec) * (size_t)pl.V, sizeof(PrimRec) * n, sizeof(float2) * kFeatSums * 1024,
                        sizeof(SceneConsts), sizeof(SceneStats), sizeof(uint2) * n,
                        sizeof(unsigned) * (cells + 64), sizeof(unsigned) * cells,
                        sizeof(unsigned) * (cells / kScanCells), sizeof(uint32_t) * n,
@@ -291,7 +291,7 @@ inline SceneScratch carve_scene(Carver &cv, const ScenePlan &pl)
     SceneScratch x;
     x.cams = cv.take<CamRec>(pl.V);
     x.recs = cv.take<PrimRec>(n);
-    x.partials = cv.take<double>(kFeatSums * 1024);
+    x.partials = cv.take<float2>(kFeatSums * 1024);
     x.consts = cv.take<SceneConsts>(1);
     x.stats = cv.take<SceneStats>(1);
     x.cell = cv.take<uint2>(n);

@@ -59,6 +59,30 @@ struct SceneStats {
 // ln s_max with its square (for the size split of the processing order).
 constexpr int kFeatSums = 15;
 
+// Float-float numbers: an unevaluated sum hi + lo of two floats, added on
+// the FP32 pipes (the FP64 rate of this part is 1/64 of the FP32 rate).
+// Each addition keeps the rounding error of its leading sum exactly
+// (Knuth's TwoSum) and renormalises with Dekker's FastTwoSum, so a sum of
+// many terms carries about 44 significant bits.  Every step is an explicit
+// round-to-nearest add, never contracted, and the addition is commutative
+// bit for bit, so a fixed reduction order gives fixed bits.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, t);
+    return {hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+
+// The value as a double (exact: hi and lo do not overlap).
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
 // Per-thread content-feature sums (kFeatSums of them) and a non-finite trap.
 struct FeatSums {
     float s[kFeatSums];

@@ -130,9 +130,10 @@ struct ScoreLaunch {
     int grid;                   // CTAs (persistent)
 };
 
-// What the feature pass's last block does after the sums: the scene
-// constants (Eq. 18-19, the processing-order grid and size split) and the
-// camera records of views 0, vstride, 2 vstride, ... (V of them).
+// What the feature pass forms besides the primitive records: the camera
+// records of views 0, vstride, 2 vstride, ... (V of them, spread over its
+// blocks) and, in its last block, the scene constants (Eq. 18-19, the
+// processing-order grid and size split).
 struct FeatureTail {
     const refine_camera *cams;
     int V, vstride;
@@ -145,7 +146,7 @@ struct FeatureTail {
 };
 int feature_blocks(int64_t n);
 cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
-                            float eta, const float luma[3], PrimRec *recs, double *partials, int *status,
+                            float eta, const float luma[3], PrimRec *recs, float2 *partials, int *status,
                             const FeatureTail &tail, cudaStream_t s);
 cudaError_t launch_cells(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n, int cell_bits,
                          const SceneConsts *consts, uint2 *cell, unsigned *counts, int num_sms, cudaStream_t s);

@@ -53,20 +53,25 @@ __device__ void prep_camera(const refine_camera *__restrict__ cams, int v, int v
 // Eq. (features) -> Eq. 18 -> Eq. 19 in double, by one block (every thread
 // calls it); also the grid box (mean +- 3 sigma of the means) and the size
 // split of the processing order.
-__device__ void finalize_features(const double *partials, int nblocks, int64_t n, const refine_params &p,
+__device__ void finalize_features(const float2 *partials, int nblocks, int64_t n, const refine_params &p,
                                   int cell_bits, SceneConsts *consts, SceneStats *stats)
 {
     // each sum k is reduced by one warp over the block partials in a fixed
-    // order (lane-strided, then a shuffle tree), whichever warp it is
+    // order (lane-strided, then a shuffle tree) in float-float, whichever
+    // warp it is, and converted to double once
     __shared__ double red[kFeatSums][1];
     const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int k = threadIdx.x >> 5; k < kFeatSums; k += nwarps) {
-        double v = 0.0;
+        FF v = {0.f, 0.f};
 #pragma unroll 4
-        for (int b = lane; b < nblocks; b += 32) v += __ldcg(partials + (int64_t)b * kFeatSums + k);
+        for (int b = lane; b < nblocks; b += 32) {
+            const float2 q = __ldcg(partials + (int64_t)b * kFeatSums + k);
+            v = ff_add(v, FF{q.x, q.y});
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[k][0] = v;
+        for (int o = 16; o > 0; o >>= 1)
+            v = ff_add(v, FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+        if (lane == 0) red[k][0] = ff_to_double(v);
     }
     __syncthreads();
     // The scalar tail in double, spread over three threads: thread t forms
@@ -129,19 +134,31 @@ __device__ void finalize_features(const double *partials, int nblocks, int64_t n
 // Content features.  One primitive per thread: its 59 attribute rows are
 // read with coalesced loads (all in flight at once), its record and its
 // feature terms formed (primitive_record), fifteen sums per thread kept in
-// float and reduced per block in a fixed double tree.  The block that
+// float and reduced per block in a fixed float-float order.  The camera
+// records (prep_camera, in double) are spread over the blocks, one camera
+// per thread, blocks first, before the primitives.  The block that
 // finishes last (a count of finished blocks, no waiting) then forms the
-// scene constants from all blocks' sums (finalize_features) and the camera
-// records (prep_camera), which saves two small launches per scene.
+// scene constants from all blocks' sums (finalize_features), which saves
+// two small launches per scene.
 // ---------------------------------------------------------------------
+constexpr int kFeatRedLanes = 16;                                 // threads per sum in the block reduction
+constexpr int kFeatRedRow = kFeatThreads + kFeatRedLanes;         // padded row: two sums of a warp hit
+                                                                  // different banks
+static_assert(kFeatSums * kFeatRedLanes <= kFeatThreads, "one reduction thread per (sum, lane)");
+static_assert(kFeatThreads % kFeatRedLanes == 0, "whole columns per reduction lane");
+
 template <typename AT>
 __global__ void __launch_bounds__(kFeatThreads, 4) k_features(const float *__restrict__ pos,
                                                            const AT *__restrict__ attr, int64_t S, int64_t n,
                                                            float eta, float l0, float l1, float l2,
                                                            PrimRec *__restrict__ recs,
-                                                           double *__restrict__ partials, int *status,
+                                                           float2 *__restrict__ partials, int *status,
                                                            FeatureTail tail)
 {
+    for (int64_t v = blockIdx.x + (int64_t)gridDim.x * threadIdx.x; v < tail.V;
+         v += (int64_t)gridDim.x * blockDim.x)
+        prep_camera(tail.cams, (int)v, tail.vstride, tail.cam_out, status);
+
     FeatSums acc;
 #pragma unroll
     for (int k = 0; k < kFeatSums; ++k) acc.s[k] = 0.f;
@@ -166,20 +183,31 @@ __global__ void __launch_bounds__(kFeatThreads, 4) k_features(const float *__res
     if (!isfinite(acc.bad)) set_status(status, kEnonfinite);
     if (zero_q) set_status(status, kEinval);
 
-    __shared__ double red[kFeatSums][kFeatThreads];
+    // Block sums in float-float: thread (k, j) adds the values of threads
+    // j, j + 16, j + 32, ... of sum k in that order, then the 16 lanes of
+    // sum k meet in a shuffle tree (xor 8, 4, 2, 1).
+    __shared__ float red[kFeatSums * kFeatRedRow];
 #pragma unroll
-    for (int k = 0; k < kFeatSums; ++k) red[k][threadIdx.x] = (double)acc.s[k];
+    for (int k = 0; k < kFeatSums; ++k) red[k * kFeatRedRow + threadIdx.x] = acc.s[k];
     __syncthreads();
-    for (int h = kFeatThreads / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) {
+    if (threadIdx.x < kFeatSums * kFeatRedLanes) {
+        const int k = threadIdx.x / kFeatRedLanes, j = threadIdx.x % kFeatRedLanes;
+        const float *col = red + k * kFeatRedRow + j;
+        FF v = {col[0], 0.f};
 #pragma unroll
-            for (int k = 0; k < kFeatSums; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
-        }
-        __syncthreads();
+        for (int t = kFeatRedLanes; t < kFeatThreads; t += kFeatRedLanes) v = ff_add(v, FF{col[t], 0.f});
+        // lanes of other sums in the same warp run the same tree on their own
+        // 16-lane groups (xor below 16 stays within a group); the last warp
+        // may hold reduction threads in its low lanes only
+        constexpr int kRedThreads = kFeatSums * kFeatRedLanes;
+        const unsigned grp = (int)(threadIdx.x | 31u) < kRedThreads ? 0xffffffffu : (1u << (kRedThreads & 31)) - 1u;
+#pragma unroll
+        for (int o = kFeatRedLanes / 2; o > 0; o >>= 1)
+            v = ff_add(v, FF{__shfl_xor_sync(grp, v.hi, o), __shfl_xor_sync(grp, v.lo, o)});
+        if (j == 0) partials[(int64_t)blockIdx.x * kFeatSums + k] = make_float2(v.hi, v.lo);
     }
-    if (threadIdx.x < kFeatSums) partials[(int64_t)blockIdx.x * kFeatSums + threadIdx.x] = red[threadIdx.x][0];
 
-    // the last block to finish: scene constants and camera records
+    // the last block to finish: scene constants
     __shared__ bool s_last;
     __threadfence();
     __syncthreads();
@@ -187,7 +215,6 @@ __global__ void __launch_bounds__(kFeatThreads, 4) k_features(const float *__res
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int v = threadIdx.x; v < tail.V; v += blockDim.x) prep_camera(tail.cams, v, tail.vstride, tail.cam_out, status);
     finalize_features(partials, gridDim.x, n, tail.p, tail.cell_bits, tail.consts, tail.stats);
 }
 
@@ -202,7 +229,7 @@ int feature_blocks(int64_t n)
 }
 
 cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n,
-                            float eta, const float luma[3], PrimRec *recs, double *partials, int *status,
+                            float eta, const float luma[3], PrimRec *recs, float2 *partials, int *status,
                             const FeatureTail &tail, cudaStream_t s)
 {
     const int nb = feature_blocks(n);
@@ -507,7 +534,9 @@ __device__ __forceinline__ int classify(const CamRec &c, const TileBox &t)
     // outside an edge by more than the footprint bound (times z^2)
     const Range TX = form_range(c.tx, t), TY = form_range(c.ty, t);
     const float tx2 = fmaxf(TX.lo * TX.lo, TX.hi * TX.hi), ty2 = fmaxf(TY.lo * TY.lo, TY.hi * TY.hi);
-    const float zz = z.hi * z.hi;
+    // per pair the bound reads (d z)^2 > b2 (fx^2 z^2 + tx^2), i.e. d^2 > b2 (fx^2 + (tx / z)^2): over
+    // the box d >= d_lo and z >= z_lo > 0, so (d_lo z_lo)^2 > b2 (fx^2 z_lo^2 + max tx^2) suffices
+    const float zz = z.lo * z.lo;
     const float bx = t.b2 * fmaf(c.k.x, zz, tx2) * 1.00390625f;  // (1 + 2^-8)
     const float by = t.b2 * fmaf(c.k.y, zz, ty2) * 1.00390625f;
     const float dl = fmaxf(-U.hi, UW.lo) * z.lo;  // > 0 when the box is left or right of the image

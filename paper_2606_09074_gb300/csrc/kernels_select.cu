@@ -86,6 +86,9 @@ __global__ void __launch_bounds__(kSelThreads) k_select_pass(const float *__rest
         bad |= valid && isnan(f);
         const uint32_t k = score_key(f);
         const bool match = valid && (PASS == 0 ? true : ((k >> (SHIFT + WIDTH)) == prefix));
+        // after the first pass few keys still match the digits decided so
+        // far: a warp with none skips the grouping
+        if (PASS > 0 && !__any_sync(0xffffffffu, match)) return;
         const unsigned int d = (k >> SHIFT) & (NB - 1);
         const unsigned int grp = __match_any_sync(0xffffffffu, match ? d : 0xffffffffu);
         if (match && (__ffs(grp) - 1) == (int)(threadIdx.x & 31)) atomicAdd(&h[d], __popc(grp));
