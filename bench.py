@@ -68,6 +68,35 @@ def workload(name: str, rank: int = 0, storage: str = "f32"):
     return w
 
 
+def cell_bits_for(n: int) -> int:
+    """Resolution of the processing-order grid the library picks for n
+    primitives (2^(3b) Morton cells, b in 4..7, about 0.5 or more per cell)."""
+    b = 4
+    while b < 7 and (1 << (3 * (b + 1))) <= 2 * n:
+        b += 1
+    return b
+
+
+def stream_bytes(n: int, n_keep: int, storage: str) -> dict:
+    """Algorithmic DRAM bytes of one plain step, per kernel class: what each
+    kernel must read and write at least once (row bytes by storage type;
+    the processing-order keys are cells and size classes, 2 x 8^b)."""
+    es = 4 if storage == "f32" else 2
+    row = 12 + 56 * es                       # pos (FP32) + 56 attribute rows
+    keys = 2 * (1 << (3 * cell_bits_for(n)))
+    return {
+        "features": n * row + 64 * n,        # all rows in, one 64-B record out
+        "cells": n * (12 + 3 * es) + 8 * n,  # pos and log-scales in, (cell, slot) out
+        "cell_scan": 8 * keys,               # counts in, offsets out
+        "cell_scatter": 16 * n,              # (cell, slot) and the cell's offset in, order out
+        "score": 72 * n,                     # record and order entry in, score out
+        "select_pass": 12 * n,               # three passes over the scores
+        "select_mask": 4 * n + n // 8,       # scores in, keep bits out
+        "compact_count": n // 8,             # keep bits in
+        "compact_scatter": n * row + n_keep * (row + 4),  # all rows in, kept rows and indices out
+    }
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -478,6 +507,29 @@ def run_ours(args, rank: int, world: int):
                 "kernels_ms_per_step": {k: v["ms"] / b_steps for k, v in kt_all.items()},
                 "kernels_ms_per_step_basis": f"every kernel bracketed by CUDA events, {b_steps} steps after the "
                                              f"timed region"}
+    # the measured FP32 FMA rate of this device (refine_fma_rate), beside
+    # the nominal peak above
+    fma_rate, fma_ms = ctx.fma_rate(stream=stream)
+    roofline["peak_measured"] = fma_rate / 1e12
+    roofline["frac_of_measured"] = achieved / (fma_rate / 1e12)
+    roofline["peak_measured_basis"] = (f"refine_fma_rate: 8 CTAs x 256 threads per SM, 8 independent FP32 FMA "
+                                       f"chains per thread, one launch of {fma_ms:.2f} ms timed with CUDA events "
+                                       f"after the timed region")
+    # every kernel against the measured HBM copy peak, by its algorithmic bytes
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    kb = stream_bytes(n, n_keep, w.scene.dtype)
+    per_kernel = {}
+    for k, v in kt_all.items():
+        ms_k = v["ms"] / b_steps
+        entry = {"ms": ms_k}
+        if k in kb and ms_k > 0:
+            gbs = kb[k] / (ms_k * 1e-3) / 1e9
+            entry.update({"bytes": kb[k], "gbs": gbs, "frac_hbm": gbs / hbm})
+        per_kernel[k] = entry
+    roofline["kernels"] = per_kernel
+    roofline["kernels_basis"] = (f"algorithmic bytes per step (each input byte read once, each output byte "
+                                 f"written once) / the kernel's event-bracketed time, against the measured "
+                                 f"{hbm:.0f} GB/s copy peak of MEASURED_PEAKS.json")
     if prof:
         roofline["ncu"] = {k: prof[k] for k in ("fp32_flops_executed", "fp32_executed_frac", "fma_pipe_pct",
                                                 "issue_active_pct", "thread_inst_per_pair", "source")

@@ -547,6 +547,21 @@ int64_t refine_ctx_launch_count(const refine_ctx *ctx);
 refine_status refine_selftest_wait(refine_ctx *ctx, uint32_t bytes, uint32_t missing_bytes,
                                    int64_t wait_cycles, refine_stream_t stream);
 
+/* Measured FP32 FMA throughput of the context's device: the denominator
+ * that the score kernel's roofline (an FP32-issue-bound kernel, no dense
+ * contraction) is compared with, beside the nominal SMs x 128 lanes x 2 x
+ * clock.  The paper has no counterpart.  A grid of 8 CTAs of 256 threads per
+ * SM runs `iters` steps of 8 independent FMA chains per thread with no
+ * memory traffic; one launch runs untimed, the next is timed with CUDA
+ * events on `stream`.
+ *   iters        1 .. 2^20 (2^17 takes about 8 ms on a 152-SM part)
+ *   flops_per_s  2 FLOPs per FMA / elapsed seconds, at whatever SM clock the
+ *                device ran (required)
+ *   ms_out       the timed launch's duration, or NULL
+ * Synchronises `stream`.  EINVAL for iters out of range. */
+refine_status refine_fma_rate(refine_ctx *ctx, int32_t iters, double *flops_per_s, double *ms_out,
+                              refine_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -176,6 +176,7 @@ _SIGNATURES = {
                                           C.POINTER(C.c_int64), C.c_int32, C.POINTER(C.c_int32)]),
     "refine_ctx_launch_count": (C.c_int64, [_P]),
     "refine_selftest_wait": (C.c_int, [_P, C.c_uint32, C.c_uint32, C.c_int64, _P]),
+    "refine_fma_rate": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), _P]),
 }
 
 
@@ -399,6 +400,14 @@ class Context:
         never arrive)."""
         return int(refine_selftest_wait(self.handle, nbytes, missing, cycles,  # noqa: F821
                                         _stream_handle(stream, self.device)))
+
+    def fma_rate(self, iters=1 << 17, stream=None):
+        """Measured FP32 FMA throughput of the device (refine_fma_rate):
+        returns (FLOP/s, ms of the timed launch)."""
+        rate, ms = C.c_double(), C.c_double()
+        _check(self.handle, refine_fma_rate(self.handle, int(iters), C.byref(rate), C.byref(ms),  # noqa: F821
+                                            _stream_handle(stream, self.device)))
+        return rate.value, ms.value
 
     def autotune(self, jobs, params=None, reps=3):
         """Times the batched score launch of ``jobs`` (device-tensor dicts as

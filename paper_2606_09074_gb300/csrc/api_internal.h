@@ -34,13 +34,14 @@ enum KClass {
     K_CMP_COUNT,
     K_CMP_SCATTER,
     K_SELFTEST,
+    K_FMA_PROBE,
     K_NCLASS
 };
 const char *const kClassName[K_NCLASS] = {"features",
                                           "cells",         "cell_scan",    "cell_scatter",
                                           "score",         "select_pass",  "select_ties",
                                           "select_mask",   "mask_fill",    "compact_count",
-                                          "compact_scatter", "selftest"};
+                                          "compact_scatter", "selftest",   "fma_probe"};
 
 struct Arena {
     void *p = nullptr;

@@ -158,6 +158,13 @@ cudaError_t launch_cell_scatter(const uint2 *cell, int64_t n,
 cudaError_t launch_score(const ScoreLaunch &a, const ScoreShape &sh, cudaStream_t s);
 int score_grid(int num_sms, int64_t n, int vcount, const ScoreShape &sh);
 
+// FP32 FMA throughput probe (refine_fma_rate): FLOPs of one launch of
+// `iters` steps on `num_sms` SMs, and the launch itself (sink: one float,
+// never written).
+constexpr int kFmaProbeMaxIters = 1 << 20;  // about 65 ms at the nominal FP32 peak
+double fma_probe_flops(int num_sms, int iters);
+cudaError_t launch_fma_probe(int num_sms, int iters, float *sink, cudaStream_t s);
+
 // Self-test of the bounded mbarrier wait (refine_selftest_wait).
 constexpr uint32_t kSelftestMaxBytes = 1024;
 cudaError_t launch_wait_selftest(const void *src, uint32_t bytes, uint32_t missing, long long limit, int *status,

@@ -308,6 +308,42 @@ refine_status refine_selftest_wait(refine_ctx *c, uint32_t bytes, uint32_t missi
     return read_status(c, s);
 }
 
+refine_status refine_fma_rate(refine_ctx *c, int32_t iters, double *flops_per_s, double *ms_out,
+                              refine_stream_t stream)
+{
+    if (!c || !flops_per_s) return REFINE_EINVAL;
+    refine_status st = use_device(c);
+    if (st) return st;
+    if (iters < 1 || iters > kFmaProbeMaxIters)
+        return fail(c, REFINE_EINVAL, "fma_rate: iters %d out of [1, %d]", (int)iters, kFmaProbeMaxIters);
+    if ((st = ensure(c, c->score, 256))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    float *sink = static_cast<float *>(c->score.p);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e != cudaSuccess) {
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+        return cuda_fail(c, e, "cudaEventCreate");
+    }
+    // one untimed launch (clocks ramp, code loaded), then the timed one
+    st = launch(c, K_FMA_PROBE, s, [&] { return launch_fma_probe(c->num_sms, iters, sink, s); });
+    if (!st && (e = cudaEventRecord(ev[0], s)) != cudaSuccess) st = cuda_fail(c, e, "cudaEventRecord");
+    if (!st) st = launch(c, K_FMA_PROBE, s, [&] { return launch_fma_probe(c->num_sms, iters, sink, s); });
+    if (!st && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) st = cuda_fail(c, e, "cudaEventRecord");
+    if (!st && (e = cudaEventSynchronize(ev[1])) != cudaSuccess) st = cuda_fail(c, e, "cudaEventSynchronize");
+    float ms = 0.f;
+    if (!st && (e = cudaEventElapsedTime(&ms, ev[0], ev[1])) != cudaSuccess) st = cuda_fail(c, e, "cudaEventElapsedTime");
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (st) return st;
+    if (!(ms > 0.f)) return fail(c, REFINE_ECUDA, "fma_rate: no elapsed time");
+    *flops_per_s = fma_probe_flops(c->num_sms, iters) / (ms * 1e-3);
+    if (ms_out) *ms_out = ms;
+    return REFINE_OK;
+}
+
 }  // extern "C"
 
 // ==================================================================== batch
