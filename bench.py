@@ -690,6 +690,7 @@ def run_batch_mode(args):
         s = ctx.score(x["pos"], x["a16"], x["cams"])
         same &= bool(torch.equal(s, batch.outputs[k]["scores"]))
     ctx.check()
+    acc = batch_accuracy(batch, seeds, scenes) if args.accuracy else None
     line = {"mode": "batch", "metric": "scenes/s", "value": res["batched_bf16"]["scenes_per_s"],
             "unit": "scenes/s", "n_gpus": 1, "steps": args.batch_steps, "warmup": args.warmup,
             "scenes": len(scenes), "pairs_per_batch": pairs, "primitives": sum(x["n"] for x in scenes),
@@ -698,9 +699,42 @@ def run_batch_mode(args):
             "batched_scores_equal_plain": same, "results": res, "data": "synthetic",
             "autotune": {"best": best, "candidates": table},
             "config": {"workload": "64 scenes, seeds 100-163, N log-uniform 50k-2M, V 50-300, ratio 0.66"}}
+    if acc is not None:
+        line["accuracy"] = acc
     print(json.dumps(line), flush=True)
     batch.close()
     ctx.close()
+
+
+def batch_accuracy(batch, seeds, scenes):
+    """The batched BF16 scores and keep masks of every scene against the FP64
+    oracle on the float32 scene each was rounded from (every primitive, all
+    views): keep-mask agreement per scene and relative score error over the
+    primitives whose oracle score is positive and has no borderline pair."""
+    import oracle
+    from paper_2606_09074_gb300 import synth
+    oracle.set_threads(os.cpu_count() or 1)
+    agree, rel_mean, rel_p99 = [], [], []
+    t0 = time.perf_counter()
+    for k, sd in enumerate(seeds):
+        w = synth.batch_scene(sd, dtype="f32")
+        ref = oracle.score(w.scene.params_f64(), w.cams)
+        m_ref, _, _ = oracle.select(ref["scores"], scenes[k]["ratio"])
+        n = w.scene.n
+        want = np.unpackbits(m_ref.view(np.uint8), bitorder="little")[:n].astype(bool)
+        out = batch.outputs[k]
+        got = np.unpackbits(out["mask"].cpu().numpy().view(np.uint8), bitorder="little")[:n].astype(bool)
+        agree.append(float((got == want).mean()))
+        s = out["scores"].cpu().numpy().astype(np.float64)
+        clean = (ref["nborder"] == 0) & (ref["scores"] > 0)
+        r = np.abs(s[clean] - ref["scores"][clean]) / ref["scores"][clean]
+        rel_mean.append(float(r.mean()))
+        rel_p99.append(float(np.quantile(r, 0.99)))
+    return {"reference": "FP64 oracle on the float32 scenes, every primitive, all views",
+            "mask_agreement": {"min": min(agree), "mean": statistics.mean(agree),
+                               "below_99.9": sum(a < 0.999 for a in agree), "per_scene": agree},
+            "rel_error": {"mean_of_means": statistics.mean(rel_mean), "max_p99": max(rel_p99)},
+            "oracle_s": time.perf_counter() - t0}
 
 
 def _percentile(xs, q):
