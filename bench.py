@@ -81,8 +81,9 @@ def stream_bytes(n: int, n_keep: int, storage: str) -> dict:
     """Algorithmic DRAM bytes of one plain step, per kernel class: what each
     kernel must read and write at least once (row bytes by storage type;
     the processing-order keys are cells and size classes, 2 x 8^b)."""
-    es = 4 if storage == "f32" else 2
-    row = 12 + 56 * es                       # pos (FP32) + 56 attribute rows
+    col = {"f32": 224, "bf16": 112, "bf16s": 118}[storage]  # the 56 attribute rows
+    es = 2 if storage == "bf16" else 4       # bytes of a log-scale element
+    row = 12 + col                           # pos (FP32) + 56 attribute rows
     keys = 2 * (1 << (3 * cell_bits_for(n)))
     return {
         "features": n * row + 64 * n,        # all rows in, one 64-B record out
@@ -314,13 +315,13 @@ def end_to_end(args, torch, rb, ctx, w, attr, params, ratio, n_keep, pairs, V_al
     n = w.scene.n
     pos_h = torch.from_numpy(w.scene.pos).pin_memory()
     attr_h = attr.cpu().pin_memory()
-    asz = attr.element_size() * 56
+    asz = rb.attr_col_bytes(attr)
     h2d = 12 * n + asz * n + 80 * V_all
     d2h = (12 + asz + 4) * n_keep + 4 + 4
 
     def outset():
         return {"out_pos": torch.empty((3, n_keep), dtype=torch.float32, pin_memory=True),
-                "out_attr": torch.empty((56, n_keep), dtype=attr.dtype, pin_memory=True),
+                "out_attr": rb.empty_attr_like(attr, n_keep, pin_memory=True),
                 "idx": torch.empty(n_keep, dtype=torch.int32, pin_memory=True)}
 
     k_e2e = max(3, min(args.steps, 60))
@@ -343,7 +344,8 @@ def end_to_end(args, torch, rb, ctx, w, attr, params, ratio, n_keep, pairs, V_al
 
         def host_rows(o):
             a = o["out_attr"]
-            a = a.view(torch.int16).numpy().view(np.uint16) if a.dtype == torch.bfloat16 else a.numpy()
+            if not isinstance(a, rb.MixedRows):
+                a = a.view(torch.int16).numpy().view(np.uint16) if a.dtype == torch.bfloat16 else a.numpy()
             return o["out_pos"].numpy(), a
         k_ply = max(2, min(args.steps, 5))
         try:
@@ -365,7 +367,7 @@ def end_to_end(args, torch, rb, ctx, w, attr, params, ratio, n_keep, pairs, V_al
     D = args.e2e_inflight
     if D < 2:
         return {**sequential, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-    dt_code = rb.REFINE_BF16 if attr.dtype == torch.bfloat16 else rb.REFINE_F32
+    dt_code = rb._dtype_code(attr)
     fp = rb.Queue.footprint(n, dt_code, len(w.cams), ratio)
     q = rb.Queue(ctx, budget_bytes=(D + 1) * fp, max_slots=D, params=params)
     sets = [outset() for _ in range(D + 1)]
@@ -410,7 +412,9 @@ def run_ours(args, rank: int, world: int):
     w = workload(args.workload, rank, args.storage)
     n, V, ratio = w.scene.n, len(w.cams), w.ratios[0]
     pos = torch.from_numpy(w.scene.pos).to(dev)
-    if w.scene.dtype == "bf16":
+    if w.scene.dtype == "bf16s":
+        attr = rb.MixedRows.from_float(w.scene.attr, device=dev)
+    elif w.scene.dtype == "bf16":
         attr = torch.from_numpy(w.scene.attr.view(np.int16)).to(dev).view(torch.bfloat16)
     else:
         attr = torch.from_numpy(w.scene.attr).to(dev)
@@ -419,7 +423,7 @@ def run_ours(args, rank: int, world: int):
     scores = torch.empty(n, dtype=torch.float32, device=dev)
     mask = torch.empty((n + 31) // 32, dtype=torch.int32, device=dev)
     out_pos = torch.empty((3, n_keep), dtype=torch.float32, device=dev)
-    out_attr = torch.empty((56, n_keep), dtype=attr.dtype, device=dev)
+    out_attr = rb.empty_attr_like(attr, n_keep, device=dev)
     kept = torch.empty(n_keep, dtype=torch.int32, device=dev)
     ctx = rb.Context(local)
     stream = torch.cuda.current_stream(dev)
@@ -554,9 +558,9 @@ def run_ours(args, rank: int, world: int):
         lat = sorted(per_step)
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if w.scene.dtype == "f32" else "f32 (bf16 storage)", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32" if w.scene.dtype == "f32" else f"f32 ({w.scene.dtype} storage)", "data": "synthetic",
                 "config": {"workload": w.name, "n": n, "views": V, "ratio": ratio, "storage": w.scene.dtype,
-                           "l2": f"inputs larger than L2 ({(236 * n) / 1e6:.0f} MB scene), no flush",
+                           "l2": f"inputs larger than L2 ({stream_bytes(n, 0, w.scene.dtype)['compact_scatter'] / 1e6:.0f} MB scene), no flush",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "scenes_per_s": world * 1000.0 / ms_step,
                 "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
@@ -604,7 +608,7 @@ def accuracy_report(ctx, w, pos, attr, cams, ratio, stream):
 
     rep["vs_oracle_same_inputs"] = rel(oracle.score_subset(w.scene.params_f64(), idx, w.cams))
     src = w.scene
-    if w.scene.dtype == "bf16":
+    if w.scene.dtype in ("bf16", "bf16s"):
         src = synth.config2(seed=2, dtype="f32").scene
         rep["vs_oracle_fp32_source"] = rel(oracle.score_subset(src.params_f64(), idx, w.cams))
     ref = oracle.score(src.params_f64(), w.cams, detail=False)
@@ -631,14 +635,18 @@ def run_batch_mode(args):
         pos = torch.from_numpy(w.scene.pos).to(dev)
         a32 = torch.from_numpy(w.scene.attr).to(dev)
         a16 = torch.from_numpy(synth.f32_to_bf16_bits(w.scene.attr).view(np.int16)).to(dev).view(torch.bfloat16)
-        scenes.append({"pos": pos, "a32": a32, "a16": a16, "cams": rb.cameras_to_device(w.cams, dev),
-                       "n": w.scene.n, "V": len(w.cams), "ratio": 0.66})
+        x = {"pos": pos, "a32": a32, "a16": a16, "cams": rb.cameras_to_device(w.cams, dev),
+             "n": w.scene.n, "V": len(w.cams), "ratio": 0.66}
+        if args.form_storage == "bf16s":
+            x["amx"] = rb.MixedRows.from_float(w.scene.attr, device=dev)
+        scenes.append(x)
+    fkey = "amx" if args.form_storage == "bf16s" else "a16"  # attribute rows of the batched form
     pairs = sum(x["n"] * x["V"] for x in scenes)
     ctx = rb.Context(0)
     stream = torch.cuda.current_stream(dev)
     # tile and CTA shape of the score kernels from the autotuner (results do
     # not depend on it); every path below runs with the tuned shape
-    best, table = ctx.autotune([{"pos": x["pos"], "attr": x["a16"], "cams": x["cams"], "ratio": x["ratio"]}
+    best, table = ctx.autotune([{"pos": x["pos"], "attr": x[fkey], "cams": x["cams"], "ratio": x["ratio"]}
                                 for x in scenes], reps=3)
 
     def plain(key):
@@ -648,7 +656,7 @@ def run_batch_mode(args):
             outs.append({"scores": torch.empty(x["n"], device=dev),
                          "mask": torch.empty((x["n"] + 31) // 32, dtype=torch.int32, device=dev),
                          "op": torch.empty((3, nk), device=dev),
-                         "oa": torch.empty((56, nk), dtype=x[key].dtype, device=dev), "nk": nk})
+                         "oa": rb.empty_attr_like(x[key], nk, device=dev), "nk": nk})
 
         def step():
             for x, o in zip(scenes, outs):
@@ -672,30 +680,33 @@ def run_batch_mode(args):
         return e0.elapsed_time(e1) / k, (time.perf_counter() - t0) * 1000 / k
 
     res = {}
-    for key, name in (("a32", "plain_f32"), ("a16", "plain_bf16")):
+    plains = (("a32", "plain_f32"), ("a16", "plain_bf16")) + ((("amx", "plain_bf16s"),) if fkey == "amx" else ())
+    for key, name in plains:
         dev_ms, wall_ms = timed(plain(key), args.batch_steps)
         res[name] = {"ms_per_batch": dev_ms, "wall_ms_per_batch": wall_ms,
                      "scenes_per_s": len(scenes) * 1000 / wall_ms, "pairs_per_s": pairs * 1000 / wall_ms}
-    batch = rb.Batch(ctx, [{"pos": x["pos"], "attr": x["a16"], "cams": x["cams"], "ratio": x["ratio"]}
+    batch = rb.Batch(ctx, [{"pos": x["pos"], "attr": x[fkey], "cams": x["cams"], "ratio": x["ratio"]}
                            for x in scenes])
     dev_ms, wall_ms = timed(lambda: batch.run(stream), args.batch_steps)
-    res["batched_bf16"] = {"ms_per_batch": dev_ms, "wall_ms_per_batch": wall_ms,
+    bname = f"batched_{args.form_storage}"
+    res[bname] = {"ms_per_batch": dev_ms, "wall_ms_per_batch": wall_ms,
                            "scenes_per_s": len(scenes) * 1000 / wall_ms, "pairs_per_s": pairs * 1000 / wall_ms,
                            "kernels_per_run": batch.launches()}
     # the batched scores equal the per-scene BF16 path bit for bit
-    plain(key="a16")  # allocate nothing new; check a few scenes directly
+    plain(key=fkey)  # allocate nothing new; check a few scenes directly
     same = True
     for k in (0, len(scenes) // 2, len(scenes) - 1):
         x = scenes[k]
-        s = ctx.score(x["pos"], x["a16"], x["cams"])
+        s = ctx.score(x["pos"], x[fkey], x["cams"])
         same &= bool(torch.equal(s, batch.outputs[k]["scores"]))
     ctx.check()
     acc = batch_accuracy(batch, seeds, scenes) if args.accuracy else None
-    line = {"mode": "batch", "metric": "scenes/s", "value": res["batched_bf16"]["scenes_per_s"],
+    line = {"mode": "batch", "metric": "scenes/s", "value": res[bname]["scenes_per_s"],
             "unit": "scenes/s", "n_gpus": 1, "steps": args.batch_steps, "warmup": args.warmup,
             "scenes": len(scenes), "pairs_per_batch": pairs, "primitives": sum(x["n"] for x in scenes),
-            "speedup_vs_plain_f32": res["plain_f32"]["wall_ms_per_batch"] / res["batched_bf16"]["wall_ms_per_batch"],
-            "speedup_vs_plain_bf16": res["plain_bf16"]["wall_ms_per_batch"] / res["batched_bf16"]["wall_ms_per_batch"],
+            "storage": args.form_storage,
+            "speedup_vs_plain_f32": res["plain_f32"]["wall_ms_per_batch"] / res[bname]["wall_ms_per_batch"],
+            "speedup_vs_plain_bf16": res["plain_bf16"]["wall_ms_per_batch"] / res[bname]["wall_ms_per_batch"],
             "batched_scores_equal_plain": same, "results": res, "data": "synthetic",
             "autotune": {"best": best, "candidates": table},
             "config": {"workload": "64 scenes, seeds 100-163, N log-uniform 50k-2M, V 50-300, ratio 0.66"}}
@@ -751,14 +762,14 @@ class _OutputSets:
     each large enough for the largest pool scene at ratio 0.5 (the queue
     writes each output contiguously, so a larger buffer serves any job)."""
 
-    def __init__(self, torch, n_max, count):
+    def __init__(self, torch, n_max, count, col_bytes=112):
         nk = n_max - n_max // 2
         self.free = []
         self.cv = threading.Condition()
         for _ in range(count):
             self.free.append({"mask": torch.empty((n_max + 31) // 32, dtype=torch.int32, pin_memory=True),
                               "out_pos": torch.empty(3 * nk, dtype=torch.float32, pin_memory=True),
-                              "out_attr": torch.empty(56 * nk, dtype=torch.bfloat16, pin_memory=True),
+                              "out_attr": torch.empty(col_bytes * nk, dtype=torch.uint8, pin_memory=True),
                               "idx": torch.empty(nk, dtype=torch.int32, pin_memory=True)})
 
     def take(self):
@@ -794,7 +805,7 @@ def _serve_pass(torch, rb, pool, jobs, arrivals, q, outsets, on_done=None):
             outs = outsets.take()
             sc = pool[p]
             t_sub = time.perf_counter()
-            t = q.submit(sc["pos"], sc["a16"], sc["cams"], r, outputs=outs, mask=True, compact=True)
+            t = q.submit(sc["pos"], sc["attr"], sc["cams"], r, outputs=outs, mask=True, compact=True)
             with lock:
                 sub.append((t, p, r, outs, t_arr, t_sub))
             ready.release()
@@ -863,9 +874,12 @@ def run_serve_mode(args):
     torch.cuda.set_device(dev)
     pool = []
     for pos, attr, cams in raw:
-        a16 = torch.from_numpy(synth.f32_to_bf16_bits(attr).view(np.int16)).view(torch.bfloat16)
+        if args.form_storage == "bf16s":
+            af = rb.MixedRows.from_float(attr, pin_memory=True)  # log-scales float32, the rest bfloat16
+        else:
+            af = torch.from_numpy(synth.f32_to_bf16_bits(attr).view(np.int16)).view(torch.bfloat16).pin_memory()
         pool.append({"pos": torch.from_numpy(pos).pin_memory(), "a32": torch.from_numpy(attr).pin_memory(),
-                     "a16": a16.pin_memory(), "cams": cams, "n": pos.shape[1], "V": len(cams)})
+                     "attr": af, "cams": cams, "n": pos.shape[1], "V": len(cams)})
     del raw
     ratio_of = lambda k: synth.job_spec(1000 + k)[3]  # noqa: E731
     jobs = [(k % P, ratio_of(k)) for k in range(args.jobs)]
@@ -903,7 +917,7 @@ def run_serve_mode(args):
     plain_sat = len(sat_jobs) / plain_wall
     del plain_out
 
-    outsets = _OutputSets(torch, n_max, args.slots + 4)
+    outsets = _OutputSets(torch, n_max, args.slots + 4, 118 if args.form_storage == "bf16s" else 112)
     budget = int(args.budget_gb * (1 << 30))
     small_budget = int(args.small_budget_gb * (1 << 30))
 
@@ -971,7 +985,7 @@ def run_serve_mode(args):
                 "slots": st_["slots"], "dispatch_ms_per_job": st_["dispatch_ms"] / max(n_jobs, 1)}
 
     line = {"mode": "serve", "metric": "scenes/s", "value": served_sat, "unit": "scenes/s", "n_gpus": 1,
-            "higher_is_better": True, "dtype": "f32 (bf16 storage)", "data": "synthetic",
+            "higher_is_better": True, "dtype": f"f32 ({args.form_storage} storage)", "data": "synthetic",
             "poisson": {**side(lat, rounds, wall, st, len(jobs)), "rate_per_s": args.rate,
                         "plain_f32_p50_ms": _percentile(plain_lat, 0.5),
                         "plain_f32_p99_ms": _percentile(plain_lat, 0.99), "plain_f32_wall_s": plain_wall_p},
@@ -995,7 +1009,7 @@ def run_serve_mode(args):
             "config": {"workload": f"serving: {args.jobs} jobs, Poisson arrivals at {args.rate}/s (seed 999), then "
                                    f"{args.sat_jobs} back to back; job k scores pool scene k mod {P} (seeds "
                                    f"1000-{999 + P}, N log-uniform 50k-3.5M, V 50-300) with the ratio its seed "
-                                   f"draws; BF16 storage; HBM budget {args.budget_gb} GB (and "
+                                   f"draws; {args.form_storage.upper()} storage; HBM budget {args.budget_gb} GB (and "
                                    f"{args.small_budget_gb} GB)",
                        "plain_path": "refine_prune_host, FP32, one FIFO server thread fed the same arrivals "
                                      "from page-locked host memory"}}
@@ -1015,7 +1029,11 @@ def main(argv=None):
     ap.add_argument("--e2e-inflight", type=int, default=3,
                     help="requests in flight in the end-to-end measurement (1: sequential calls only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--storage", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--form-storage", default="bf16", choices=["bf16", "bf16s"],
+                    help="batch / serve: attribute rows of the batched and served forms (bfloat16, or bfloat16 "
+                         "with float32 log-scales)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "bf16s"],
+                    help="attribute rows: float32, bfloat16, or bfloat16 with float32 log-scales")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"],
                     help="single: the default workload; batch: 64 scenes, batched vs per-scene; "
                          "serve: the request queue under Poisson and back-to-back arrivals")

@@ -49,8 +49,18 @@ typedef enum refine_status {
     REFINE_ENOTFOUND = 8
 } refine_status;
 
-/* Storage type of primitive rows 3..58 (positions are always float32). */
-enum { REFINE_F32 = 0, REFINE_BF16 = 1 };
+/* Storage type of primitive rows 3..58 (positions are always float32).
+ *   REFINE_F32    all 56 attribute rows float32 (224 B per primitive)
+ *   REFINE_BF16   all 56 attribute rows bfloat16 (112 B)
+ *   REFINE_BF16S  the 3 log-scale rows float32, the other 53 rows bfloat16
+ *                 (12 + 106 = 118 B): the rows are laid out as 3 float32
+ *                 rows of row_stride elements followed, at byte offset
+ *                 12 * row_stride, by 53 bfloat16 rows of row_stride
+ *                 elements.  The bfloat16 rounding of the log-scales is what
+ *                 moves the keep mask of the BF16 form most (its error grows
+ *                 with |ln s| and m_gem carries two scales); this form keeps
+ *                 them exact for 6 more bytes per primitive. */
+enum { REFINE_F32 = 0, REFINE_BF16 = 1, REFINE_BF16S = 2 };
 
 /* refine_params.flags */
 #define REFINE_FLAG_NO_VIS       (1 << 0) /* Table 3 "w/o V": alpha -> 1 in Eq. 20          */
@@ -87,14 +97,15 @@ typedef struct refine_camera {
 /* A scene of n primitives in structure-of-arrays form (Eq. 1: mean, scale,
  * rotation, SH colour, opacity -- 59 parameters per primitive).
  *   pos   device, float32 [3][row_stride]: rows 0-2, mean x, y, z
- *   attr  device, [56][row_stride] in `dtype` (float32 or bfloat16):
+ *   attr  device, [56][row_stride] in `dtype` (float32, bfloat16, or the
+ *           mixed layout of REFINE_BF16S):
  *           row 0-2   log-scale
  *           row 3-6   rotation quaternion (w, x, y, z), need not be unit
  *           row 7     opacity logit
  *           row 8-10  SH DC (r, g, b)
  *           row 11-55 SH degree 1-3, 15 coefficients x 3 channels
- *   row_stride  elements between consecutive rows, >= n (for BF16 the
- *           stride counts bfloat16 elements of attr and float32 of pos).
+ *   row_stride  elements between consecutive rows, >= n (the stride counts
+ *           elements of each row's own type).
  * pos and attr must be 16-byte aligned. */
 typedef struct refine_scene {
     int64_t n;

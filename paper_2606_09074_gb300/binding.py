@@ -36,6 +36,7 @@ REFINE_F32 = 0
 TIMING_ALL = 1    # REFINE_TIMING_ALL
 TIMING_SCORE = 2  # REFINE_TIMING_SCORE
 REFINE_BF16 = 1
+REFINE_BF16S = 2  # log-scale rows float32, the other 53 rows bfloat16
 
 FLAG_NO_VIS = 1 << 0
 FLAG_NO_PROJ = 1 << 1
@@ -226,8 +227,108 @@ def _stream_handle(stream, device):
     return C.c_void_p(stream.cuda_stream)
 
 
+class MixedRows:
+    """The 56 attribute rows of a scene in the REFINE_BF16S layout, in one
+    byte buffer: the 3 log-scale rows float32 ([3, stride]), then the other 53
+    rows bfloat16 ([53, stride]).  It stands where the float32 or bfloat16
+    [56, n] tensor stands elsewhere in this binding: ``shape``, ``stride``,
+    ``data_ptr``, ``[:, :k]`` column views, ``to``/``cpu``, ``is_pinned``."""
+
+    dtype = "bf16s"
+    NF = 3
+
+    def __init__(self, buf, n: int, stride: int):
+        self.buf, self.n, self.row_stride = buf, int(n), int(stride)
+
+    @classmethod
+    def empty(cls, n: int, stride: int | None = None, device=None, pin_memory: bool = False):
+        import torch
+        stride = max(int(n), 1) if stride is None else int(stride)
+        buf = torch.empty(stride * (4 * cls.NF + 2 * (56 - cls.NF)), dtype=torch.uint8, device=device,
+                          pin_memory=pin_memory)
+        return cls(buf, n, stride)
+
+    @classmethod
+    def from_float(cls, attr, device=None, pin_memory: bool = False):
+        """Rows of a float32 [56, n] array or tensor, the last 53 rounded to
+        bfloat16 (round to nearest even)."""
+        import torch
+        a = torch.as_tensor(attr, dtype=torch.float32)
+        out = cls.empty(a.shape[1], device=device, pin_memory=pin_memory)
+        out.f32_rows()[:, : out.n].copy_(a[: cls.NF])
+        out.bf16_rows()[:, : out.n].copy_(a[cls.NF:].to(torch.bfloat16))
+        return out
+
+    def f32_rows(self):
+        import torch
+        return self.buf[: 4 * self.NF * self.row_stride].view(torch.float32).view(self.NF, self.row_stride)
+
+    def bf16_rows(self):
+        import torch
+        o = 4 * self.NF * self.row_stride
+        return self.buf[o: o + 2 * (56 - self.NF) * self.row_stride].view(torch.bfloat16).view(
+            56 - self.NF, self.row_stride)
+
+    def float(self):
+        """The rows widened to a float32 [56, n] tensor (exact)."""
+        import torch
+        return torch.cat([self.f32_rows()[:, : self.n], self.bf16_rows()[:, : self.n].float()], 0)
+
+    @property
+    def shape(self):
+        return (56, self.n)
+
+    @property
+    def device(self):
+        return self.buf.device
+
+    def stride(self, dim: int) -> int:
+        return self.row_stride if dim == 0 else 1
+
+    def data_ptr(self) -> int:
+        return self.buf.data_ptr()
+
+    def is_pinned(self) -> bool:
+        return self.buf.is_pinned()
+
+    def to(self, device, non_blocking: bool = False):
+        return MixedRows(self.buf.to(device, non_blocking=non_blocking), self.n, self.row_stride)
+
+    def cpu(self):
+        return self.to("cpu")
+
+    def pin_memory(self):
+        return MixedRows(self.buf.pin_memory(), self.n, self.row_stride)
+
+    col_bytes = 4 * NF + 2 * (56 - NF)  # bytes of the 56 rows per element of the stride
+
+    def __getitem__(self, key):
+        rows, cols = key
+        if rows != slice(None) or not isinstance(cols, slice) or cols.start not in (None, 0) or cols.step not in (None, 1):
+            raise IndexError("MixedRows supports [:, :k] column views only")
+        k = self.n if cols.stop is None else min(int(cols.stop), self.n)
+        return MixedRows(self.buf, k, self.row_stride)
+
+
+def empty_attr_like(attr, cols: int, device=None, pin_memory: bool = False):
+    """An uninitialised [56, cols] attribute block of the same storage type
+    as ``attr`` (a float32 or bfloat16 tensor, or MixedRows)."""
+    import torch
+    if isinstance(attr, MixedRows):
+        return MixedRows.empty(cols, device=device, pin_memory=pin_memory)
+    return torch.empty((56, cols), dtype=attr.dtype, device=device, pin_memory=pin_memory)
+
+
+def attr_col_bytes(attr) -> int:
+    """Bytes of the 56 attribute rows per primitive: 224 (float32), 112
+    (bfloat16) or 118 (MixedRows)."""
+    return MixedRows.col_bytes if isinstance(attr, MixedRows) else 56 * attr.element_size()
+
+
 def _dtype_code(t) -> int:
     import torch
+    if isinstance(t, MixedRows):
+        return REFINE_BF16S
     if t.dtype == torch.float32:
         return REFINE_F32
     if t.dtype in (torch.bfloat16, torch.int16, torch.uint16):
@@ -325,7 +426,7 @@ class Context:
         if out_pos is None:
             out_pos = torch.empty((3, stride), dtype=torch.float32, device=self.device)
         if out_attr is None:
-            out_attr = torch.empty((56, stride), dtype=attr.dtype, device=self.device)
+            out_attr = empty_attr_like(attr, stride, device=self.device)
         idx = torch.empty(max(n_keep, 1), dtype=torch.int32, device=self.device) if kept_idx else None
         cnt = C.c_int64()
         rc = refine_compact(self.handle, C.byref(sc), C.c_void_p(mask.data_ptr()),  # noqa: F821
@@ -348,7 +449,7 @@ class Context:
         if out is None:
             pin = pos_host.is_pinned()
             out = {"out_pos": torch.empty((3, max(n_keep, 1)), dtype=torch.float32, pin_memory=pin),
-                   "out_attr": torch.empty((56, max(n_keep, 1)), dtype=attr_host.dtype, pin_memory=pin),
+                   "out_attr": empty_attr_like(attr_host, max(n_keep, 1), pin_memory=pin),
                    "idx": torch.empty(max(n_keep, 1), dtype=torch.int32, pin_memory=pin)}
             if want_scores:
                 out["scores"] = torch.empty(max(n, 1), dtype=torch.float32, pin_memory=pin)
@@ -455,7 +556,7 @@ def _make_jobs(ctx, jobs, compact=True):
         j.keep_mask_dev = out["mask"].data_ptr()
         if compact and jd.get("compact", True):
             out["out_pos"] = torch.empty((3, max(n_keep, 1)), dtype=torch.float32, device=ctx.device)
-            out["out_attr"] = torch.empty((56, max(n_keep, 1)), dtype=attr.dtype, device=ctx.device)
+            out["out_attr"] = empty_attr_like(attr, max(n_keep, 1), device=ctx.device)
             out["idx"] = torch.empty(max(n_keep, 1), dtype=torch.int32, device=ctx.device)
             j.out_pos_dev = out["out_pos"].data_ptr()
             j.out_attr_dev = out["out_attr"].data_ptr()
@@ -521,12 +622,18 @@ def _host_ptr(a) -> int:
         if not a.flags["C_CONTIGUOUS"]:
             raise ValueError("host arrays must be C-contiguous")
         return a.ctypes.data
+    if isinstance(a, MixedRows):
+        if a.buf.is_cuda or a.row_stride != max(a.n, 1):
+            raise ValueError("host MixedRows must be CPU rows with row stride n")
+        return a.data_ptr()
     if a.is_cuda or not a.is_contiguous():
         raise ValueError("host tensors must be contiguous CPU tensors")
     return a.data_ptr()
 
 
 def _host_dtype_code(a) -> int:
+    if isinstance(a, MixedRows):
+        return REFINE_BF16S
     if isinstance(a, np.ndarray):
         if a.dtype == np.float32:
             return REFINE_F32
@@ -583,8 +690,12 @@ class Queue:
             alloc("scores", (n,), np.float32, torch.float32)
         if compact:
             alloc("out_pos", (3, n_keep), np.float32, torch.float32)
-            alloc("out_attr", (56, n_keep), np.float32 if dt == REFINE_F32 else np.uint16,
-                  torch.float32 if dt == REFINE_F32 else torch.bfloat16)
+            if dt == REFINE_BF16S:
+                if "out_attr" not in out:
+                    out["out_attr"] = MixedRows.empty(n_keep, pin_memory=pin)
+            else:
+                alloc("out_attr", (56, n_keep), np.float32 if dt == REFINE_F32 else np.uint16,
+                      torch.float32 if dt == REFINE_F32 else torch.bfloat16)
             alloc("idx", (n_keep,), np.int32, torch.int32)
         r = refine_request()
         r.n = n
@@ -656,8 +767,17 @@ class Queue:
 
 def write_ply(path: str, pos, attr) -> None:
     """Writes host rows pos [3, n] float32 and attr [56, n] (float32 or
-    bfloat16 bits as uint16) as a 3DGS scene PLY (refine_write_ply)."""
+    bfloat16 bits as uint16, or host MixedRows) as a 3DGS scene PLY
+    (refine_write_ply)."""
     pos = np.ascontiguousarray(pos, dtype=np.float32)
+    if isinstance(attr, MixedRows):
+        if attr.buf.is_cuda:
+            raise ValueError("write_ply takes host rows")
+        rc = refine_write_ply(os.fsencode(path), attr.n, REFINE_BF16S, pos.ctypes.data,  # noqa: F821
+                              attr.data_ptr(), attr.row_stride)
+        if rc != REFINE_OK:
+            raise RefineError(rc, f"refine_write_ply: cannot write {path}")
+        return
     attr = np.ascontiguousarray(attr)
     dt = REFINE_F32 if attr.dtype == np.float32 else REFINE_BF16
     if dt == REFINE_BF16 and attr.dtype not in (np.uint16, np.int16):

@@ -200,7 +200,7 @@ inline refine_status check_scene(refine_ctx *c, const refine_scene *s)
 {
     if (!s) return fail(c, REFINE_EINVAL, "scene is NULL");
     if (s->n < 0 || s->n > INT32_MAX) return fail(c, REFINE_EINVAL, "scene: n=%lld out of [0, 2^31-1]", (long long)s->n);
-    if (s->dtype != REFINE_F32 && s->dtype != REFINE_BF16) return fail(c, REFINE_EINVAL, "scene: unknown dtype %d", s->dtype);
+    if (!valid_dtype(s->dtype)) return fail(c, REFINE_EINVAL, "scene: unknown dtype %d", s->dtype);
     if (s->n == 0) return REFINE_OK;
     if (!s->pos || !s->attr) return fail(c, REFINE_EINVAL, "scene: NULL pos/attr");
     if (s->row_stride < s->n) return fail(c, REFINE_EINVAL, "scene: row_stride < n");

@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "refine.h"
+
 namespace refine {
 
 // Device status codes; the values match refine_status in include/refine.h.
@@ -147,12 +149,55 @@ __device__ __forceinline__ void primitive_record(FeatSums &acc, float mx, float 
     rd = make_float4(s2 * (1.f - 2.f * (qx * qx + qy * qy)), alpha, mg, mc);
 }
 
+// ------------------------------------------------------ row layouts
+// The 56 attribute rows of a storage type: rows [0, attr_f32_rows) are
+// float32, the rest bfloat16, one block of rows after the other, each row
+// `stride` elements of its own type (REFINE_F32: all 56 rows float32;
+// REFINE_BF16: all bfloat16; REFINE_BF16S: the 3 log-scale rows float32).
+__host__ __device__ constexpr int attr_f32_rows(int dtype)
+{
+    return dtype == REFINE_F32 ? 56 : (dtype == REFINE_BF16S ? 3 : 0);
+}
+__host__ __device__ constexpr bool valid_dtype(int dtype)
+{
+    return dtype == REFINE_F32 || dtype == REFINE_BF16 || dtype == REFINE_BF16S;
+}
+// Bytes of one element column of the 56 rows (236 - 12 = 224, 112 or 118).
+__host__ __device__ constexpr size_t attr_col_bytes(int dtype)
+{
+    return (size_t)attr_f32_rows(dtype) * 4 + (size_t)(56 - attr_f32_rows(dtype)) * 2;
+}
+
 // ---------------------------------------------------------------- loads
 __device__ __forceinline__ float ld_attr(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ld_attr(const __nv_bfloat16 *p)
 {
     return __bfloat162float(__ldg(p));
 }
+
+// Read access to the 56 attribute rows of storage type DT (REFINE_F32,
+// REFINE_BF16 or REFINE_BF16S), each row widened to float on load.  The row
+// index is a compile-time constant wherever the kernels unroll over rows,
+// so the choice of block (float32 or bfloat16) costs nothing.
+template <int DT>
+struct AttrRows {
+    const float *f;          // the float32 rows [0, attr_f32_rows(DT))
+    const __nv_bfloat16 *b;  // the bfloat16 rows after them
+    int64_t S;               // row stride in elements
+
+    __host__ __device__ AttrRows(const void *attr, int64_t stride)
+        : f(static_cast<const float *>(attr)),
+          b(reinterpret_cast<const __nv_bfloat16 *>(static_cast<const char *>(attr) +
+                                                    (size_t)attr_f32_rows(DT) * 4 * (size_t)stride)),
+          S(stride)
+    {
+    }
+    __device__ __forceinline__ float ld(int r, int64_t i) const
+    {
+        return r < attr_f32_rows(DT) ? ld_attr(f + (int64_t)r * S + i)
+                                     : ld_attr(b + (int64_t)(r - attr_f32_rows(DT)) * S + i);
+    }
+};
 
 // --------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p)

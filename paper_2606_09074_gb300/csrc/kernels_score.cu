@@ -147,9 +147,9 @@ constexpr int kFeatRedRow = kFeatThreads + kFeatRedLanes;         // padded row:
 static_assert(kFeatSums * kFeatRedLanes <= kFeatThreads, "one reduction thread per (sum, lane)");
 static_assert(kFeatThreads % kFeatRedLanes == 0, "whole columns per reduction lane");
 
-template <typename AT>
+template <int DT>
 __global__ void __launch_bounds__(kFeatThreads, 4) k_features(const float *__restrict__ pos,
-                                                           const AT *__restrict__ attr, int64_t S, int64_t n,
+                                                           AttrRows<DT> attr, int64_t S, int64_t n,
                                                            float eta, float l0, float l1, float l2,
                                                            PrimRec *__restrict__ recs,
                                                            float2 *__restrict__ partials, int *status,
@@ -168,15 +168,14 @@ __global__ void __launch_bounds__(kFeatThreads, 4) k_features(const float *__res
         float sq = 0.f;
 #pragma unroll
         for (int r = 8; r < 56; ++r) {
-            const float x = ld_attr(attr + r * S + i);
+            const float x = attr.ld(r, i);
             sq = fmaf(x, x, sq);
         }
         float4 ra, rb, rc, rd;
-        primitive_record(acc, __ldg(pos + i), __ldg(pos + S + i), __ldg(pos + 2 * S + i), ld_attr(attr + i),
-                         ld_attr(attr + S + i), ld_attr(attr + 2 * S + i), ld_attr(attr + 3 * S + i),
-                         ld_attr(attr + 4 * S + i), ld_attr(attr + 5 * S + i), ld_attr(attr + 6 * S + i),
-                         ld_attr(attr + 7 * S + i), ld_attr(attr + 8 * S + i), ld_attr(attr + 9 * S + i),
-                         ld_attr(attr + 10 * S + i), sq, eta, l0, l1, l2, ra, rb, rc, rd, zero_q);
+        primitive_record(acc, __ldg(pos + i), __ldg(pos + S + i), __ldg(pos + 2 * S + i), attr.ld(0, i),
+                         attr.ld(1, i), attr.ld(2, i), attr.ld(3, i), attr.ld(4, i), attr.ld(5, i), attr.ld(6, i),
+                         attr.ld(7, i), attr.ld(8, i), attr.ld(9, i), attr.ld(10, i), sq, eta, l0, l1, l2, ra, rb,
+                         rc, rd, zero_q);
         PrimRec *r = recs + i;
         r->a = ra; r->b = rb; r->c = rc; r->d = rd;
     }
@@ -234,12 +233,15 @@ cudaError_t launch_features(const float *pos, const void *attr, int dtype, int64
 {
     const int nb = feature_blocks(n);
     if (dtype == REFINE_BF16)
-        k_features<__nv_bfloat16><<<nb, kFeatThreads, 0, s>>>(pos, static_cast<const __nv_bfloat16 *>(attr), stride,
-                                                              n, eta, luma[0], luma[1], luma[2], recs, partials,
-                                                              status, tail);
+        k_features<REFINE_BF16><<<nb, kFeatThreads, 0, s>>>(pos, AttrRows<REFINE_BF16>(attr, stride), stride, n, eta,
+                                                            luma[0], luma[1], luma[2], recs, partials, status, tail);
+    else if (dtype == REFINE_BF16S)
+        k_features<REFINE_BF16S><<<nb, kFeatThreads, 0, s>>>(pos, AttrRows<REFINE_BF16S>(attr, stride), stride, n,
+                                                             eta, luma[0], luma[1], luma[2], recs, partials, status,
+                                                             tail);
     else
-        k_features<float><<<nb, kFeatThreads, 0, s>>>(pos, static_cast<const float *>(attr), stride, n, eta, luma[0],
-                                                      luma[1], luma[2], recs, partials, status, tail);
+        k_features<REFINE_F32><<<nb, kFeatThreads, 0, s>>>(pos, AttrRows<REFINE_F32>(attr, stride), stride, n, eta,
+                                                           luma[0], luma[1], luma[2], recs, partials, status, tail);
     return cudaGetLastError();
 }
 
@@ -273,8 +275,8 @@ __device__ __forceinline__ uint32_t quantise(float x, float lo, float qs, float 
     return (uint32_t)fminf(fmaxf((x - lo) * qs, 0.f), top);
 }
 
-template <typename AT>
-__global__ void k_cells(const float *__restrict__ pos, const AT *__restrict__ attr, int64_t stride, int64_t n,
+template <int DT>
+__global__ void k_cells(const float *__restrict__ pos, AttrRows<DT> attr, int64_t stride, int64_t n,
                         int cell_bits, const SceneConsts *__restrict__ consts, uint2 *__restrict__ cell,
                         unsigned *__restrict__ counts)
 {
@@ -291,8 +293,7 @@ __global__ void k_cells(const float *__restrict__ pos, const AT *__restrict__ at
             x[u] = ok ? __ldg(pos + j) : 0.f;
             y[u] = ok ? __ldg(pos + stride + j) : 0.f;
             z[u] = ok ? __ldg(pos + 2 * stride + j) : 0.f;
-            ls[u] = ok ? fmaxf(ld_attr(attr + j), fmaxf(ld_attr(attr + stride + j), ld_attr(attr + 2 * stride + j)))
-                       : 0.f;
+            ls[u] = ok ? fmaxf(attr.ld(0, j), fmaxf(attr.ld(1, j), attr.ld(2, j))) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < kSortU; ++u) {
@@ -318,12 +319,16 @@ static int sort_grid(int num_sms, int64_t n)
 cudaError_t launch_cells(const float *pos, const void *attr, int dtype, int64_t stride, int64_t n, int cell_bits,
                          const SceneConsts *consts, uint2 *cell, unsigned *counts, int num_sms, cudaStream_t s)
 {
+    const int g = sort_grid(num_sms, n);
     if (dtype == REFINE_BF16)
-        k_cells<__nv_bfloat16><<<sort_grid(num_sms, n), 256, 0, s>>>(
-            pos, static_cast<const __nv_bfloat16 *>(attr), stride, n, cell_bits, consts, cell, counts);
+        k_cells<REFINE_BF16><<<g, 256, 0, s>>>(pos, AttrRows<REFINE_BF16>(attr, stride), stride, n, cell_bits, consts,
+                                               cell, counts);
+    else if (dtype == REFINE_BF16S)
+        k_cells<REFINE_BF16S><<<g, 256, 0, s>>>(pos, AttrRows<REFINE_BF16S>(attr, stride), stride, n, cell_bits,
+                                                consts, cell, counts);
     else
-        k_cells<float><<<sort_grid(num_sms, n), 256, 0, s>>>(pos, static_cast<const float *>(attr), stride, n,
-                                                             cell_bits, consts, cell, counts);
+        k_cells<REFINE_F32><<<g, 256, 0, s>>>(pos, AttrRows<REFINE_F32>(attr, stride), stride, n, cell_bits, consts,
+                                              cell, counts);
     return cudaGetLastError();
 }
 

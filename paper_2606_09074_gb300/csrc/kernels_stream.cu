@@ -55,15 +55,24 @@ __device__ __forceinline__ void move_rows(const T *__restrict__ in, int64_t S, b
     }
 }
 
-template <typename AT>
+// DT is the storage type of the attribute rows: its float32 rows are moved
+// as float, the rest as bfloat16, each block of rows from and to its own
+// place in the layout (attr_f32_rows).
+template <int DT>
 __global__ void __launch_bounds__(32 * kCmpWarps) k_compact_warp(const float *__restrict__ pos,
-                                                                 const AT *__restrict__ attr, int64_t S, int64_t n,
+                                                                 const void *__restrict__ attr, int64_t S, int64_t n,
                                                                  const uint32_t *__restrict__ mask,
                                                                  const unsigned long long *__restrict__ seg_off,
                                                                  const CmpState *cs, float *__restrict__ out_pos,
-                                                                 AT *__restrict__ out_attr, int64_t OS,
+                                                                 void *__restrict__ out_attr, int64_t OS,
                                                                  int32_t *__restrict__ out_idx)
 {
+    constexpr int NF = attr_f32_rows(DT), NB = 56 - NF;
+    const float *in_f = static_cast<const float *>(attr);
+    const __nv_bfloat16 *in_b =
+        reinterpret_cast<const __nv_bfloat16 *>(static_cast<const char *>(attr) + (size_t)NF * 4 * (size_t)S);
+    float *out_f = static_cast<float *>(out_attr);
+    __nv_bfloat16 *out_b = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(out_attr) + (size_t)NF * 4 * (size_t)OS);
     __shared__ unsigned char src_of[kCmpWarps][32];
     if (!cs->ok) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -94,7 +103,8 @@ __global__ void __launch_bounds__(32 * kCmpWarps) k_compact_warp(const float *__
         const bool st = lane < kept;
         if (out_idx && st) out_idx[dst] = (int32_t)(base + src);
         move_rows<float, 3>(pos + base + lane, S, ld, src, out_pos + dst, OS, st);
-        move_rows<AT, 56>(attr + base + lane, S, ld, src, out_attr + dst, OS, st);
+        if constexpr (NF > 0) move_rows<float, NF>(in_f + base + lane, S, ld, src, out_f + dst, OS, st);
+        if constexpr (NB > 0) move_rows<__nv_bfloat16, NB>(in_b + base + lane, S, ld, src, out_b + dst, OS, st);
     }
 }
 
@@ -212,10 +222,11 @@ cudaError_t launch_compact_scatter(const refine_scene &in, const uint32_t *mask,
                                    int32_t *out_idx, CmpShape shape, cudaStream_t s)
 {
     if (in.dtype == REFINE_BF16) {
-        const __nv_bfloat16 *a = static_cast<const __nv_bfloat16 *>(in.attr);
-        __nv_bfloat16 *oa = static_cast<__nv_bfloat16 *>(out_attr);
-        k_compact_warp<__nv_bfloat16><<<shape.grid, 32 * kCmpWarps, 0, s>>>(
-            in.pos, a, in.row_stride, in.n, mask, seg_off, cs, out_pos, oa, out_stride, out_idx);
+        k_compact_warp<REFINE_BF16><<<shape.grid, 32 * kCmpWarps, 0, s>>>(
+            in.pos, in.attr, in.row_stride, in.n, mask, seg_off, cs, out_pos, out_attr, out_stride, out_idx);
+    } else if (in.dtype == REFINE_BF16S) {
+        k_compact_warp<REFINE_BF16S><<<shape.grid, 32 * kCmpWarps, 0, s>>>(
+            in.pos, in.attr, in.row_stride, in.n, mask, seg_off, cs, out_pos, out_attr, out_stride, out_idx);
     } else {
         const float *a = static_cast<const float *>(in.attr);
         float *oa = static_cast<float *>(out_attr);
@@ -223,8 +234,9 @@ cudaError_t launch_compact_scatter(const refine_scene &in, const uint32_t *mask,
             k_compact_seg<<<shape.grid, 32 * kCmpWarps, 0, s>>>(in.pos, a, in.row_stride, in.n, mask, seg_off, cs,
                                                                 out_pos, oa, out_stride, out_idx);
         else
-            k_compact_warp<float><<<shape.grid, 32 * kCmpWarps, 0, s>>>(in.pos, a, in.row_stride, in.n, mask,
-                                                                        seg_off, cs, out_pos, oa, out_stride, out_idx);
+            k_compact_warp<REFINE_F32><<<shape.grid, 32 * kCmpWarps, 0, s>>>(in.pos, a, in.row_stride, in.n, mask,
+                                                                             seg_off, cs, out_pos, oa, out_stride,
+                                                                             out_idx);
     }
     return cudaGetLastError();
 }

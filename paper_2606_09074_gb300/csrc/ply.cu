@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include "refine.h"
+#include "common.cuh"
 
 namespace {
 
@@ -42,16 +43,18 @@ int scene_row(int p)
     return 3 + 3 + (p - 58);             // rot_*    = attr rows 3-6
 }
 
-float load(const void *attr, int dtype, int64_t idx)
+// Attribute row r (0..55) of primitive i, widened to float: float32 rows
+// first, then bfloat16 rows, each of row_stride elements.
+float load(const void *attr, int dtype, int r, int64_t row_stride, int64_t i)
 {
-    if (dtype == REFINE_BF16) {
-        const unsigned short b = static_cast<const unsigned short *>(attr)[idx];
-        unsigned int u = (unsigned int)b << 16;
-        float f;
-        memcpy(&f, &u, 4);
-        return f;
-    }
-    return static_cast<const float *>(attr)[idx];
+    const int nf = refine::attr_f32_rows(dtype);
+    if (r < nf) return static_cast<const float *>(attr)[r * row_stride + i];
+    const unsigned short *b =
+        reinterpret_cast<const unsigned short *>(static_cast<const char *>(attr) + (size_t)nf * 4 * row_stride);
+    unsigned int u = (unsigned int)b[(r - nf) * row_stride + i] << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
 }
 
 }  // namespace
@@ -61,7 +64,7 @@ extern "C" {
 refine_status refine_write_ply(const char *path, int64_t n, int32_t dtype, const float *pos_host,
                                const void *attr_host, int64_t row_stride)
 {
-    if (!path || n < 0 || (dtype != REFINE_F32 && dtype != REFINE_BF16) || row_stride < n ||
+    if (!path || n < 0 || !refine::valid_dtype(dtype) || row_stride < n ||
         (n > 0 && (!pos_host || !attr_host)))
         return REFINE_EINVAL;
     FILE *f = fopen(path, "wb");
@@ -79,7 +82,7 @@ refine_status refine_write_ply(const char *path, int64_t n, int32_t dtype, const
             float *row = &buf[(size_t)j * kPlyProps];
             for (int p = 0; p < kPlyProps; ++p) {
                 const int r = scene_row(p);
-                row[p] = r < 0 ? 0.f : (r < 3 ? pos_host[r * row_stride + i] : load(attr_host, dtype, (r - 3) * row_stride + i));
+                row[p] = r < 0 ? 0.f : (r < 3 ? pos_host[r * row_stride + i] : load(attr_host, dtype, r - 3, row_stride, i));
             }
         }
         // PLY binary_little_endian: the hosts this builds for are little-endian

@@ -112,7 +112,8 @@ bool is_pinned(const void *p)
     return a.type == cudaMemoryTypeHost;
 }
 
-size_t elem_size(int dtype) { return dtype == REFINE_BF16 ? 2 : 4; }
+// Bytes of the 56 attribute rows per primitive (per element of the stride).
+size_t elem_size(int dtype) { return attr_col_bytes(dtype); }
 
 }  // namespace
 
@@ -165,9 +166,9 @@ uint64_t footprint_of(int64_t n, int dtype, int V, const ScenePlan &pl, double r
 {
     const size_t S = (size_t)dev_stride(n), es = elem_size(dtype);
     const int64_t nk = keep_count(n, ratio);
-    const size_t parts = carve_size({3 * S * 4, 56 * S * es, sizeof(refine_camera) * (size_t)V, 4 * (size_t)n,
+    const size_t parts = carve_size({3 * S * 4, S * es, sizeof(refine_camera) * (size_t)V, 4 * (size_t)n,
                                      4 * (size_t)((n + 31) / 32), compact ? 3 * (size_t)nk * 4 : 0,
-                                     compact ? 56 * (size_t)nk * es : 0, compact ? 4 * (size_t)nk : 0, 256});
+                                     compact ? (size_t)nk * es : 0, compact ? 4 * (size_t)nk : 0, 256});
     return parts + scene_bytes(pl) + select_bytes(n) + compact_bytes(n) + 3 * 256;
 }
 
@@ -178,13 +179,13 @@ void carve_job(QJob *j)
     const size_t es = elem_size(j->req.dtype);
     Carver cv(j->block);
     float *pos = cv.take<float>(3 * (size_t)S);
-    char *attr = cv.take<char>(56 * (size_t)S * es);
+    char *attr = cv.take<char>((size_t)S * es);
     j->cams = cv.take<refine_camera>(j->req.n_views);
     j->scores = cv.take<float>(n);
     j->mask = cv.take<uint32_t>((n + 31) / 32);
     if (j->compact) {
         j->out_pos = cv.take<float>(3 * (size_t)nk);
-        j->out_attr = cv.take<char>(56 * (size_t)nk * es);
+        j->out_attr = cv.take<char>((size_t)nk * es);
         j->idx = cv.take<int32_t>(nk);
     } else {
         cv.take<char>(0);
@@ -224,12 +225,18 @@ refine_status issue_prep(refine_queue *q, QJob *j)
     }
     carve_job(j);
     const int64_t n = j->req.n, S = dev_stride(n);
-    const size_t es = elem_size(j->req.dtype);
     e = cudaMemcpy2DAsync(const_cast<float *>(j->scene.pos), (size_t)S * 4, j->req.pos_host, (size_t)n * 4,
                           (size_t)n * 4, 3, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync(const_cast<void *>(j->scene.attr), (size_t)S * es, j->req.attr_host, (size_t)n * es,
-                              (size_t)n * es, 56, cudaMemcpyHostToDevice, cs);
+    // the attribute rows block by block (float32 rows, then bfloat16 rows),
+    // from host rows of n elements to device rows of S
+    const int nf = attr_f32_rows(j->req.dtype);
+    char *dst = static_cast<char *>(const_cast<void *>(j->scene.attr));
+    const char *src = static_cast<const char *>(j->req.attr_host);
+    if (e == cudaSuccess && nf > 0)
+        e = cudaMemcpy2DAsync(dst, (size_t)S * 4, src, (size_t)n * 4, (size_t)n * 4, nf, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && nf < 56)
+        e = cudaMemcpy2DAsync(dst + (size_t)nf * 4 * S, (size_t)S * 2, src + (size_t)nf * 4 * n, (size_t)n * 2,
+                              (size_t)n * 2, 56 - nf, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(j->cams, j->req.cams_host, sizeof(refine_camera) * j->req.n_views,
                             cudaMemcpyHostToDevice, cs);
@@ -280,7 +287,7 @@ refine_status issue_finish(refine_queue *q, QJob *j, const RoundRes &R)
         if (e == cudaSuccess && j->compact) {
             e = cudaMemcpyAsync(j->req.out_pos_host, j->out_pos, 12 * (size_t)nk, cudaMemcpyDeviceToHost, cs);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(j->req.out_attr_host, j->out_attr, 56 * es * (size_t)nk, cudaMemcpyDeviceToHost,
+                e = cudaMemcpyAsync(j->req.out_attr_host, j->out_attr, es * (size_t)nk, cudaMemcpyDeviceToHost,
                                     cs);
             if (e == cudaSuccess && j->req.kept_idx_host)
                 e = cudaMemcpyAsync(j->req.kept_idx_host, j->idx, 4 * (size_t)nk, cudaMemcpyDeviceToHost, cs);
@@ -478,7 +485,7 @@ refine_status finish_pageable(refine_queue *q, QJob *j)
     if (e == cudaSuccess && j->compact) {
         e = cudaMemcpyAsync(j->req.out_pos_host, j->out_pos, 12 * (size_t)nk, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(j->req.out_attr_host, j->out_attr, 56 * es * (size_t)nk, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(j->req.out_attr_host, j->out_attr, es * (size_t)nk, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && j->req.kept_idx_host)
             e = cudaMemcpyAsync(j->req.kept_idx_host, j->idx, 4 * (size_t)nk, cudaMemcpyDeviceToHost, s);
     }
@@ -602,7 +609,7 @@ extern "C" {
 
 uint64_t refine_queue_footprint(int64_t n, int32_t dtype, int32_t n_views, double ratio, int32_t compact)
 {
-    if (n < 1 || n > INT32_MAX || (dtype != REFINE_F32 && dtype != REFINE_BF16) || n_views < 1 ||
+    if (n < 1 || n > INT32_MAX || !valid_dtype(dtype) || n_views < 1 ||
         n_views > 65535 || !(ratio >= 0.0 && ratio < 1.0))
         return 0;
     // the smallest camera block: the running sums are included whenever a
@@ -718,7 +725,7 @@ refine_status refine_queue_submit(refine_queue *q, const refine_request *req, ui
 {
     if (!q || !req || !ticket) return REFINE_EINVAL;
     const refine_request &r = *req;
-    if (r.n < 1 || r.n > INT32_MAX || (r.dtype != REFINE_F32 && r.dtype != REFINE_BF16) || r.n_views < 1 ||
+    if (r.n < 1 || r.n > INT32_MAX || !valid_dtype(r.dtype) || r.n_views < 1 ||
         r.n_views > 65535 || !(r.ratio >= 0.0 && r.ratio < 1.0) || !r.pos_host || !r.attr_host ||
         !r.cams_host || (r.out_pos_host && !r.out_attr_host) || (!r.out_pos_host && (r.out_attr_host || r.kept_idx_host)))
         return REFINE_EINVAL;

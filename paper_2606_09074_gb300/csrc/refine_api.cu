@@ -176,34 +176,34 @@ refine_status refine_prune_host(refine_ctx *c, int64_t n, int32_t dtype, const f
     refine_status st = use_device(c);
     if (st) return st;
     if (n < 0 || n > INT32_MAX) return fail(c, REFINE_EINVAL, "prune_host: n out of range");
-    if (dtype != REFINE_F32 && dtype != REFINE_BF16) return fail(c, REFINE_EINVAL, "prune_host: bad dtype");
+    if (!valid_dtype(dtype)) return fail(c, REFINE_EINVAL, "prune_host: bad dtype");
     if (n_views < 1 || n_views > 65535 || !cams_host) return fail(c, REFINE_EINVAL, "prune_host: bad cameras");
     if (!(ratio >= 0.0 && ratio < 1.0)) return fail(c, REFINE_EINVAL, "prune_host: ratio must lie in [0, 1)");
     if (n > 0 && (!pos_host || !attr_host || !out_pos_host || !out_attr_host))
         return fail(c, REFINE_EINVAL, "prune_host: NULL host buffer");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const size_t es = dtype == REFINE_BF16 ? 2 : 4;
+    const size_t es = attr_col_bytes(dtype);  // bytes of the 56 attribute rows per primitive
     const int64_t n_keep = n - (int64_t)floor(ratio * (double)n);
     const int64_t words = (n + 31) / 32;
     const int64_t nk_alloc = n_keep > 0 ? n_keep : 1;
     if ((st = ensure(c, c->host,
-                     carve_size({12 * (size_t)n, 56 * es * (size_t)n, sizeof(refine_camera) * (size_t)n_views,
+                     carve_size({12 * (size_t)n, es * (size_t)n, sizeof(refine_camera) * (size_t)n_views,
                                  4 * (size_t)n, 4 * (size_t)words, 12 * (size_t)nk_alloc,
-                                 56 * es * (size_t)nk_alloc, 4 * (size_t)nk_alloc}))))
+                                 es * (size_t)nk_alloc, 4 * (size_t)nk_alloc}))))
         return st;
     Carver cv(c->host.p);
     float *d_pos = cv.take<float>(3 * (size_t)n);
-    char *d_attr = cv.take<char>(56 * es * (size_t)n);
+    char *d_attr = cv.take<char>(es * (size_t)n);
     refine_camera *d_cams = cv.take<refine_camera>(n_views);
     float *d_scores = cv.take<float>(n);
     uint32_t *d_mask = cv.take<uint32_t>(words);
     float *d_opos = cv.take<float>(3 * (size_t)nk_alloc);
-    char *d_oattr = cv.take<char>(56 * es * (size_t)nk_alloc);
+    char *d_oattr = cv.take<char>(es * (size_t)nk_alloc);
     int32_t *d_idx = cv.take<int32_t>(nk_alloc);
     cudaError_t e = cudaSuccess;
     if (n > 0) {
         e = cudaMemcpyAsync(d_pos, pos_host, 12 * (size_t)n, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_attr, attr_host, 56 * es * (size_t)n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_attr, attr_host, es * (size_t)n, cudaMemcpyHostToDevice, s);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_cams, cams_host, sizeof(refine_camera) * (size_t)n_views, cudaMemcpyHostToDevice, s);
@@ -224,7 +224,7 @@ refine_status refine_prune_host(refine_ctx *c, int64_t n, int32_t dtype, const f
     if (n_keep > 0) {
         e = cudaMemcpyAsync(out_pos_host, d_opos, 12 * (size_t)n_keep, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(out_attr_host, d_oattr, 56 * es * (size_t)n_keep, cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(out_attr_host, d_oattr, es * (size_t)n_keep, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && out_idx_host)
             e = cudaMemcpyAsync(out_idx_host, d_idx, 4 * (size_t)n_keep, cudaMemcpyDeviceToHost, s);
     }

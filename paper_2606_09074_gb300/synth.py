@@ -57,8 +57,10 @@ RESOLUTIONS = ((960, 540), (1297, 840), (1600, 1063))
 @dataclasses.dataclass
 class Scene:
     """A scene in SoA form. ``pos`` is float32 [3, n]; ``attr`` is float32
-    [56, n] (``dtype == 'f32'``) or uint16 bfloat16 bits [56, n]
-    (``dtype == 'bf16'``)."""
+    [56, n] (``dtype == 'f32'``), uint16 bfloat16 bits [56, n]
+    (``dtype == 'bf16'``), or float32 [56, n] whose rows 3..55 hold
+    bfloat16-rounded values and rows 0..2 (log-scales) float32 values
+    (``dtype == 'bf16s'``, the storage form with float32 log-scales)."""
 
     pos: np.ndarray
     attr: np.ndarray
@@ -70,7 +72,7 @@ class Scene:
 
     def attr_f32(self) -> np.ndarray:
         """Attributes widened to float32 (exact for both storage forms)."""
-        if self.dtype == "f32":
+        if self.dtype in ("f32", "bf16s"):
             return self.attr
         return bf16_bits_to_f32(self.attr)
 
@@ -89,7 +91,15 @@ class Scene:
     def to_bf16(self) -> "Scene":
         if self.dtype == "bf16":
             return self
-        return Scene(self.pos.copy(), f32_to_bf16_bits(self.attr), "bf16")
+        return Scene(self.pos.copy(), f32_to_bf16_bits(self.attr_f32()), "bf16")
+
+    def to_bf16s(self) -> "Scene":
+        """Log-scale rows kept float32, the other 53 rows rounded to bfloat16."""
+        if self.dtype == "bf16s":
+            return self
+        a = np.array(self.attr_f32(), dtype=np.float32, copy=True)
+        a[3:] = bf16_bits_to_f32(f32_to_bf16_bits(a[3:]))
+        return Scene(self.pos.copy(), a, "bf16s")
 
 
 def f32_to_bf16_bits(x: np.ndarray) -> np.ndarray:
@@ -226,6 +236,8 @@ def config2(seed: int = 2, n: int = 3_500_000, v: int = 250, dtype: str = "f32")
     w.ratios = (0.5,)
     if dtype == "bf16":
         w.scene = w.scene.to_bf16()
+    elif dtype == "bf16s":
+        w.scene = w.scene.to_bf16s()
     return w
 
 
@@ -242,6 +254,8 @@ def batch_scene(seed: int, nmin: int = 50_000, nmax: int = 2_000_000,
     cams = make_cameras(hemisphere_centers(rng, v), wh[0], wh[1], 1100.0)
     if dtype == "bf16":
         sc = sc.to_bf16()
+    elif dtype == "bf16s":
+        sc = sc.to_bf16s()
     return Workload(f"batch seed={seed} N={n} V={v} {wh[0]}x{wh[1]}", sc, cams, (0.66,))
 
 
@@ -271,6 +285,8 @@ def job_scene(seed: int, dtype: str = "bf16", n_override: int | None = None) -> 
     cams = make_cameras(hemisphere_centers(rng, v), wh[0], wh[1], 1100.0)
     if dtype == "bf16":
         sc = sc.to_bf16()
+    elif dtype == "bf16s":
+        sc = sc.to_bf16s()
     return Workload(f"job seed={seed} N={n} V={v}", sc, cams, (ratio,))
 
 

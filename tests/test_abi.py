@@ -105,6 +105,8 @@ def test_queue_footprint_host_only(lib):
     bf16 = fp(n, b.REFINE_BF16, 200, 0.5)
     assert f32 > 236 * n + 120 * n          # scene copy + compacted half
     assert bf16 < f32 and bf16 > 124 * n
+    bf16s = fp(n, b.REFINE_BF16S, 200, 0.5)   # 6 more bytes per primitive (and per kept one) than bf16
+    assert bf16 < bf16s < f32 and bf16s - bf16 >= 6 * n
     assert fp(n, b.REFINE_F32, 200, 0.5, compact=False) < f32
     assert fp(2 * n, b.REFINE_F32, 200, 0.5) > f32
     assert fp(0, b.REFINE_F32, 200, 0.5) == 0 and fp(n, 7, 200, 0.5) == 0
@@ -113,3 +115,14 @@ def test_queue_footprint_host_only(lib):
     assert fp(n, b.REFINE_F32, 33, 0.5) >= fp(n, b.REFINE_F32, 32, 0.5) + 8 * n
     assert fp(n, b.REFINE_F32, 1100, 0.5) > fp(n, b.REFINE_F32, 200, 0.5)
     assert fp(n, b.REFINE_F32, 65536, 0.5) == 0 and fp(n, b.REFINE_F32, 200, 1.0) == 0
+
+
+def test_storage_type_codes_match_header():
+    """The binding's storage-type codes are the header's enum values."""
+    import re
+    from paper_2606_09074_gb300 import binding as b
+    hdr = open(os.path.join(ROOT, "include", "refine.h")).read()
+    m = re.search(r"enum\s*\{\s*REFINE_F32\s*=\s*(\d+),\s*REFINE_BF16\s*=\s*(\d+),\s*REFINE_BF16S\s*=\s*(\d+)\s*\}", hdr)
+    assert m, "storage-type enum not found in include/refine.h"
+    assert (b.REFINE_F32, b.REFINE_BF16, b.REFINE_BF16S) == tuple(int(x) for x in m.groups())
+

@@ -25,6 +25,8 @@ def upload(torch, rb, w):
     pos = torch.from_numpy(w.scene.pos).to(dev)
     if w.scene.dtype == "bf16":
         attr = torch.from_numpy(w.scene.attr.view(np.int16)).to(dev).view(torch.bfloat16)
+    elif w.scene.dtype == "bf16s":
+        attr = rb.MixedRows.from_float(w.scene.attr, device=dev)
     else:
         attr = torch.from_numpy(w.scene.attr).to(dev)
     return pos, attr, rb.cameras_to_device(w.cams, dev)
@@ -77,14 +79,17 @@ def test_batch_rejects_bad_jobs(env):
 
 
 def test_batch_mixed_storage_and_flags(env):
-    """Scenes of both storage types share one batched launch; each equals
-    its own per-scene run, for every projection mode."""
+    """Scenes of all three storage types share one batched launch; each
+    equals its own per-scene run (scores, and the compacted rows of the
+    mixed-layout scene), for every projection mode."""
     torch, rb, ctx = env
     ws = []
-    for k, (seed, n, v) in enumerate([(41, 5000, 9), (42, 33_333, 40), (43, 700, 3)]):
+    for k, (seed, n, v) in enumerate([(41, 5000, 9), (42, 33_333, 40), (43, 700, 3), (44, 20_011, 17)]):
         w = synth.random_scene(seed=seed, n=n, v=v, means="core_shell")
-        if k % 2:
+        if k == 1:
             w.scene = w.scene.to_bf16()
+        elif k == 3:
+            w.scene = w.scene.to_bf16s()
         ws.append(w)
     up = [upload(torch, rb, w) for w in ws]
     jobs = [{"pos": p, "attr": a, "cams": c, "ratio": 0.5} for (p, a, c) in up]
@@ -98,6 +103,10 @@ def test_batch_mixed_storage_and_flags(env):
             m, thr, nk = ctx.select(s, 0.5)
             assert torch.equal(batch.outputs[k]["scores"], s), (flags, k)
             assert nk_b[k] == nk and thr_b[k] == thr
+            if isinstance(a, rb.MixedRows):
+                op, oa, idx = ctx.compact(p, a, m, nk)
+                assert torch.equal(batch.outputs[k]["idx"][:nk], idx)
+                assert torch.equal(batch.outputs[k]["out_attr"][:, :nk].float(), oa.float())
         batch.close()
 
 

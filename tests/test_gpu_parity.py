@@ -45,6 +45,8 @@ def upload(torch, rb, scene, cams):
     pos = torch.from_numpy(np.ascontiguousarray(scene.pos)).to(dev)
     if scene.dtype == "bf16":
         attr = torch.from_numpy(np.ascontiguousarray(scene.attr).view(np.int16)).to(dev).view(torch.bfloat16)
+    elif scene.dtype == "bf16s":
+        attr = rb.MixedRows.from_float(scene.attr, device=dev)
     else:
         attr = torch.from_numpy(np.ascontiguousarray(scene.attr)).to(dev)
     return pos, attr, rb.cameras_to_device(cams, dev)
@@ -86,7 +88,12 @@ def check_compact_exact(torch, ctx, scene, pos, attr, mask, nk):
     assert np.array_equal(idx.cpu().numpy(), ki)
     assert np.array_equal(op.cpu().numpy(), kp)
     got_attr = oa.cpu()
-    got_attr = got_attr.view(torch.int16).numpy().view(np.uint16) if scene.dtype == "bf16" else got_attr.numpy()
+    if scene.dtype == "bf16":
+        got_attr = got_attr.view(torch.int16).numpy().view(np.uint16)
+    elif scene.dtype == "bf16s":
+        got_attr = got_attr.float().numpy()  # widened exactly, rows 3..55 from bfloat16
+    else:
+        got_attr = got_attr.numpy()
     assert np.array_equal(got_attr, ka)
 
 
@@ -130,6 +137,43 @@ def test_bf16_storage_parity(torch, rb, ctx):
     assert_score_parity(s, S, ref)
     mask, _, nk = check_select_exact(torch, ctx, s, 0.66)
     check_compact_exact(torch, ctx, sc, pos, attr, mask, nk)
+
+
+def test_bf16s_storage_parity(torch, rb, ctx):
+    """Log-scale rows float32, rows 6-58 bfloat16 (REFINE_BF16S): the oracle
+    sees the same numbers; selection and compaction are exact, the mixed
+    rows included; and the log-scales reach the kernels unrounded (the
+    scores differ from the all-BF16 form's wherever a log-scale is not a
+    bfloat16 value)."""
+    w = synth.config0(seed=4)
+    sc = w.scene.to_bf16s()
+    assert np.array_equal(sc.attr[:3], w.scene.attr[:3])
+    s, S, _, (pos, attr) = gpu_score(torch, rb, ctx, sc, w.cams)
+    ref = oracle.score(sc.params_f64(), w.cams)
+    assert_score_parity(s, S, ref)
+    mask, _, nk = check_select_exact(torch, ctx, s, 0.66)
+    check_compact_exact(torch, ctx, sc, pos, attr, mask, nk)
+    sb = gpu_score(torch, rb, ctx, w.scene.to_bf16(), w.cams)[0]
+    assert not np.array_equal(s, sb)
+
+
+@pytest.mark.parametrize("n,v", [(1, 3), (1000, 7), (33_333, 40)])
+def test_bf16s_ragged_and_host_path(torch, rb, ctx, n, v):
+    """Ragged sizes in the mixed layout, and the whole pass from host rows
+    (refine_prune_host) equal to the device path."""
+    w = synth.random_scene(seed=n + v, n=n, v=v, means="core_shell")
+    sc = w.scene.to_bf16s()
+    s, S, _, (pos, attr) = gpu_score(torch, rb, ctx, sc, w.cams)
+    assert_score_parity(s, S, oracle.score(sc.params_f64(), w.cams))
+    mask, thr, nk = ctx.select(torch.from_numpy(s).cuda(), 0.5)
+    op, oa, idx = ctx.compact(pos, attr, mask, nk)
+    r = ctx.prune_host(torch.from_numpy(sc.pos).pin_memory(), rb.MixedRows.from_float(sc.attr, pin_memory=True),
+                       w.cams, 0.5, want_scores=True)
+    assert r["n_keep"] == nk and r["threshold"] == thr
+    assert np.array_equal(r["scores"].numpy().view(np.uint32), s.view(np.uint32))
+    assert np.array_equal(r["idx"].numpy(), idx.cpu().numpy())
+    assert np.array_equal(r["out_pos"].numpy(), op.cpu().numpy())
+    assert torch.equal(r["out_attr"].float(), oa.float().cpu())
 
 
 def test_many_views_multipass(torch, rb, ctx):
@@ -312,14 +356,17 @@ def test_core_shell_3p5m_full(torch, rb, ctx, c2_oracle):
     check_compact_exact(torch, ctx, w.scene, pos, attr, mask, nk)
 
 
-def test_core_shell_3p5m_bf16_accuracy(torch, rb, ctx, c2_oracle):
+@pytest.mark.parametrize("dtype,min_agree", [("bf16", 0.999), ("bf16s", 0.9995)])
+def test_core_shell_3p5m_bf16_accuracy(torch, rb, ctx, c2_oracle, dtype, min_agree):
     """The precision form on the benchmark scene: rows 3-58 stored as
-    bfloat16.  On its own (rounded) inputs it matches the oracle within the
-    float32 tolerance (100k-primitive sample); against the oracle on the
-    float32 scene it was rounded from, the keep mask at ratio 0.5 agrees on
-    at least 99.9 % of the primitives, and the score error is reported."""
+    bfloat16 (or, for bf16s, rows 6-58 with the log-scales kept float32).
+    On its own (rounded) inputs it matches the oracle within the float32
+    tolerance (100k-primitive sample); against the oracle on the float32
+    scene it was rounded from, the keep mask at ratio 0.5 agrees on at least
+    99.9 % of the primitives (99.95 % with float32 log-scales), and the score
+    error is reported."""
     w, ref32 = c2_oracle
-    sb = w.scene.to_bf16()
+    sb = w.scene.to_bf16() if dtype == "bf16" else w.scene.to_bf16s()
     s, S, _, _ = gpu_score(torch, rb, ctx, sb, w.cams)
     idx = np.sort(np.random.default_rng(7).choice(w.scene.n, 100_000, replace=False))
     refb = oracle.score_subset(sb.params_f64(), idx, w.cams)
@@ -329,9 +376,9 @@ def test_core_shell_3p5m_bf16_accuracy(torch, rb, ctx, c2_oracle):
     _, words, _ = check_select_exact(torch, ctx, s, 0.5)
     m_ref, _, _ = oracle.select(ref32["scores"], 0.5)
     agree = float(np.mean(unpack(words, w.scene.n) == unpack(m_ref, w.scene.n)))
-    print(f"3.5M x 250 BF16 vs the FP64 oracle on the float32 scene: rel err mean {rel.mean():.3e} "
+    print(f"3.5M x 250 {dtype} vs the FP64 oracle on the float32 scene: rel err mean {rel.mean():.3e} "
           f"p99 {np.quantile(rel, 0.99):.3e} max {rel.max():.3e}; mask agreement {agree:.5%}")
-    assert agree >= 0.999
+    assert agree >= min_agree
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
@@ -364,7 +411,8 @@ def test_padded_row_stride(torch, rb, ctx, dtype):
 
 @pytest.mark.parametrize("dtype,pattern,ratio,pad,opad,with_idx", [
     ("f32", "random", 0.5, 0, 0, True), ("f32", "random", 0.1, 37, 5, True), ("f32", "random", 0.97, 64, 0, True),
-    ("f32", "blocks", 0.5, 3, 11, True), ("f32", "random", 0.5, 0, 0, False), ("bf16", "random", 0.66, 9, 2, True)])
+    ("f32", "blocks", 0.5, 3, 11, True), ("f32", "random", 0.5, 0, 0, False), ("bf16", "random", 0.66, 9, 2, True),
+    ("bf16s", "random", 0.5, 7, 3, True)])
 def test_compact_large_ragged(torch, rb, ctx, dtype, pattern, ratio, pad, opad, with_idx):
     """Scenes of about 1.9M primitives or more: FP32 rows are scattered one
     warp per 256-primitive segment, BF16 rows one warp per mask word.  A
@@ -377,17 +425,24 @@ def test_compact_large_ragged(torch, rb, ctx, dtype, pattern, ratio, pad, opad, 
     attr_h = rng.standard_normal((56, n), dtype=np.float32)
     if dtype == "bf16":
         attr_h = synth.f32_to_bf16_bits(attr_h)  # uint16 bit patterns
+    elif dtype == "bf16s":
+        attr_h[3:] = synth.bf16_bits_to_f32(synth.f32_to_bf16_bits(attr_h[3:]))  # exact in the mixed layout
     scores = rng.random(n, dtype=np.float32)
     if pattern == "blocks":
         scores += ((np.arange(n) // 700) % 3).astype(np.float32)
     dev = torch.device("cuda", 0)
     tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
     pos_p = torch.zeros((3, n + pad), dtype=torch.float32, device=dev)
-    attr_p = torch.zeros((56, n + pad), dtype=tdt, device=dev)
     pos_p[:, :n] = torch.from_numpy(pos_h).to(dev)
+    if dtype == "bf16s":
+        attr_p = rb.MixedRows.empty(n, stride=n + pad, device=dev)
+        attr_p.f32_rows()[:, :n] = torch.from_numpy(attr_h[:3]).to(dev)
+        attr_p.bf16_rows()[:, :n] = torch.from_numpy(attr_h[3:]).to(dev).to(torch.bfloat16)
+    else:
+        attr_p = torch.zeros((56, n + pad), dtype=tdt, device=dev)
     if dtype == "bf16":
         attr_p[:, :n] = torch.from_numpy(attr_h.view(np.int16)).to(dev).view(torch.bfloat16)
-    else:
+    elif dtype == "f32":
         attr_p[:, :n] = torch.from_numpy(attr_h).to(dev)
     m, _, nk = ctx.select(torch.from_numpy(scores).to(dev), ratio)
     op, oa, idx, cnt = ctx.compact(pos_p[:, :n], attr_p[:, :n], m, nk, out_row_stride=nk + opad,
@@ -402,7 +457,10 @@ def test_compact_large_ragged(torch, rb, ctx, dtype, pattern, ratio, pad, opad, 
         assert idx is None
     assert np.array_equal(op[:, :nk].cpu().numpy(), kp[:, :nk])
     got = oa[:, :nk].cpu()
-    got = got.view(torch.int16).numpy().view(np.uint16) if dtype == "bf16" else got.numpy()
+    if dtype == "bf16s":
+        got = got.float().numpy()
+    else:
+        got = got.view(torch.int16).numpy().view(np.uint16) if dtype == "bf16" else got.numpy()
     assert np.array_equal(got, ka[:, :nk])
 
 

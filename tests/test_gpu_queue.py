@@ -29,6 +29,7 @@ SPECS = [  # seed, n, views, ratio, storage
     (24, 150_000, 120, 0.5, "bf16"),
     (25, 1, 1, 0.5, "f32"),
     (26, 90_017, 300, 0.0, "f32"),
+    (27, 45_001, 64, 0.66, "bf16s"),
 ]
 
 
@@ -38,6 +39,8 @@ def scenes():
         w = synth.random_scene(seed=seed, n=n, v=v, means="core_shell")
         if st == "bf16":
             w.scene = w.scene.to_bf16()
+        elif st == "bf16s":
+            w.scene = w.scene.to_bf16s()
         out.append((w, r))
     return out
 
@@ -48,6 +51,8 @@ def plain(torch, rb, ctx, w, ratio):
     pos = torch.from_numpy(w.scene.pos).to(dev)
     if w.scene.dtype == "bf16":
         attr = torch.from_numpy(w.scene.attr.view(np.int16)).to(dev).view(torch.bfloat16)
+    elif w.scene.dtype == "bf16s":
+        attr = rb.MixedRows.from_float(w.scene.attr, device=dev)
     else:
         attr = torch.from_numpy(w.scene.attr).to(dev)
     cams = rb.cameras_to_device(w.cams, dev)
@@ -55,9 +60,14 @@ def plain(torch, rb, ctx, w, ratio):
     m, thr, nk = ctx.select(s, ratio)
     op, oa, idx = ctx.compact(pos, attr, m, nk)
     n = pos.shape[1]
+    if w.scene.dtype == "bf16":
+        oa_h = oa.contiguous().cpu().view(torch.int16).numpy().view(np.uint16)
+    elif w.scene.dtype == "bf16s":
+        oa_h = oa.float().cpu().numpy()  # widened exactly
+    else:
+        oa_h = oa.cpu().numpy()
     return {"scores": s.cpu().numpy(), "mask": m[: (n + 31) // 32].cpu().numpy().view(np.uint32),
-            "out_pos": op.cpu().numpy(), "out_attr": oa.contiguous().cpu().view(torch.int16).numpy().view(np.uint16)
-            if w.scene.dtype == "bf16" else oa.cpu().numpy(), "idx": idx.cpu().numpy(), "thr": thr, "nk": nk}
+            "out_pos": op.cpu().numpy(), "out_attr": oa_h, "idx": idx.cpu().numpy(), "thr": thr, "nk": nk}
 
 
 def check_same(ref, res, out, w):
@@ -69,15 +79,29 @@ def check_same(ref, res, out, w):
     assert np.array_equal(np.asarray(out["mask"]).view(np.uint32), ref["mask"])
     assert np.array_equal(np.asarray(out["idx"]), ref["idx"])
     assert np.array_equal(np.asarray(out["out_pos"]).view(np.uint32), ref["out_pos"].view(np.uint32))
-    oa = np.asarray(out["out_attr"])
+    oa = host_attr_array(out["out_attr"])
     if w.scene.dtype == "bf16":
         assert np.array_equal(oa.view(np.uint16), ref["out_attr"])
     else:
         assert np.array_equal(oa.view(np.uint32), ref["out_attr"].view(np.uint32))
 
 
-def host_inputs(w):
+def host_attr_array(a):
+    """A host attribute output as a numpy array (the mixed layout widened to
+    float32, which is exact)."""
+    from paper_2606_09074_gb300 import binding as rb
+    return a.float().numpy() if isinstance(a, rb.MixedRows) else np.asarray(a)
+
+
+def host_inputs(w, pin=False):
+    from paper_2606_09074_gb300 import binding as rb
+    if w.scene.dtype == "bf16s":
+        return w.scene.pos, rb.MixedRows.from_float(w.scene.attr, pin_memory=pin), w.cams
     return w.scene.pos, w.scene.attr, w.cams
+
+
+def dtype_code(rb, w):
+    return {"f32": rb.REFINE_F32, "bf16": rb.REFINE_BF16, "bf16s": rb.REFINE_BF16S}[w.scene.dtype]
 
 
 def test_alone_equals_mix_equals_plain(env):
@@ -116,8 +140,7 @@ def test_pinned_buffers_and_budget_admission(env):
     torch, rb, ctx = env
     sc = scenes()
     refs = [plain(torch, rb, ctx, w, r) for w, r in sc]
-    big = max(rb.Queue.footprint(w.scene.n, rb.REFINE_BF16 if w.scene.dtype == "bf16" else rb.REFINE_F32,
-                                 len(w.cams), r) for w, r in sc)
+    big = max(rb.Queue.footprint(w.scene.n, dtype_code(rb, w), len(w.cams), r) for w, r in sc)
     budget = big + big // 2  # never two of the largest at once
     q = rb.Queue(ctx, budget_bytes=budget, max_slots=4)
     try:
@@ -125,13 +148,17 @@ def test_pinned_buffers_and_budget_admission(env):
         for rep in range(2):
             for (w, r) in sc:
                 pos = torch.from_numpy(w.scene.pos).pin_memory()
-                attr = (torch.from_numpy(w.scene.attr.view(np.int16)).view(torch.bfloat16)
-                        if w.scene.dtype == "bf16" else torch.from_numpy(w.scene.attr)).pin_memory()
+                if w.scene.dtype == "bf16s":
+                    attr = host_inputs(w, pin=True)[1]
+                else:
+                    attr = (torch.from_numpy(w.scene.attr.view(np.int16)).view(torch.bfloat16)
+                            if w.scene.dtype == "bf16" else torch.from_numpy(w.scene.attr)).pin_memory()
                 tickets.append(q.submit(pos, attr, w.cams, r, scores=True, pin=True))
         for k, t in enumerate(tickets):
             res, out = q.poll(t, timeout_ms=60_000)
             w, _ = sc[k % len(sc)]
-            outn = {key: (v.view(torch.int16).numpy().view(np.uint16) if v.dtype == torch.bfloat16 else v.numpy())
+            outn = {key: (v if isinstance(v, rb.MixedRows) else
+                          v.view(torch.int16).numpy().view(np.uint16) if v.dtype == torch.bfloat16 else v.numpy())
                     for key, v in out.items()}
             check_same(refs[k % len(sc)], res, outn, w)
         st = q.stats()
@@ -210,7 +237,7 @@ def test_queue_matches_oracle(env):
             assert res["n_keep"] == ki.shape[0]
             assert np.array_equal(np.asarray(out["idx"]), ki)
             assert np.array_equal(np.asarray(out["out_pos"]).view(np.uint32), kp.view(np.uint32))
-            oa = np.asarray(out["out_attr"])
+            oa = host_attr_array(out["out_attr"])
             assert np.array_equal(oa.view(np.uint16 if w.scene.dtype == "bf16" else np.uint32),
                                   ka.view(np.uint16 if w.scene.dtype == "bf16" else np.uint32))
     finally:

@@ -51,6 +51,18 @@ def test_bf16_is_widened_exactly(rb, tmp_path):
     assert np.array_equal(attr, synth.bf16_bits_to_f32(sc.attr))
 
 
+def test_mixed_layout_is_widened_exactly(rb, tmp_path):
+    """Host rows in the REFINE_BF16S layout (log-scales float32, the rest
+    bfloat16) are written with every value widened exactly."""
+    sc = synth.random_scene(seed=7, n=555, v=1).scene.to_bf16s()
+    rows = rb.MixedRows.from_float(sc.attr)
+    assert rows.row_stride == sc.n and np.array_equal(rows.float().numpy(), sc.attr)
+    path = str(tmp_path / "bf16s.ply")
+    rb.write_ply(path, sc.pos, rows)
+    pos, attr = rb.read_ply(path)
+    assert np.array_equal(pos, sc.pos) and np.array_equal(attr, sc.attr)
+
+
 def test_reads_properties_by_name(rb, tmp_path):
     """A file with the properties in another order plus an extra one."""
     rng = np.random.default_rng(0)

@@ -86,3 +86,9 @@ def test_bf16_storage_rounds_to_nearest_even():
     assert s16.dtype == "bf16" and np.array_equal(s16.pos, w.scene.pos)  # positions stay float32
     back = synth.bf16_bits_to_f32(s16.attr)
     assert np.all(np.abs(back - w.scene.attr) <= np.abs(w.scene.attr) * 2.0 ** -8)
+    # the mixed form: log-scale rows untouched, every other row as bf16 rounds it
+    s16s = w.scene.to_bf16s()
+    assert s16s.dtype == "bf16s" and s16s.attr.dtype == np.float32
+    assert np.array_equal(s16s.attr[:3], w.scene.attr[:3])
+    assert np.array_equal(s16s.attr[3:], back[3:])
+    assert np.array_equal(s16s.params_f64()[3:], s16s.attr.astype(np.float64))
