@@ -7,10 +7,11 @@
 // of the segment's earlier words.  The warp inverts the ranks of the kept
 // bits once (lane d of the output reads from the lane holding the d-th kept
 // primitive), then moves each of the 59 rows with one coalesced load, one
-// shuffle and one contiguous store; the loads of sixteen rows are in flight
-// at a time.  The CTA is 8 warps with a few hundred bytes of shared memory
-// and 40 registers per thread, so an SM keeps 48 warps, and their 768 row
-// loads, resident.
+// shuffle and one contiguous store.  The loads of sixteen float rows, or of
+// 28 bfloat16 rows (64-byte warp loads, so more of them must be in flight),
+// are issued together.  The CTA is 8 warps with a few hundred bytes of
+// shared memory; at 40 registers per thread (FP32 rows) an SM keeps 48 warps
+// and their 768 row loads resident, at 64 (bfloat16 rows) 32 warps and 896.
 //
 // Segment form (k_compact_seg, FP32 attributes only).  One warp owns a
 // whole segment (8 mask words); the offsets of its words come from a shuffle
@@ -27,7 +28,8 @@
 namespace refine {
 
 constexpr int kCmpWarps = 8;
-constexpr int kCmpBatch = 16;  // rows in flight per warp
+constexpr int kCmpBatch = 16;      // float rows in flight per warp
+constexpr int kCmpBatchB16 = 28;   // bfloat16 rows in flight per warp (56 rows in two steps)
 
 __device__ __forceinline__ float shfl_row(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ __nv_bfloat16 shfl_row(__nv_bfloat16 v, int src)
@@ -36,22 +38,22 @@ __device__ __forceinline__ __nv_bfloat16 shfl_row(__nv_bfloat16 v, int src)
     return __ushort_as_bfloat16(b);
 }
 
-template <typename T, int NR>
+template <typename T, int NR, int B = (sizeof(T) == 2 ? kCmpBatchB16 : kCmpBatch)>
 __device__ __forceinline__ void move_rows(const T *__restrict__ in, int64_t S, bool ld, int src, T *__restrict__ out,
                                           int64_t OS, bool st)
 {
 #pragma unroll 1
-    for (int r0 = 0; r0 < NR; r0 += kCmpBatch) {
-        T v[kCmpBatch];
+    for (int r0 = 0; r0 < NR; r0 += B) {
+        T v[B];
 #pragma unroll
-        for (int k = 0; k < kCmpBatch; ++k) v[k] = (ld && r0 + k < NR) ? in[k * S] : T(0.f);
+        for (int k = 0; k < B; ++k) v[k] = (ld && r0 + k < NR) ? in[k * S] : T(0.f);
 #pragma unroll
-        for (int k = 0; k < kCmpBatch; ++k) {
+        for (int k = 0; k < B; ++k) {
             const T x = shfl_row(v[k], src);
             if (st && r0 + k < NR) out[k * OS] = x;
         }
-        in += kCmpBatch * S;
-        out += kCmpBatch * OS;
+        in += B * S;
+        out += B * OS;
     }
 }
 
