@@ -228,7 +228,8 @@ refine_status refine_select(refine_ctx *ctx, const float *scores_dev, int64_t n,
  *   in             the scene (device)
  *   keep_mask_dev  device uint32 [ceil(n/32)] as written by refine_select
  *   out_pos_dev    device float32 [3][out_row_stride]
- *   out_attr_dev   device [56][out_row_stride] in in->dtype
+ *   out_attr_dev   device [56][out_row_stride] in in->dtype (the same row
+ *                  layout as the input, with out_row_stride)
  *   out_row_stride >= number of kept primitives
  *   kept_idx_dev   device int32 [n_keep] original indices, or NULL
  *   n_keep_out     host or NULL; non-NULL synchronises and returns the count
@@ -385,7 +386,7 @@ typedef struct refine_queue refine_queue;
  * the queue's threads synchronously, which is slower. */
 typedef struct refine_request {
     int64_t n;                       /* primitives, 1 .. 2^31 - 1                           */
-    int32_t dtype;                   /* REFINE_F32 or REFINE_BF16 (attribute rows)          */
+    int32_t dtype;                   /* REFINE_F32, REFINE_BF16 or REFINE_BF16S (attr rows) */
     int32_t n_views;                 /* 1 .. 65535                                          */
     const float *pos_host;           /* [3][n] float32 means                               */
     const void *attr_host;           /* [56][n] in dtype, rows as in refine_scene          */
@@ -509,7 +510,8 @@ refine_status refine_select_noalloc(const float *scores_dev, int64_t n, double r
  * written as 0 and ignored on reading). */
 
 /* Writes n primitives from host rows pos_host [3][row_stride] (float32) and
- * attr_host [56][row_stride] (dtype; bfloat16 is widened exactly).  EINVAL
+ * attr_host [56][row_stride] (dtype, any storage type; bfloat16 is widened
+ * exactly).  EINVAL
  * for bad arguments or a file that cannot be written. */
 refine_status refine_write_ply(const char *path, int64_t n, int32_t dtype, const float *pos_host,
                                const void *attr_host, int64_t row_stride);
