@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -125,4 +126,35 @@ def test_storage_type_codes_match_header():
     m = re.search(r"enum\s*\{\s*REFINE_F32\s*=\s*(\d+),\s*REFINE_BF16\s*=\s*(\d+),\s*REFINE_BF16S\s*=\s*(\d+)\s*\}", hdr)
     assert m, "storage-type enum not found in include/refine.h"
     assert (b.REFINE_F32, b.REFINE_BF16, b.REFINE_BF16S) == tuple(int(x) for x in m.groups())
+
+
+def test_mixed_rows_container_host_only():
+    """MixedRows (the REFINE_BF16S layout in one byte buffer): the float32
+    block and the bfloat16 block sit where the header says (the bfloat16 rows
+    at byte 12 * stride), column views keep the stride, the widened rows are
+    exact, and the column bytes are 118."""
+    torch = pytest.importorskip("torch")
+    from paper_2606_09074_gb300 import binding as b
+    rng = np.random.default_rng(3)
+    n, stride = 37, 40
+    a = rng.standard_normal((56, n)).astype(np.float32)
+    want = a.copy()
+    want[3:] = torch.from_numpy(a[3:]).to(torch.bfloat16).float().numpy()
+    m = b.MixedRows.empty(n, stride=stride)
+    m.f32_rows()[:, :n] = torch.from_numpy(a[:3])
+    m.bf16_rows()[:, :n] = torch.from_numpy(a[3:]).to(torch.bfloat16)
+    assert m.shape == (56, n) and m.stride(0) == stride and m.stride(1) == 1
+    assert b.attr_col_bytes(m) == 118 and m.buf.numel() == 118 * stride
+    raw = m.buf.numpy()
+    assert np.array_equal(raw[: 12 * stride].view(np.float32).reshape(3, stride)[:, :n], a[:3])
+    bf = raw[12 * stride: 118 * stride].view(np.uint16).reshape(53, stride)[:, :n]
+    assert np.array_equal(bf, want[3:].view(np.uint32) >> 16)
+    assert np.array_equal(m.float().numpy(), want)
+    v = m[:, :10]
+    assert v.shape == (56, 10) and v.stride(0) == stride and np.array_equal(v.float().numpy(), want[:, :10])
+    f = b.MixedRows.from_float(a)
+    assert f.row_stride == n and np.array_equal(f.float().numpy(), want)
+    e = b.empty_attr_like(f, 5)
+    assert isinstance(e, b.MixedRows) and e.shape == (56, 5)
+    assert b.empty_attr_like(torch.zeros(56, 3, dtype=torch.bfloat16), 4).dtype == torch.bfloat16
 
